@@ -1,0 +1,256 @@
+"""Plain CPU float64 oracle for one closed-shell RI-qsGW pass.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+module.  It shares no code with the CUDA library and never calls it.
+
+Each function follows one equation of the paper (arXiv 2210.17093, Sec. II) in
+the paper's order and notation, in float64 NumPy.  ``numpy.linalg.eigh`` and
+matrix products serve as library steps; there is no blocking or fusion beyond
+what the equations state.
+
+Notation (closed shell, real orbitals, S = I):
+  nb = n_basis, no = n_occ, nv = nb - no, n_ov = no*nv, na = n_aux;
+  i, j occupied; a, b virtual; p, q, m any MO; P auxiliary; s excitation;
+  transition index t = i*nv + (a - no) (occupied-major).
+
+Readings taken where the paper is silent or ambiguous (each one is listed in
+the design notes with its justification):
+  R1  Coulomb kernel sign in Eqs. (Casida.A/B): "+" (standard RPA), so for
+      singlets A = D + 2K, B = 2K with K_tu = (t|u).
+  R2  The spin sum over sigma' in Eq. (w.residue) for a closed shell contributes
+      sqrt(2), folded into (X+Y).
+  R3  The qsGW matrix of Eq. (Sigma.c.qsGW.real) takes the real part of
+      Eq. (Sigma.c.GW): 1/(x -/+ i eta) -> x/(x^2 + eta^2).
+  R4  (P|mu nu) are RI factors already contracted with the Coulomb metric.
+  R5  H0 = h + J with h_MO = diag(eps0) - J0 - Sigma_x0 (input read as an HF
+      solution) unless h is supplied; h_MO follows the orbital rotation.
+  R6  Aufbau occupations of the sorted updated energies; no mixing.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+# ----------------------------------------------------------------------------
+# Eq. (AO.to.MO) in RI form
+# ----------------------------------------------------------------------------
+def ri_mo_transform(L: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """B^P_pq = sum_{mu nu} C_{mu p} (P|mu nu) C_{nu q}.
+
+    Eq. (AO.to.MO) contracts the four AO indices of (mu nu|la ta) with C; with
+    (mu nu|la ta) = sum_P (P|mu nu)(P|la ta) (reading R4) the same contraction
+    acts on each three-centre factor, so (pq|rs) = sum_P B^P_pq B^P_rs (Eq. MO.4.ERI).
+    L: [na, nb, nb], C: [nb, nb] with column p the MO p (Eq. MO).
+    """
+    na = L.shape[0]
+    B = np.empty_like(L)
+    for P in range(na):
+        B[P] = C.T @ L[P] @ C
+    return B
+
+
+def transitions(n_basis: int, n_occ: int):
+    """(i, a) of each transition t = i*nv + (a - no), occupied-major."""
+    nv = n_basis - n_occ
+    i = np.repeat(np.arange(n_occ), nv)
+    a = np.tile(np.arange(n_occ, n_basis), n_occ)
+    return i, a
+
+
+# ----------------------------------------------------------------------------
+# Eqs. (Casida.AB.XY), (Casida.A), (Casida.B)
+# ----------------------------------------------------------------------------
+def casida_AB(B: np.ndarray, eps: np.ndarray, n_occ: int):
+    """Singlet (spin-summed) Casida blocks A and B.
+
+    Eq. (Casida.A): A = (eps_a - eps_i) delta + kernel, Eq. (Casida.B): B = kernel,
+    with the Coulomb kernel (ia sigma|jb sigma') summed over the two spins of a
+    closed shell (factor 2) and the "+" sign of reading R1.
+    Returns (A, Bc, D) with D_t = eps_a - eps_i.
+    """
+    nb = eps.shape[0]
+    i, a = transitions(nb, n_occ)
+    D = eps[a] - eps[i]
+    Bia = B[:, i, a]                 # [na, n_ov]: B^P_{ia}
+    K = Bia.T @ Bia                  # K_tu = (ia|jb) = sum_P B^P_ia B^P_jb
+    A = np.diag(D) + 2.0 * K
+    Bc = 2.0 * K
+    return A, Bc, D
+
+
+def casida_M(A: np.ndarray, Bc: np.ndarray, D: np.ndarray) -> np.ndarray:
+    """Symmetric reduction of Eq. (Casida.AB.XY) for real orbitals.
+
+    (A - B)^(1/2) (A + B) (A - B)^(1/2) Z = Omega^2 Z.  Here A - B = diag(D),
+    so M = D^(1/2) (A + B) D^(1/2) = D^2 + 4 D^(1/2) K D^(1/2).
+    """
+    sq = np.sqrt(D)
+    return sq[:, None] * (A + Bc) * sq[None, :]
+
+
+def rpa_eigensolve(M: np.ndarray, D: np.ndarray):
+    """Omega_s ascending and (X+Y)^s from the eigenpairs of M.
+
+    With M Z = Z Lambda: Omega = sqrt(Lambda) and, normalising (X-Y)^T (X+Y) = 1,
+    X + Y = (A - B)^(1/2) Z Omega^(-1/2).  The closed-shell spin sum of
+    Eq. (w.residue) contributes sqrt(2) (reading R2), folded in here:
+    (X+Y)_ts = sqrt(2) sqrt(D_t) Z_ts / sqrt(Omega_s).
+    Eigenvector gauge: the largest-magnitude component of each Z column is positive.
+    """
+    lam, Z = np.linalg.eigh(M)
+    if lam[0] <= 0.0:
+        raise FloatingPointError("RPA instability: M has a non-positive eigenvalue")
+    Z = fix_gauge(Z)
+    Omega = np.sqrt(lam)
+    XpY = np.sqrt(2.0) * np.sqrt(D)[:, None] * Z / np.sqrt(Omega)[None, :]
+    return Omega, XpY, Z
+
+
+def fix_gauge(Z: np.ndarray) -> np.ndarray:
+    """Flip each column so that its largest-magnitude entry is positive."""
+    idx = np.argmax(np.abs(Z), axis=0)
+    s = np.sign(Z[idx, np.arange(Z.shape[1])])
+    s[s == 0] = 1.0
+    return Z * s[None, :]
+
+
+# ----------------------------------------------------------------------------
+# Eq. (w.residue)
+# ----------------------------------------------------------------------------
+def gw_residues(B: np.ndarray, XpY: np.ndarray, n_occ: int):
+    """w^s_pq = sum_{ia} (pq|ia) (X+Y)^s_ia = sum_P B^P_pq R_Ps, R = B_ia^T-weighted.
+
+    R_Ps = sum_t B^P_t (X+Y)_ts (t = ia); returns (R [na, n_ov], w [n_ov, nb, nb]).
+    """
+    nb = B.shape[1]
+    i, a = transitions(nb, n_occ)
+    R = B[:, i, a] @ XpY
+    w = np.einsum("Ppq,Ps->spq", B, R, optimize=True)
+    return R, w
+
+
+# ----------------------------------------------------------------------------
+# Eq. (K): exchange, and Eq. (J): Hartree, in the MO basis
+# ----------------------------------------------------------------------------
+def sigma_x(B: np.ndarray, n_occ: int) -> np.ndarray:
+    """Sigma_x,pq = -sum_i (p i|i q) = -sum_i sum_P B^P_pi B^P_qi (Eq. K, one spin)."""
+    Bo = B[:, :, :n_occ]            # [na, nb, no]
+    return -np.einsum("Ppi,Pqi->pq", Bo, Bo, optimize=True)
+
+
+def hartree(B: np.ndarray, n_occ: int) -> np.ndarray:
+    """J_pq = sum_{sigma} sum_i (pq|ii) = 2 sum_P B^P_pq sum_i B^P_ii (Eqs. J, D)."""
+    rho = np.einsum("Pii->P", B[:, :n_occ, :n_occ])
+    return 2.0 * np.einsum("Ppq,P->pq", B, rho, optimize=True)
+
+
+# ----------------------------------------------------------------------------
+# Eqs. (Sigma.c.GW) and (Sigma.c.qsGW.real)
+# ----------------------------------------------------------------------------
+def g_real(x, eta: float):
+    """Re 1/(x -/+ i eta) = x / (x^2 + eta^2) (reading R3; same for both signs)."""
+    return x / (x * x + eta * eta)
+
+
+def sigma_c_rows(w: np.ndarray, eps: np.ndarray, Omega: np.ndarray, n_occ: int,
+                 eta: float) -> np.ndarray:
+    """S_pq = Re Sigma^GW_c,pq(omega = eps_p), Eq. (Sigma.c.GW).
+
+    Sigma_pq(w) = sum_{i,s} w^s_pi w^s_qi / (w - eps_i + Omega_s - i eta)
+                + sum_{a,s} w^s_pa w^s_qa / (w - eps_a - Omega_s + i eta).
+    Row p is taken at omega = eps_p.  The sum over the state m (= i or a) is a
+    loop; the sum over s for all (p, q) of one m is a matrix product.
+    """
+    nb = eps.shape[0]
+    S = np.zeros((nb, nb))
+    for m in range(nb):
+        shift = Omega if m < n_occ else -Omega        # -eps_i + Omega_s | -eps_a - Omega_s
+        x = eps[:, None] - eps[m] + shift[None, :]    # [p, s]
+        wm = w[:, :, m].T                             # [p, s] = w^s_pm
+        S += (wm * g_real(x, eta)) @ wm.T
+    return S
+
+
+def sigma_c_qs(S: np.ndarray) -> np.ndarray:
+    """Eq. (Sigma.c.qsGW.real): 1/2 [Sigma_mn(eps_n) + Sigma_nm(eps_m)] = 1/2 (S + S^T)^T."""
+    return 0.5 * (S + S.T)
+
+
+def sigma_c_at(w: np.ndarray, eps: np.ndarray, Omega: np.ndarray, n_occ: int,
+               eta: float, omega: float) -> np.ndarray:
+    """Re Sigma^GW_c,pq(omega) for one frequency, all (p, q) (Eq. Sigma.c.GW)."""
+    nb = eps.shape[0]
+    out = np.zeros((nb, nb))
+    for m in range(nb):
+        shift = Omega if m < n_occ else -Omega
+        gm = g_real(omega - eps[m] + shift, eta)     # [s]
+        wm = w[:, :, m]                               # [s, p]
+        out += (wm * gm[:, None]).T @ wm
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Eqs. (H), (GEP): quasiparticle update
+# ----------------------------------------------------------------------------
+def hf_core_mo(B: np.ndarray, eps: np.ndarray, n_occ: int) -> np.ndarray:
+    """h_MO = diag(eps) - J - Sigma_x: the one-body part that makes (eps, C) an
+    HF solution of Eq. (H) with Sigma_c = 0 (reading R5)."""
+    return np.diag(eps) - hartree(B, n_occ) - sigma_x(B, n_occ)
+
+
+def qs_update(h_mo: np.ndarray, J: np.ndarray, Sx: np.ndarray, Sc: np.ndarray,
+              C: np.ndarray):
+    """Solve H U = U diag(eps') with H = h + J + Sigma_x + Sigma_c (Eqs. H, GEP, S = I).
+
+    Returns (eps' ascending, C' = C U, h_MO' = U^T h_MO U, U), gauge as fix_gauge.
+    """
+    H = h_mo + J + Sx + Sc
+    H = 0.5 * (H + H.T)
+    e, U = np.linalg.eigh(H)
+    U = fix_gauge(U)
+    return e, C @ U, U.T @ h_mo @ U, U
+
+
+# ----------------------------------------------------------------------------
+# One qsGW iteration
+# ----------------------------------------------------------------------------
+def qsgw_pass(L: np.ndarray, eps: np.ndarray, C: np.ndarray, n_occ: int,
+              eta: float, h_mo: np.ndarray | None = None, correlation: bool = True) -> dict:
+    """One RI-qsGW iteration: Eqs. (AO.to.MO) -> (Casida) -> (w.residue) ->
+    (Sigma.c.GW, Sigma.c.qsGW.real, K) -> (H, GEP).
+
+    ``h_mo`` is the one-body Hamiltonian in the basis of the current orbitals; if
+    None it is derived from the input read as an HF solution (reading R5).
+    ``correlation=False`` sets Sigma_c = 0 (the exchange-only limit).
+    Returns every intermediate and the updated (eps', C', h_MO').
+    """
+    B = ri_mo_transform(L, C)
+    if h_mo is None:
+        h_mo = hf_core_mo(B, eps, n_occ)
+    A, Bc, D = casida_AB(B, eps, n_occ)
+    M = casida_M(A, Bc, D)
+    Omega, XpY, Z = rpa_eigensolve(M, D)
+    R, w = gw_residues(B, XpY, n_occ)
+    Sx = sigma_x(B, n_occ)
+    if correlation:
+        Sc = sigma_c_qs(sigma_c_rows(w, eps, Omega, n_occ, eta))
+    else:
+        Sc = np.zeros_like(Sx)
+    J = hartree(B, n_occ)
+    eps_new, C_new, h_new, U = qs_update(h_mo, J, Sx, Sc, C)
+    return {
+        "B": B, "D": D, "M": M, "Omega": Omega, "XpY": XpY, "Z": Z, "R": R, "w": w,
+        "sigma_x": Sx, "sigma_c": Sc, "J": J, "h_mo": h_mo,
+        "eps_new": eps_new, "C_new": C_new, "h_mo_new": h_new, "U": U,
+    }
+
+
+def qsgw_iterations(L, eps, C, n_occ, eta, n_iter, h_mo=None) -> list:
+    """n_iter successive qsGW iterations, each starting from the previous (eps', C')."""
+    out = []
+    for _ in range(n_iter):
+        r = qsgw_pass(L, eps, C, n_occ, eta, h_mo)
+        out.append(r)
+        eps, C, h_mo = r["eps_new"], r["C_new"], r["h_mo_new"]
+    return out

@@ -1,0 +1,38 @@
+"""Writes tests/golden/qsgw_nb24_no5_na72_seed0.json from the CPU oracle only.
+
+Workload: one closed-shell molecule, n_basis=24, n_occ=5, n_aux=72, seed 0,
+eta = 1e-3 Ha, one RI-qsGW pass (Eqs. AO.to.MO, Casida, w.residue, Sigma.c.GW,
+Sigma.c.qsGW.real, K, H, GEP of arXiv 2210.17093).  The values are the oracle's;
+the paper prints no worked example.  Run from the repository root:
+    python tests/golden/make_golden.py
+"""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import synthetic as sy  # noqa: E402
+from oracle import qsgw  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "qsgw_nb24_no5_na72_seed0.json")
+
+
+def main():
+    m = sy.molecule(24, 5, 72, 0)
+    r = qsgw.qsgw_pass(m["L"], m["eps"], m["C"], 5, sy.ETA)
+    doc = {
+        "source": "oracle/qsgw.py qsgw_pass; equations of arXiv 2210.17093 Sec. II",
+        "workload": {"n_basis": 24, "n_occ": 5, "n_aux": 72, "seed": 0, "eta": sy.ETA},
+        "Omega": r["Omega"].tolist(),
+        "eps_new": r["eps_new"].tolist(),
+        "sigma_x": r["sigma_x"].tolist(),
+        "sigma_c": r["sigma_c"].tolist(),
+    }
+    with open(OUT, "w") as f:
+        json.dump(doc, f, indent=0)
+
+
+if __name__ == "__main__":
+    main()
