@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Seconds per qsGW iteration of the RI-qsGW hot path on GB300 (one JSON line).
+
+A step is one qsGW iteration of one molecule -- stages (a) ri_mo_transform,
+(b) rpa_build, (c) rpa_eigensolve, (d) gw_residues, (e) sigma_assembly and
+(f) qs_update -- through the C ABI, on seeded synthetic inputs (synthetic.py)
+that stand in for the paper's cc-pVTZ alkanes.  Default workload: n_basis=200,
+n_occ=40, n_aux=600 (6,400 transitions, M is 6400^2 float64), seed 1, plain
+float64 on the GPU.  Each step continues the self-consistency from the previous
+one (the orbitals are updated in place).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent molecule (seed + rank): the units
+are independent, there is no data-path collective, scaling is weak.
+--impl reference times the CPU float64 oracle (oracle/) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic as sy  # noqa: E402
+
+METRIC = "s per qsGW iteration; TFLOP/s vs peak; mixed vs FP64 GPU speedup at ≤1 meV QP error"
+WORKLOADS = {
+    "B": dict(nb=200, no=40, na=600, seed=1),
+    "C": dict(nb=400, no=80, na=1200, seed=4),
+    "E": dict(nb=600, no=120, na=1800, seed=7),
+}
+# float64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
+# (NVIDIA lists 1.25 TFLOP/s FP64 for this part; a register-only DFMA loop measured 1.20).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def workload_flops(nb, no, na):
+    """Useful float64 flops per qsGW iteration, per kernel class (one product = 2 flops)."""
+    n = no * (nb - no)
+    return {
+        "sigma": 2.0 * nb * nb * na * n + 2.0 * nb ** 3 * n,      # w^s_pm per m block + S += (w g) w^T
+        "tridiag": 4.0 / 3.0 * n ** 3,                              # Householder reduction of M
+        "backtransform": 4.0 * na * n * n,                          # Q^T Xv and R = Y^T Z_T
+        "rpa_build": 1.0 * na * n * n,                              # lower half of Xv Xv^T
+        "ri_mo_transform": 4.0 * na * nb ** 3,
+        "sigma_x": 2.0 * nb * nb * na * no,
+        "qs_update": 4.0 / 3.0 * nb ** 3 + 6.0 * nb ** 3,
+    }
+
+
+def config_dict(wl, precision):
+    nb, no, na = wl["nb"], wl["no"], wl["na"]
+    n = no * (nb - no)
+    return {
+        "workload": f"closed-shell RI-qsGW iteration, n_basis={nb}, n_occ={no}, n_aux={na}, "
+                    f"{n} transitions, seed {wl['seed']} (+rank)",
+        "n_basis": nb, "n_occ": no, "n_aux": na, "n_transitions": n, "eta_ha": sy.ETA,
+        "precision": precision,
+        "l2": f"inputs larger than L2: L {na * nb * nb * 8 / 1e6:.0f} MB, M {n * n * 8 / 1e6:.0f} MB per step",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 9]
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except ImportError:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_steps(wl, steps, warmup, eta):
+    """Time `steps` oracle iterations after `warmup` (the CPU float64 reference)."""
+    from oracle import qsgw
+    m = sy.molecule(wl["nb"], wl["no"], wl["na"], wl["seed"])
+    L, eps, C, h = m["L"], m["eps"], m["C"], None
+    for _ in range(warmup):
+        r = qsgw.qsgw_pass(L, eps, C, wl["no"], eta, h)
+        eps, C, h = r["eps_new"], r["C_new"], r["h_mo_new"]
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        r = qsgw.qsgw_pass(L, eps, C, wl["no"], eta, h)
+        eps, C, h = r["eps_new"], r["C_new"], r["h_mo_new"]
+    return (time.perf_counter() - t0) / max(steps, 1)
+
+
+def run_reference(args, wl):
+    world, rank, local, dist = dist_setup()
+    if rank != 0:
+        return 0
+    steps, warmup = min(args.steps, 3), min(args.warmup, 1)
+    t = oracle_steps(wl, steps, warmup, sy.ETA)
+    cores = os.cpu_count()
+    sample = (f"{steps} oracle iteration(s) after {warmup} warm-up of the same workload "
+              f"(seed {wl['seed']}), NumPy float64 with multithreaded BLAS")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": t, "unit": "s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": warmup, "ms_per_step": t * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(wl, "fp64"),
+        "cpu_baseline": {"value": t, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": t, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args, wl):
+    import torch
+
+    world, rank, local, dist = dist_setup()
+    from paper_2210_17093_gb300 import Context
+
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    nb, no, na = wl["nb"], wl["no"], wl["na"]
+    n = no * (nb - no)
+    m = sy.molecule(nb, no, na, wl["seed"] + rank)
+    st = torch.cuda.Stream(device=dev)
+    L_d = torch.from_numpy(m["L"]).to(dev)
+    eps_d = torch.from_numpy(m["eps"]).to(dev)
+    C_d = torch.from_numpy(m["C"]).to(dev)
+    torch.cuda.synchronize()
+    flops = workload_flops(nb, no, na)
+    total_flops = sum(flops.values())
+
+    with Context(precision=args.precision, device=local, eta=sy.ETA, stream=st) as ctx:
+        ctx.set_ri(0, nb, na, L_d)
+        ctx.set_orbitals(0, no, eps_d, C_d)
+        for _ in range(args.warmup):
+            ctx.qs_step(0)
+        ctx.sync()
+        dominant = args.dominant
+        ctx.set_timing([dominant])
+        ctx.kernel_stats(reset=True)
+        l0 = ctx.launch_count()
+        sampler = ClockSampler(local)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier(dist)
+        torch.cuda.synchronize()
+        sampler.start()
+        e0.record(st)
+        for _ in range(args.steps):
+            ctx.qs_step(0)
+        e1.record(st)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        barrier(dist)
+        launches = ctx.launch_count() - l0
+        t_dev = e0.elapsed_time(e1) / 1e3
+        kstats = ctx.kernel_stats(reset=True)
+        ctx.set_timing([])
+        t_max = max_over_ranks(dist, t_dev)
+
+        # per-class breakdown: one more iteration with every class event-timed
+        ctx.set_timing(["gemm_f64", "tridiag_panel", "tridiag_syr2k", "bisect", "twisted",
+                        "backtransform", "sigma", "gemm_tc", "misc"])
+        ctx.kernel_stats(reset=True)
+        ctx.qs_step(0)
+        breakdown = ctx.kernel_stats(reset=True)
+        ctx.set_timing([])
+
+        # end to end through the public API: pinned host inputs and outputs every step
+        L_h = torch.from_numpy(m["L"]).pin_memory()
+        eps_h = torch.from_numpy(m["eps"]).pin_memory()
+        C_h = torch.from_numpy(m["C"]).pin_memory()
+        eps_o = torch.empty(nb, dtype=torch.float64).pin_memory()
+        C_o = torch.empty(nb * nb, dtype=torch.float64).pin_memory()
+        for _ in range(1):
+            ctx.set_ri(0, nb, na, L_h)
+            ctx.set_orbitals(0, no, eps_h, C_h)
+            ctx.qs_step(0, eps_o, C_o)
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 3))
+        for _ in range(e2e_steps):
+            ctx.set_ri(0, nb, na, L_h)
+            ctx.set_orbitals(0, no, eps_h, C_h)
+            ctx.qs_step(0, eps_o, C_o)
+        torch.cuda.synchronize()
+        t_e2e = (time.perf_counter() - t0) / e2e_steps
+        barrier(dist)
+        t_e2e = max_over_ranks(dist, t_e2e)
+
+    if rank != 0:
+        return 0
+    value = t_max / (args.steps * world)
+    nl, kms = kstats[dominant]
+    dom_flops = {"sigma": flops["sigma"], "tridiag_panel": flops["tridiag"] / 2,
+                 "tridiag_syr2k": flops["tridiag"] / 2, "backtransform": flops["backtransform"]}.get(dominant)
+    achieved = dom_flops * args.steps / (kms / 1e3) / 1e12 if (dom_flops and kms > 0) else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else args.precision,
+        "data": "synthetic", "config": config_dict(wl, args.precision),
+        "tflops": total_flops / (t_max / args.steps) / 1e12,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "roofline": {
+            "kernel": dominant, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+            "traffic": None, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+            "launches": nl, "event_ms": kms,
+        },
+        "stages_ms": {k: round(v[1], 3) for k, v in breakdown.items() if v[0]},
+        "e2e": {"value": t_e2e, "unit": "s",
+                "h2d_bytes_per_step": int((na * nb * nb + nb + nb * nb) * 8),
+                "d2h_bytes_per_step": int((nb + nb * nb) * 8)},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        t_cpu = oracle_steps(wl, 1, 0, sy.ETA)
+        line["cpu_baseline"] = {
+            "value": t_cpu, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"1 oracle iteration of the same workload (seed {wl['seed']}), NumPy float64, "
+                      f"BLAS threads = host cores"}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="B")
+    ap.add_argument("--precision", choices=["fp64", "bf16x3", "tf32x3"], default="fp64")
+    ap.add_argument("--dominant", default="sigma", help="kernel class reported in 'roofline'")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

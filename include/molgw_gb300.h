@@ -1,0 +1,181 @@
+/*
+ * molgw_gb300.h -- C ABI of the GB300 (sm_103a) RI-qsGW hot path.
+ *
+ * One closed-shell quasiparticle self-consistent GW iteration (arXiv 2210.17093,
+ * Sec. II.C) with the resolution-of-identity factorisation of the Coulomb
+ * integrals, split into the stages
+ *   (a) ri_mo_transform   B^P_pq = sum_{mu nu} C_{mu p} (P|mu nu) C_{nu q}        Eq. (AO.to.MO)
+ *   (b) rpa_build         M = D^2 + 4 D^1/2 K D^1/2, K_tu = sum_P B^P_t B^P_u    Eqs. (Casida.A/B)
+ *   (c) rpa_eigensolve    M Z = Z Omega^2, (X+Y) = sqrt(2) D^1/2 Z Omega^-1/2     Eq. (Casida.AB.XY)
+ *   (d) gw_residues       w^s_pq = sum_P B^P_pq (B^T (X+Y))_Ps                   Eq. (w.residue)
+ *   (e) sigma_assembly    Sigma_x (Eq. K) and the Hermitised Sigma_c
+ *                         1/2 Re[Sigma_pq(eps_p) + Sigma_pq(eps_q)]        Eqs. (Sigma.c.GW), (Sigma.c.qsGW.real)
+ *   (f) qs_update         H = h + J + Sigma_x + Sigma_c, H U = U eps', C' = C U   Eqs. (H), (GEP), (J)
+ *
+ * Conventions (all entry points)
+ *   - Closed shell, real orbitals, orthonormal AO basis (S = I).  Sizes:
+ *     nb = n_basis, no = n_occ, nv = nb - no, n_ov = no*nv, na = n_aux.
+ *     Transition index t = i*nv + (a - no), occupied-major.
+ *   - Every array argument is a plain pointer to float64 data that may live in
+ *     host memory (pageable or pinned) or in device memory of the context's
+ *     device; the library tells them apart with cudaPointerGetAttributes.
+ *     Matrices are row-major: X[r][c] at X[r*ld + c] with ld = the row length.
+ *   - Ownership: the caller owns every pointer it passes.  Inputs are copied
+ *     into library-owned device memory on the context stream before the call
+ *     returns control of the stream; a device input must stay valid until the
+ *     stream passes that point.  Outputs are written stream-ordered; for a host
+ *     output the call synchronises the stream before it returns.
+ *   - Errors: argument and call-order errors are returned at once and change no
+ *     state.  Errors found on the device (non-positive RPA eigenvalue, a
+ *     non-finite value, an eigensolver iteration cap or a bounded wait that ran
+ *     out) are latched in a device status word and returned by the next call
+ *     that synchronises (a call with a host output, molgw_b200_sync or
+ *     molgw_b200_destroy).
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef MOLGW_GB300_H
+#define MOLGW_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct molgw_ctx_s* molgw_ctx;
+
+enum molgw_status {
+  MOLGW_OK = 0,
+  MOLGW_E_ARG = -1,      /* bad argument (size, NULL, index out of range)           */
+  MOLGW_E_STATE = -2,    /* call out of order (e.g. rpa before set_ri/set_orbitals) */
+  MOLGW_E_NOMEM = -3,    /* device allocation failed                                */
+  MOLGW_E_CUDA = -4,     /* a CUDA runtime call failed                              */
+  MOLGW_E_NOCONV = -5,   /* eigensolver iteration cap reached                       */
+  MOLGW_E_TIMEOUT = -6,  /* a bounded device-side wait ran out                      */
+  MOLGW_E_NUMERIC = -7   /* non-positive RPA eigenvalue or non-finite value         */
+};
+
+/* Arithmetic of the dense contractions (a), (b), (d) and the Sigma_c
+ * contraction of (e).  The eigensolvers (c), (f) and the denominators
+ * eps_p - eps_m -/+ Omega_s always run in float64. */
+enum molgw_precision {
+  MOLGW_PREC_FP64 = 0,    /* float64 on the CUDA cores                                   */
+  MOLGW_PREC_BF16X3 = 1,  /* tcgen05 BF16 products, 3-term hi/lo split, FP32 accumulate  */
+  MOLGW_PREC_TF32X3 = 2   /* tcgen05 TF32 products, 3-term hi/lo split, FP32 accumulate  */
+};
+
+enum molgw_flags {
+  MOLGW_FLAG_FULL_XPY = 1u << 0, /* keep the full n_ov x n_ov (X+Y) so molgw_b200_rpa can return it */
+  MOLGW_FLAG_KTIMING = 1u << 1,  /* record CUDA events around kernels for molgw_b200_kernel_stats  */
+  MOLGW_FLAG_GRAPH = 1u << 2     /* replay each molecule's qs_step from a captured CUDA graph        */
+};
+
+typedef struct {
+  int32_t struct_size; /* sizeof(molgw_opts)                                        */
+  int32_t precision;   /* enum molgw_precision                                      */
+  int32_t max_mols;    /* molecules the context holds, indices 0 .. max_mols-1 (>=1) */
+  int32_t device;      /* CUDA device ordinal                                       */
+  double eta;          /* broadening eta > 0 of Eq. (Sigma.c.GW), Hartree           */
+  void* stream;        /* cudaStream_t to run on; NULL = a stream the context owns  */
+  uint32_t flags;      /* enum molgw_flags                                          */
+} molgw_opts;
+
+/* Create a context.  Returns MOLGW_E_ARG for a bad opts, MOLGW_E_CUDA if the
+ * device cannot be used.  *out is NULL on failure. */
+int molgw_b200_create(const molgw_opts* opts, molgw_ctx* out);
+
+/* Three-centre RI factors of molecule `mol`: L[P][mu][nu], n_aux x n_basis x
+ * n_basis, symmetric in (mu, nu), already contracted with the Coulomb metric
+ * so that (mu nu|la ta) = sum_P L[P][mu][nu] L[P][la][ta] (Sec. II.B names
+ * the RI approximation; Eq. (AO.4.ERI) is the integral it factorises).
+ * Clears the molecule's orbitals and every result: set_orbitals must follow.
+ * n_basis >= 2, n_aux >= 1. */
+int molgw_b200_set_ri(molgw_ctx ctx, int mol, int n_basis, int n_aux, const double* L);
+
+/* Orbitals of molecule `mol`: eps[n_basis] ascending MO energies, C[mu][p]
+ * (row mu, column = MO p, Eq. (MO)), orthonormal columns.  h_core[mu][nu] is
+ * the one-body Hamiltonian T + V_ext of Eq. (H) in the AO basis; NULL reads
+ * (eps, C) as a Hartree-Fock solution and derives h_MO = diag(eps) - J - Sigma_x
+ * from it at the next pass.  1 <= n_occ < n_basis; set_ri must come first. */
+int molgw_b200_set_orbitals(molgw_ctx ctx, int mol, int n_occ, const double* eps,
+                            const double* C, const double* h_core);
+
+/* Stages (a)-(c) for the current orbitals.  omega[n_ov] receives Omega_s
+ * ascending (may be NULL).  xpy[n_ov][n_ov] receives (X+Y)_ts (row t, column s)
+ * with each column's largest-magnitude entry of Z made positive; it needs
+ * MOLGW_FLAG_FULL_XPY (else MOLGW_E_ARG) and may be NULL.  mol = -1 runs every
+ * molecule that has RI factors and orbitals (omega and xpy must then be NULL). */
+int molgw_b200_rpa(molgw_ctx ctx, int mol, double* omega, double* xpy);
+
+/* Stages (a)-(e), reusing (a)-(c) when still valid for the current orbitals.
+ * sigma_x[n_basis][n_basis] and sigma_c[n_basis][n_basis] (the Hermitised qsGW
+ * correlation matrix) are in the basis of the current MOs; either may be NULL.
+ * mol = -1: every ready molecule, outputs must be NULL. */
+int molgw_b200_sigma(molgw_ctx ctx, int mol, double* sigma_x, double* sigma_c);
+
+/* One qsGW iteration: stages (a)-(f).  The updated energies and orbitals become
+ * the current ones; eps_out[n_basis] and C_out[n_basis][n_basis] receive them
+ * (either may be NULL).  Occupations follow the aufbau order of eps'.
+ * mol = -1: every ready molecule, outputs must be NULL. */
+int molgw_b200_qs_step(molgw_ctx ctx, int mol, double* eps_out, double* C_out);
+
+/* Synchronise the context stream and return the latched device status (then
+ * cleared). */
+int molgw_b200_sync(molgw_ctx ctx);
+
+/* Copy an intermediate of the last pass of molecule `mol` into out[count]
+ * (count must equal the item's size).  Items: */
+enum molgw_item {
+  MOLGW_ITEM_B = 0,        /* B[P][p][q], n_aux*n_basis^2, current orbitals           */
+  MOLGW_ITEM_OMEGA = 1,    /* Omega_s, n_ov                                           */
+  MOLGW_ITEM_R = 2,        /* R[P][s] = sum_t B^P_t (X+Y)_ts, n_aux*n_ov              */
+  MOLGW_ITEM_SIGMA_X = 3,  /* n_basis^2                                               */
+  MOLGW_ITEM_SIGMA_C = 4,  /* n_basis^2                                               */
+  MOLGW_ITEM_J = 5,        /* Hartree J_pq, n_basis^2                                 */
+  MOLGW_ITEM_H_MO = 6,     /* one-body h in the basis of the current MOs, n_basis^2    */
+  MOLGW_ITEM_EPS = 7,      /* current eps, n_basis                                    */
+  MOLGW_ITEM_C = 8         /* current C, n_basis^2                                    */
+};
+int molgw_b200_fetch(molgw_ctx ctx, int mol, int item, double* out, size_t count);
+
+/* Stages (a)-(b) only: the Casida matrix M[t][u] (n_ov x n_ov, both triangles)
+ * of molecule `mol` for its current orbitals. */
+int molgw_b200_rpa_matrix(molgw_ctx ctx, int mol, double* M);
+
+/* The float64 symmetric eigensolver used by stages (c) and (f), on its own:
+ * A[n][n] symmetric (read only), w[n] eigenvalues ascending, Z[n][n] (row i,
+ * column k = eigenvector k, largest-magnitude entry positive; may be NULL).
+ * Householder tridiagonalisation, bisection, twisted-factorisation vectors and
+ * the blocked back-transformation, all on the device. */
+int molgw_b200_eigh(molgw_ctx ctx, int n, const double* A, double* w, double* Z);
+
+/* Kernel timing collected while MOLGW_FLAG_KTIMING is set: for kernel class k
+ * (enum molgw_kernel) the number of launches and their summed event time in ms
+ * since the last reset.  names may be NULL.  Synchronises.  reset != 0 clears. */
+enum molgw_kernel {
+  MOLGW_K_GEMM_F64 = 0, MOLGW_K_TRIDIAG_PANEL = 1, MOLGW_K_TRIDIAG_SYR2K = 2,
+  MOLGW_K_BISECT = 3, MOLGW_K_TWISTED = 4, MOLGW_K_BACKTRANSFORM = 5,
+  MOLGW_K_SIGMA = 6, MOLGW_K_GEMM_TC = 7, MOLGW_K_MISC = 8, MOLGW_K_COUNT = 9
+};
+int molgw_b200_kernel_stats(molgw_ctx ctx, int64_t* launches, double* ms, int reset);
+
+/* Choose which kernel classes are timed with events (bit k = enum molgw_kernel
+ * k; 0 turns timing off, MOLGW_FLAG_KTIMING at create time sets all bits).
+ * Synchronises and returns the latched device status. */
+int molgw_b200_set_timing(molgw_ctx ctx, uint32_t class_mask);
+
+/* Number of device kernels this context has launched since creation. */
+int64_t molgw_b200_launch_count(molgw_ctx ctx);
+
+/* Free every resource of the context (synchronises first).  Returns the
+ * latched device status.  ctx may be NULL. */
+int molgw_b200_destroy(molgw_ctx ctx);
+
+/* Static text for a status code. */
+const char* molgw_b200_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOLGW_GB300_H */

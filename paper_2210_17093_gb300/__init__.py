@@ -1,0 +1,10 @@
+"""GB300-native (sm_103a) RI-qsGW hot path of arXiv 2210.17093.
+
+The compute runs in the CUDA library ``libmolgw_gb300.so`` built from ``csrc/``
+(C ABI in ``include/molgw_gb300.h``); this package only builds and binds it.
+"""
+from .native import (EXPORTS, FLAG_FULL_XPY, FLAG_GRAPH, FLAG_KTIMING, ITEM, KERNELS,  # noqa: F401
+                     Context, MolgwError, load)
+
+__all__ = ["Context", "MolgwError", "load", "EXPORTS", "FLAG_FULL_XPY", "FLAG_GRAPH", "FLAG_KTIMING",
+           "ITEM", "KERNELS"]

@@ -1,0 +1,328 @@
+// Float64 tridiagonal eigensolver and back-transformation.
+//
+//  * Eigenvalues: bisection on Sturm counts (one thread per eigenvalue index),
+//    the count taken from the LDL^T pivots q_j = d_j - x - e_{j-1}^2 / q_{j-1}
+//    with tiny pivots replaced by -pivmin (Kahan/Demmel; LAPACK dstebz style).
+//  * Eigenvectors: for each eigenvalue a twisted factorisation of T - lambda I
+//    (Fernando; Parlett and Dhillon): the stationary factor L+ D+ from the top,
+//    the progressive factor U- D- from the bottom, the twist index r minimising
+//    |gamma_r| = |D+_r + D-_r - (d_r - lambda)|, then z_r = 1 and the two
+//    bidiagonal solves outward.  One thread per eigenvector; vector s is stored
+//    as the strided column ZT[j*ldz + s] so that a warp reads and writes
+//    consecutive addresses at every step.
+//  * Back-transformation: compact-WY T factors per 64-column panel (dlarft),
+//    then X <- (I - V T^(T) V^T) X panel by panel with float64 GEMMs.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace molgw {
+
+namespace {
+
+constexpr int NBP = 64;
+
+__global__ void k_gersh(const double* d, const double* e, int n, double* out) {
+  // out[0] = lo, out[1] = hi, out[2] = max e^2, out[3] = max |d| + 2 max |e|
+  __shared__ double slo[256], shi[256], se[256];
+  double lo = INFINITY, hi = -INFINITY, em = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double ea = (k > 0) ? fabs(e[k - 1]) : 0.0;
+    const double eb = (k < n - 1) ? fabs(e[k]) : 0.0;
+    lo = fmin(lo, d[k] - ea - eb);
+    hi = fmax(hi, d[k] + ea + eb);
+    if (k < n - 1) em = fmax(em, e[k] * e[k]);
+  }
+  slo[threadIdx.x] = lo; shi[threadIdx.x] = hi; se[threadIdx.x] = em;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + s]);
+      shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + s]);
+      se[threadIdx.x] = fmax(se[threadIdx.x], se[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double nrm = fmax(fabs(slo[0]), fabs(shi[0]));
+    const double eps = 2.220446049250313e-16;
+    out[0] = slo[0] - 2.0 * eps * nrm * n - 1e-300;
+    out[1] = shi[0] + 2.0 * eps * nrm * n + 1e-300;
+    out[2] = fmax(se[0], 1e-300) * 2.2250738585072014e-308 * 64.0;  // pivmin
+    out[3] = nrm;
+  }
+}
+
+__device__ __forceinline__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2,
+                                           int n, double x, double pivmin) {
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  int cnt = (q < 0.0);
+  for (int j = 1; j < n; ++j) {
+    q = d[j] - x - e2[j - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += (q < 0.0);
+  }
+  return cnt;
+}
+
+__global__ void k_e2(const double* e, double* e2, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n - 1) e2[k] = e[k] * e[k];
+}
+
+__global__ void __launch_bounds__(128) k_bisect(const double* d, const double* e2, const double* g,
+                                                int n, double* lam, int* status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double lo = g[0], hi = g[1];
+  const double pivmin = g[2];
+  const double eps = 2.220446049250313e-16;
+  // relative tolerance, plus an absolute floor of a few ulps of ||T|| so that an
+  // eigenvalue at or near zero also converges
+  const double atol = 4.0 * eps * g[3] + 4.0 * pivmin;
+  bool ok = false;
+  for (int it = 0; it < 256; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + atol || mid <= lo || mid >= hi) {
+      ok = true;
+      break;
+    }
+    if (sturm_count(d, e2, n, mid, pivmin) > k) hi = mid; else lo = mid;
+  }
+  if (!ok) set_status(status, MOLGW_E_NOCONV);
+  lam[k] = 0.5 * (lo + hi);
+}
+
+// Twisted factorisation eigenvector of T - lambda_s I; S1/S2 are strided scratch
+// columns (element j at [j*ld + s]); the normalised vector is left in S1.
+__global__ void __launch_bounds__(128) k_twisted(const double* __restrict__ d, const double* __restrict__ e,
+                                                 const double* __restrict__ lam, const double* g, int n,
+                                                 double* S1, double* S2, long long ld) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const double l = lam[s];
+  // guard for zero pivots: a tiny multiple of the matrix scale
+  const double piv = fmax(g[3], 1e-300) * 2.220446049250313e-16 * 1e-6 + 1e-300;
+  double* z = S1 + s;
+  double* u = S2 + s;
+  // forward: D+_j into z[j]
+  double Dp = d[0] - l;
+  if (fabs(Dp) < piv) Dp = piv;
+  z[0] = Dp;
+  for (int j = 0; j < n - 1; ++j) {
+    const double Lp = e[j] / Dp;
+    Dp = d[j + 1] - l - Lp * e[j];
+    if (fabs(Dp) < piv) Dp = piv;
+    z[(long long)(j + 1) * ld] = Dp;
+  }
+  // backward: U-_j into u[j], gamma_j, twist index
+  double Dm = d[n - 1] - l;
+  if (fabs(Dm) < piv) Dm = piv;
+  double best = fabs(z[(long long)(n - 1) * ld] + Dm - (d[n - 1] - l));
+  int r = n - 1;
+  for (int j = n - 2; j >= 0; --j) {
+    const double Um = e[j] / Dm;
+    u[(long long)j * ld] = Um;
+    Dm = d[j] - l - Um * e[j];
+    if (fabs(Dm) < piv) Dm = piv;
+    const double gam = fabs(z[(long long)j * ld] + Dm - (d[j] - l));
+    if (gam < best) { best = gam; r = j; }
+  }
+  // solve outward from the twist index
+  double nrm2 = 1.0, big = 1.0;
+  int sgn = 1;
+  double zj = 1.0;
+  for (int j = r - 1; j >= 0; --j) {
+    const double Dpj = z[(long long)j * ld];
+    zj = -(e[j] / Dpj) * zj;
+    z[(long long)j * ld] = zj;
+    nrm2 += zj * zj;
+    if (fabs(zj) > big) { big = fabs(zj); sgn = (zj >= 0.0) ? 1 : -1; }
+  }
+  z[(long long)r * ld] = 1.0;
+  zj = 1.0;
+  for (int j = r; j < n - 1; ++j) {
+    zj = -u[(long long)j * ld] * zj;
+    z[(long long)(j + 1) * ld] = zj;
+    nrm2 += zj * zj;
+    if (fabs(zj) > big) { big = fabs(zj); sgn = (zj >= 0.0) ? 1 : -1; }
+  }
+  const double sc = (sgn > 0 ? 1.0 : -1.0) / sqrt(nrm2);
+  for (int j = 0; j < n; ++j) z[(long long)j * ld] *= sc;
+}
+
+// T factor of one panel from its Gram matrix G = V^T V (dlarft, forward, columnwise):
+// T(c,c) = tau_c, T(0:c, c) = -tau_c T(0:c, 0:c) G(0:c, c).
+__global__ void k_wy_t(const double* Gall, const double* tau, int n, double* Tall) {
+  const int p = blockIdx.x;
+  const int k0 = p * NBP;
+  const int nbp = min(NBP, (n - 1) - k0);
+  const double* G = Gall + (long long)p * NBP * NBP;
+  double* T = Tall + (long long)p * NBP * NBP;
+  __shared__ double Ts[NBP][NBP + 1];
+  __shared__ double gcol[NBP];
+  const int t = threadIdx.x;  // 64 threads
+  for (int r = 0; r < NBP; ++r) Ts[r][t] = 0.0;
+  __syncthreads();
+  for (int c = 0; c < nbp; ++c) {
+    const double tc = tau[k0 + c];
+    gcol[t] = (t < c) ? G[t * NBP + c] : 0.0;
+    __syncthreads();
+    double s = 0.0;
+    if (t < c) {
+      for (int k = t; k < c; ++k) s += Ts[t][k] * gcol[k];  // T upper triangular
+    }
+    __syncthreads();
+    if (t < c) Ts[t][c] = -tc * s;
+    if (t == c) Ts[c][c] = tc;
+    __syncthreads();
+  }
+  for (int r = 0; r < NBP; ++r) T[r * NBP + t] = Ts[r][t];
+}
+
+}  // namespace
+
+size_t eig_work_bytes(int nmax, int ncols_max) {
+  const size_t n = (size_t)std::max(nmax, 2);
+  const size_t nrbt = (n + 63) / 64;
+  const size_t npan = n / 64 + 1;
+  size_t part = 2 * ((n + 255) / 256 + 1) + nrbt * 128 + 4 * n * 128 + ((nrbt + 7) / 8) * n + 64;
+  size_t b = 0;
+  b += 4 * n;                         // d, e, tau, lam
+  b += n * 64;                        // Wp
+  b += part;                          // partials
+  b += 64;                            // scal
+  b += n * n;                         // S2
+  b += npan * 64 * 64;                // Tm
+  b += 2 * (size_t)64 * std::max(ncols_max, 64);   // tmp1, tmp2
+  b += (size_t)16 * 64 * std::max(ncols_max, 64);  // gk (split-K work)
+  b += npan * 64 * 64;                // Gram matrices (in gk region when large enough)
+  return b * sizeof(double);
+}
+
+int eig_work_alloc(EigWork& w, int nmax, int ncols_max) {
+  eig_work_free(w);
+  const size_t n = (size_t)std::max(nmax, 2);
+  const size_t nrbt = (n + 63) / 64;
+  const size_t npan = n / 64 + 1;
+  w.nmax = (int)n;
+  w.ncols_max = std::max(ncols_max, 64);
+  w.part_cap = 2 * ((n + 255) / 256 + 1) + nrbt * 128 + 4 * n * 128 + ((nrbt + 7) / 8) * n + 64;
+  w.gk_cap = std::max((size_t)16 * 64 * w.ncols_max, (size_t)8 * npan * 64 * 64);
+  double* p = nullptr;
+  const size_t total = 4 * n + n * 64 + w.part_cap + 64 + n * n + 2 * npan * 64 * 64 +
+                       2 * (size_t)64 * w.ncols_max + w.gk_cap;
+  if (cudaMalloc(&p, total * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return MOLGW_E_NOMEM; }
+  w.d = p; p += n; w.e = p; p += n; w.tau = p; p += n; w.lam = p; p += n;
+  w.Wp = p; p += n * 64;
+  w.part = p; p += w.part_cap;
+  w.scal = p; p += 64;
+  w.S2 = p; p += n * n;
+  w.Tm = p; p += 2 * npan * 64 * 64;   // T factors, then the Gram matrices
+  w.tmp1 = p; p += (size_t)64 * w.ncols_max;
+  w.tmp2 = p; p += (size_t)64 * w.ncols_max;
+  w.gk = p; p += w.gk_cap;
+  return MOLGW_OK;
+}
+
+void eig_work_free(EigWork& w) {
+  if (w.d) cudaFree(w.d);
+  w = EigWork{};
+}
+
+void tridiag_eigvals(Exec& ex, EigWork& w, int n) {
+  double* g = w.scal + 8;       // lo, hi, pivmin, norm
+  double* e2 = w.part;          // n-1 squares (partials are free after the reduction)
+  KScope ks(ex, MOLGW_K_BISECT, 3);
+  k_gersh<<<1, 256, 0, ex.st>>>(w.d, w.e, n, g);
+  k_e2<<<ceil_div(n, 256), 256, 0, ex.st>>>(w.e, e2, n);
+  k_bisect<<<ceil_div(n, 128), 128, 0, ex.st>>>(w.d, e2, g, n, w.lam, ex.status);
+}
+
+void tridiag_eigvecs(Exec& ex, EigWork& w, int n, double* ZT, long long ldz) {
+  KScope ks(ex, MOLGW_K_TWISTED, 1);
+  k_twisted<<<ceil_div(n, 128), 128, 0, ex.st>>>(w.d, w.e, w.lam, w.scal + 8, n, ZT, w.S2, ldz);
+}
+
+void build_wy(Exec& ex, EigWork& w, int n, const double* A) {
+  const int ncols = n - 1;
+  if (ncols <= 0) return;
+  const int npan = ceil_div(ncols, NBP);
+  double* G = w.Tm + (size_t)(w.nmax / NBP + 1) * NBP * NBP;   // npan x 64 x 64 Gram matrices
+  // G_p(a, b) = sum_r V_p(r, a) V_p(r, b); V_p = A[:, k0..k0+64) is zero above its
+  // unit diagonal, so every full panel is one batch entry of a K = n GEMM.
+  const int nfull = (ncols % NBP == 0) ? npan : npan - 1;
+  if (nfull > 0) {
+    GemmF64 gm;
+    gm.M = NBP; gm.N = NBP; gm.K = n; gm.batch = nfull;
+    gm.A = A; gm.sa_m = n; gm.sa_k = 1; gm.sa_b = (long long)NBP * n;
+    gm.B = A; gm.sb_k = 1; gm.sb_n = n; gm.sb_b = (long long)NBP * n;
+    gm.C = G; gm.sc_m = NBP; gm.sc_n = 1; gm.sc_b = NBP * NBP;
+    gm.ksplit = gemm_f64_pick_split(NBP, NBP, n, nfull, w.gk_cap);
+    gm.work = w.gk;
+    gm.kclass = MOLGW_K_BACKTRANSFORM;
+    gemm_f64(ex, gm);
+  }
+  if (nfull < npan) {
+    const int k0 = nfull * NBP;
+    const int nbp = ncols - k0;
+    GemmF64 gm;
+    gm.M = nbp; gm.N = nbp; gm.K = n - k0;
+    gm.A = A + k0 + (long long)k0 * n; gm.sa_m = n; gm.sa_k = 1;
+    gm.B = A + k0 + (long long)k0 * n; gm.sb_k = 1; gm.sb_n = n;
+    gm.C = G + (long long)nfull * NBP * NBP; gm.sc_m = NBP; gm.sc_n = 1;
+    gm.kclass = MOLGW_K_BACKTRANSFORM;
+    gemm_f64(ex, gm);
+  }
+  KScope ks(ex, MOLGW_K_BACKTRANSFORM, 1);
+  k_wy_t<<<npan, NBP, 0, ex.st>>>(G, w.tau, n, w.Tm);
+}
+
+void apply_q(Exec& ex, EigWork& w, int n, const double* A, double* X, long long sr, long long sc,
+             int ncols, int trans) {
+  const int nref = n - 1;
+  if (nref <= 0 || ncols <= 0) return;
+  const int npan = ceil_div(nref, NBP);
+  for (int c0 = 0; c0 < ncols; c0 += w.ncols_max) {
+    const int nc = std::min(w.ncols_max, ncols - c0);
+    double* Xc = X + (long long)c0 * sc;
+    for (int q = 0; q < npan; ++q) {
+      const int p = trans ? q : (npan - 1 - q);
+      const int k0 = p * NBP;
+      const int nbp = std::min(NBP, nref - k0);
+      const int m = n - k0;
+      const double* V = A + k0 + (long long)k0 * n;     // m x nbp, column-major
+      const double* T = w.Tm + (long long)p * NBP * NBP;
+      // tmp1 (nbp x nc) = V^T X[k0:, :]
+      GemmF64 g1;
+      g1.M = nbp; g1.N = nc; g1.K = m;
+      g1.A = V; g1.sa_m = n; g1.sa_k = 1;
+      g1.B = Xc + (long long)k0 * sr; g1.sb_k = sr; g1.sb_n = sc;
+      g1.C = w.tmp1; g1.sc_m = nc; g1.sc_n = 1;
+      g1.ksplit = gemm_f64_pick_split(nbp, nc, m, 1, w.gk_cap);
+      g1.work = w.gk;
+      g1.kclass = MOLGW_K_BACKTRANSFORM;
+      gemm_f64(ex, g1);
+      // tmp2 = T^T tmp1 (Q^T) or T tmp1 (Q)
+      GemmF64 g2;
+      g2.M = nbp; g2.N = nc; g2.K = nbp;
+      g2.A = T; if (trans) { g2.sa_m = 1; g2.sa_k = NBP; } else { g2.sa_m = NBP; g2.sa_k = 1; }
+      g2.B = w.tmp1; g2.sb_k = nc; g2.sb_n = 1;
+      g2.C = w.tmp2; g2.sc_m = nc; g2.sc_n = 1;
+      g2.kclass = MOLGW_K_BACKTRANSFORM;
+      gemm_f64(ex, g2);
+      // X[k0:, :] -= V tmp2
+      GemmF64 g3;
+      g3.M = m; g3.N = nc; g3.K = nbp;
+      g3.A = V; g3.sa_m = 1; g3.sa_k = n;
+      g3.B = w.tmp2; g3.sb_k = nc; g3.sb_n = 1;
+      g3.C = Xc + (long long)k0 * sr; g3.sc_m = sr; g3.sc_n = sc;
+      g3.alpha = -1.0; g3.beta = 1.0;
+      g3.kclass = MOLGW_K_BACKTRANSFORM;
+      gemm_f64(ex, g3);
+    }
+  }
+}
+
+}  // namespace molgw

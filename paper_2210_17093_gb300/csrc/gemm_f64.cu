@@ -1,0 +1,172 @@
+// Float64 GEMM on the CUDA cores (DFMA) for the plain-FP64 path.
+//
+// On GB300 the FP64 pipe delivers about 2 DFMA per clock per SM (measured
+// 1.2 TFLOP/s over 152 SMs), so a 64x64x16 shared-memory tile with a 4x4
+// register block per thread needs ~0.25 byte/FMA of L2 traffic and is bound by
+// the FP64 pipe, not by memory.  The kernel takes arbitrary element strides so
+// that one routine serves every contraction of the pass (row- or column-major
+// operands, batched over an auxiliary index, transposed views).
+#include "common.cuh"
+
+namespace molgw {
+
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 16, NT = 256;
+
+struct GemmParams {
+  int M, N, K, batch, ksplit, kchunk;
+  const double* A; long long sa_m, sa_k, sa_b;
+  const double* B; long long sb_k, sb_n, sb_b;
+  double* C; long long sc_m, sc_n, sc_b;
+  double alpha, beta;
+  int lower_only;
+  double* work;
+};
+
+__global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmParams p) {
+  const int bn = blockIdx.x, bm = blockIdx.y;
+  if (p.lower_only && bm < bn) return;
+  const int z = blockIdx.z;
+  const int b = z % p.batch, kz = z / p.batch;
+  const int k_begin = kz * p.kchunk;
+  const int k_end = min(p.K, k_begin + p.kchunk);
+
+  __shared__ double As[TK][TM + 1];
+  __shared__ double Bs[TK][TN + 1];
+
+  const int t = threadIdx.x;
+  const int tx = t % 16, ty = t / 16;
+  const int m0 = bm * TM, n0 = bn * TN;
+  const double* A = p.A + (long long)b * p.sa_b;
+  const double* B = p.B + (long long)b * p.sb_b;
+  const bool a_kfast = (p.sa_k == 1);
+  const bool b_nfast = (p.sb_n == 1);
+
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int k0 = k_begin; k0 < k_end; k0 += TK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int m, k;
+      if (a_kfast) { k = t % TK; m = t / TK + 16 * r; }
+      else { m = t % TM; k = t / TM + 4 * r; }
+      const int gm = m0 + m, gk = k0 + k;
+      As[k][m] = (gm < p.M && gk < k_end) ? A[(long long)gm * p.sa_m + (long long)gk * p.sa_k] : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int n, k;
+      if (b_nfast) { n = t % TN; k = t / TN + 4 * r; }
+      else { k = t % TK; n = t / TK + 16 * r; }
+      const int gn = n0 + n, gk = k0 + k;
+      Bs[k][n] = (gn < p.N && gk < k_end) ? B[(long long)gk * p.sb_k + (long long)gn * p.sb_n] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < TK; ++k) {
+      double a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+
+  if (p.ksplit > 1) {
+    double* W = p.work + ((long long)kz * p.batch + b) * (long long)p.M * p.N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int gm = m0 + ty + 16 * i;
+      if (gm >= p.M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gn = n0 + tx + 16 * j;
+        if (gn < p.N) W[(long long)gm * p.N + gn] = acc[i][j];
+      }
+    }
+    return;
+  }
+  double* C = p.C + (long long)b * p.sc_b;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= p.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= p.N) continue;
+      double* c = C + (long long)gm * p.sc_m + (long long)gn * p.sc_n;
+      const double v = p.alpha * acc[i][j];
+      *c = (p.beta == 0.0) ? v : fma(p.beta, *c, v);
+    }
+  }
+}
+
+// C = alpha * sum_kz work[kz] + beta * C, summed in kz order.
+__global__ void gemm_splitk_reduce(GemmParams p) {
+  const long long mn = (long long)p.M * p.N;
+  const long long total = mn * p.batch;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(idx / mn);
+    const long long r = idx % mn;
+    const int gm = (int)(r / p.N), gn = (int)(r % p.N);
+    if (p.lower_only && (gm / TM) < (gn / TN)) continue;
+    double s = 0.0;
+    for (int kz = 0; kz < p.ksplit; ++kz) s += p.work[((long long)kz * p.batch + b) * mn + r];
+    double* c = p.C + (long long)b * p.sc_b + (long long)gm * p.sc_m + (long long)gn * p.sc_n;
+    const double v = p.alpha * s;
+    *c = (p.beta == 0.0) ? v : fma(p.beta, *c, v);
+  }
+}
+
+}  // namespace
+
+int gemm_f64_pick_split(int M, int N, int K, int batch, size_t work_cap_doubles) {
+  const long long tiles = (long long)ceil_div(M, TM) * ceil_div(N, TN) * batch;
+  const long long target = 152LL * 4;
+  if (tiles >= target || K < 512) return 1;
+  long long ks = (target + tiles - 1) / tiles;
+  ks = std::min<long long>(ks, K / 256);
+  const long long per = (long long)M * N * batch;
+  if (per > 0) ks = std::min<long long>(ks, (long long)(work_cap_doubles / per));
+  return (int)std::max<long long>(1, std::min<long long>(ks, 64));
+}
+
+void gemm_f64(Exec& ex, const GemmF64& g) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+  GemmParams p;
+  p.M = g.M; p.N = g.N; p.K = g.K; p.batch = g.batch;
+  p.ksplit = (g.ksplit > 1 && g.work) ? g.ksplit : 1;
+  p.kchunk = ceil_div(std::max(g.K, 1), p.ksplit);
+  p.kchunk = ceil_div(p.kchunk, TK) * TK;
+  p.ksplit = std::max(1, ceil_div(std::max(g.K, 1), p.kchunk));
+  p.A = g.A; p.sa_m = g.sa_m; p.sa_k = g.sa_k; p.sa_b = g.sa_b;
+  p.B = g.B; p.sb_k = g.sb_k; p.sb_n = g.sb_n; p.sb_b = g.sb_b;
+  p.C = g.C; p.sc_m = g.sc_m; p.sc_n = g.sc_n; p.sc_b = g.sc_b;
+  p.alpha = g.alpha; p.beta = g.beta;
+  p.lower_only = g.lower_only ? 1 : 0;
+  p.work = g.work;
+  dim3 grid(ceil_div(g.N, TN), ceil_div(g.M, TM), g.batch * p.ksplit);
+  {
+    KScope ks(ex, g.kclass, p.ksplit > 1 ? 2 : 1);
+    gemm_f64_kernel<<<grid, NT, 0, ex.st>>>(p);
+    if (p.ksplit > 1) {
+      const long long total = (long long)g.M * g.N * g.batch;
+      const int blocks = (int)std::min<long long>(ceil_div(total, 256), 152LL * 16);
+      gemm_splitk_reduce<<<blocks, 256, 0, ex.st>>>(p);
+    }
+  }
+}
+
+}  // namespace molgw

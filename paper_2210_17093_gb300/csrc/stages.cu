@@ -1,0 +1,392 @@
+// Stage kernels of one RI-qsGW pass (float64 path) and their drivers.
+#include <math.h>
+
+#include "stages.cuh"
+
+namespace molgw {
+
+namespace {
+
+__device__ __forceinline__ long long gtid() { return blockIdx.x * (long long)blockDim.x + threadIdx.x; }
+__device__ __forceinline__ long long gstride() { return (long long)gridDim.x * blockDim.x; }
+
+inline int grid_for(long long n, int bs = 256) {
+  return (int)std::max<long long>(1, std::min<long long>((n + bs - 1) / bs, 152LL * 32));
+}
+
+// Xv[t + P*n_ov] = 2 sqrt(D_t) B[P][i][a]  (t = i*nv + a - no), D[t] = eps_a - eps_i.
+__global__ void k_gather_xv(const double* B, const double* eps, int nb, int no, int na,
+                            double* Xv, double* D) {
+  const int nv = nb - no;
+  const long long nov = (long long)no * nv;
+  const long long total = nov * na;
+  for (long long idx = gtid(); idx < total; idx += gstride()) {
+    const long long t = idx % nov;
+    const int P = (int)(idx / nov);
+    const int i = (int)(t / nv), a = no + (int)(t % nv);
+    const double Dt = eps[a] - eps[i];
+    if (P == 0) D[t] = Dt;
+    Xv[idx] = 2.0 * sqrt(Dt) * B[(long long)P * nb * nb + (long long)i * nb + a];
+  }
+}
+
+__global__ void k_add_diag_sq(double* M, const double* D, long long n) {
+  for (long long t = gtid(); t < n; t += gstride()) M[t + t * n] += D[t] * D[t];
+}
+
+// Omega = sqrt(lambda); status NUMERIC if lambda <= 0 or not finite.
+__global__ void k_omega(const double* lam, double* Om, int n, int* status) {
+  for (long long s = gtid(); s < n; s += gstride()) {
+    const double l = lam[s];
+    if (!(l > 0.0) || !isfinite(l)) { set_status(status, MOLGW_E_NUMERIC); Om[s] = 0.0; }
+    else Om[s] = sqrt(l);
+  }
+}
+
+// R[P][s] *= 1 / sqrt(2 Omega_s)
+__global__ void k_scale_r(double* R, const double* Om, int na, int nov) {
+  const long long total = (long long)na * nov;
+  for (long long idx = gtid(); idx < total; idx += gstride()) {
+    const int s = (int)(idx % nov);
+    const double o = Om[s];
+    R[idx] = (o > 0.0) ? R[idx] / sqrt(2.0 * o) : 0.0;
+  }
+}
+
+// (X+Y)[t][s] = sqrt(2 D_t / Omega_s) Z[t][s] with the gauge of column s fixed
+// (largest |Z[t][s]| positive).  Z row-major n x n; one thread per column.
+__global__ void k_xpy(const double* Z, const double* D, const double* Om, int n, double* X) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  double big = -1.0, sg = 1.0;
+  for (int t = 0; t < n; ++t) {
+    const double z = Z[(long long)t * n + s];
+    if (fabs(z) > big) { big = fabs(z); sg = (z >= 0.0) ? 1.0 : -1.0; }
+  }
+  const double o = Om[s];
+  for (int t = 0; t < n; ++t)
+    X[(long long)t * n + s] = sg * sqrt(2.0 * D[t] / o) * Z[(long long)t * n + s];
+}
+
+// Bo[p][P*no + i] = B[P][p][i]
+__global__ void k_gather_bocc(const double* B, int nb, int no, int na, double* Bo) {
+  const long long K = (long long)na * no;
+  const long long total = (long long)nb * K;
+  for (long long idx = gtid(); idx < total; idx += gstride()) {
+    const int p = (int)(idx / K);
+    const long long k = idx % K;
+    const int P = (int)(k / no), i = (int)(k % no);
+    Bo[idx] = B[(long long)P * nb * nb + (long long)p * nb + i];
+  }
+}
+
+// rho_P = sum_i B[P][i][i]
+__global__ void k_rho(const double* B, int nb, int no, int na, double* rho) {
+  for (long long P = gtid(); P < na; P += gstride()) {
+    double s = 0.0;
+    for (int i = 0; i < no; ++i) s += B[P * nb * nb + (long long)i * nb + i];
+    rho[P] = s;
+  }
+}
+
+// J[pq] = 2 sum_P B[P][pq] rho_P
+__global__ void k_hartree(const double* B, const double* rho, int nb, int na, double* J) {
+  const long long nn = (long long)nb * nb;
+  for (long long pq = gtid(); pq < nn; pq += gstride()) {
+    double s = 0.0;
+    for (int P = 0; P < na; ++P) s += B[(long long)P * nn + pq] * rho[P];
+    J[pq] = 2.0 * s;
+  }
+}
+
+// Pb[p][mm][s] = Wb[p][mm][s] * g(eps_p - eps_m -/+ Omega_s), m = m0 + mm.
+// The shift is +Omega_s for an occupied m (pole eps_i - Omega_s), -Omega_s for a
+// virtual m; the subtraction is float64 and g(x) = x / (x^2 + eta^2).
+__global__ void k_apply_g(const double* Wb, const double* eps, const double* Om, int nb, int no,
+                          int m0, int mb, int nov, double eta, double* Pb) {
+  const long long K = (long long)mb * nov;
+  const long long total = (long long)nb * K;
+  const double eta2 = eta * eta;
+  for (long long idx = gtid(); idx < total; idx += gstride()) {
+    const int p = (int)(idx / K);
+    const long long k = idx % K;
+    const int mm = (int)(k / nov), s = (int)(k % nov);
+    const int m = m0 + mm;
+    const double x = (m < no) ? (eps[p] - eps[m]) + Om[s] : (eps[p] - eps[m]) - Om[s];
+    Pb[idx] = Wb[idx] * (x / (x * x + eta2));
+  }
+}
+
+// out = 1/2 (S + S^T)
+__global__ void k_symmetrize(const double* S, int n, double* out) {
+  const long long nn = (long long)n * n;
+  for (long long idx = gtid(); idx < nn; idx += gstride()) {
+    const int p = (int)(idx / n), q = (int)(idx % n);
+    out[idx] = 0.5 * (S[idx] + S[(long long)q * n + p]);
+  }
+}
+
+// h = diag(eps) - J - Sx
+__global__ void k_hf_core(const double* eps, const double* J, const double* Sx, int n, double* h) {
+  const long long nn = (long long)n * n;
+  for (long long idx = gtid(); idx < nn; idx += gstride()) {
+    const int p = (int)(idx / n), q = (int)(idx % n);
+    h[idx] = ((p == q) ? eps[p] : 0.0) - J[idx] - Sx[idx];
+  }
+}
+
+// H = 1/2 [(h + J + Sx + Sc) + (.)^T], written column-major (= row-major, symmetric).
+__global__ void k_build_h(const double* h, const double* J, const double* Sx, const double* Sc, int n,
+                          double* H) {
+  const long long nn = (long long)n * n;
+  for (long long idx = gtid(); idx < nn; idx += gstride()) {
+    const int p = (int)(idx / n), q = (int)(idx % n);
+    const long long tr = (long long)q * n + p;
+    const double a = h[idx] + J[idx] + Sx[idx] + Sc[idx];
+    const double b = h[tr] + J[tr] + Sx[tr] + Sc[tr];
+    H[idx] = 0.5 * (a + b);
+  }
+}
+
+// Fix the sign of each column of U (row-major n x n): largest |entry| positive.
+__global__ void k_gauge_cols(double* U, int n) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  double big = -1.0, sg = 1.0;
+  for (int t = 0; t < n; ++t) {
+    const double z = U[(long long)t * n + s];
+    if (fabs(z) > big) { big = fabs(z); sg = (z >= 0.0) ? 1.0 : -1.0; }
+  }
+  if (sg < 0.0)
+    for (int t = 0; t < n; ++t) U[(long long)t * n + s] = -U[(long long)t * n + s];
+}
+
+__global__ void k_copy(const double* a, double* b, long long n) {
+  for (long long i = gtid(); i < n; i += gstride()) b[i] = a[i];
+}
+
+// M[t + u*n] = M[u + t*n] for u > t (copy the lower triangle to the upper one).
+__global__ void k_fill_upper(double* M, long long n) {
+  const long long total = n * n;
+  for (long long idx = gtid(); idx < total; idx += gstride()) {
+    const long long t = idx % n, u = idx / n;
+    if (u > t) M[idx] = M[u + t * n];
+  }
+}
+
+__global__ void k_check_finite(const double* a, long long n, int* status) {
+  for (long long i = gtid(); i < n; i += gstride())
+    if (!isfinite(a[i])) { set_status(status, MOLGW_E_NUMERIC); return; }
+}
+
+}  // namespace
+
+void dev_copy(Exec& ex, const double* a, double* b, long long n) {
+  KScope ks(ex, MOLGW_K_MISC);
+  k_copy<<<grid_for(n), 256, 0, ex.st>>>(a, b, n);
+}
+
+void fill_upper(Exec& ex, double* M, long long n) {
+  KScope ks(ex, MOLGW_K_MISC);
+  k_fill_upper<<<grid_for(n * n), 256, 0, ex.st>>>(M, n);
+}
+
+void check_finite(Exec& ex, const double* a, long long n) {
+  KScope ks(ex, MOLGW_K_MISC);
+  k_check_finite<<<grid_for(n), 256, 0, ex.st>>>(a, n, ex.status);
+}
+
+// (a) B[P] = C^T L[P] C as two float64 GEMMs (through T1[P][mu][q]).
+void stage_ri_mo_transform(Exec& ex, MolBuf& m) {
+  const int nb = m.nb, na = m.na;
+  const long long nn = (long long)nb * nb;
+  GemmF64 g1;
+  g1.M = na * nb; g1.N = nb; g1.K = nb;
+  g1.A = m.L; g1.sa_m = nb; g1.sa_k = 1;
+  g1.B = m.C; g1.sb_k = nb; g1.sb_n = 1;
+  g1.C = m.T1; g1.sc_m = nb; g1.sc_n = 1;
+  gemm_f64(ex, g1);
+  GemmF64 g2;
+  g2.M = nb; g2.N = nb; g2.K = nb; g2.batch = na;
+  g2.A = m.C; g2.sa_m = 1; g2.sa_k = nb; g2.sa_b = 0;          // C^T
+  g2.B = m.T1; g2.sb_k = nb; g2.sb_n = 1; g2.sb_b = nn;
+  g2.C = m.B; g2.sc_m = nb; g2.sc_n = 1; g2.sc_b = nn;
+  gemm_f64(ex, g2);
+}
+
+// Hartree J and exchange Sigma_x from B (Eqs. J, K in the MO basis).
+void stage_j_sigx(Exec& ex, MolBuf& m, Scratch& s) {
+  const int nb = m.nb, na = m.na, no = m.no;
+  {
+    KScope ks(ex, MOLGW_K_MISC, 3);
+    k_rho<<<grid_for(na), 256, 0, ex.st>>>(m.B, nb, no, na, s.rho);
+    k_hartree<<<grid_for((long long)nb * nb), 256, 0, ex.st>>>(m.B, s.rho, nb, na, m.J);
+    k_gather_bocc<<<grid_for((long long)nb * na * no), 256, 0, ex.st>>>(m.B, nb, no, na, m.T1);
+  }
+  const long long K = (long long)na * no;
+  GemmF64 g;
+  g.M = nb; g.N = nb; g.K = (int)K;
+  g.A = m.T1; g.sa_m = K; g.sa_k = 1;
+  g.B = m.T1; g.sb_k = 1; g.sb_n = K;
+  g.C = m.sigx; g.sc_m = nb; g.sc_n = 1;
+  g.alpha = -1.0;
+  g.ksplit = gemm_f64_pick_split(nb, nb, (int)K, 1, s.splitk_cap);
+  g.work = s.splitk;
+  gemm_f64(ex, g);
+}
+
+// (b) M = diag(D^2) + Xv Xv^T, Xv = 2 D^1/2 B_ia^T (n_ov x n_aux, column-major).
+void stage_rpa_build(Exec& ex, MolBuf& m) {
+  const int nb = m.nb, na = m.na, no = m.no;
+  const long long nov = m.nov;
+  {
+    KScope ks(ex, MOLGW_K_MISC);
+    k_gather_xv<<<grid_for(nov * na), 256, 0, ex.st>>>(m.B, m.eps, nb, no, na, m.Xv, m.D);
+  }
+  GemmF64 g;
+  g.M = (int)nov; g.N = (int)nov; g.K = na;
+  g.A = m.Xv; g.sa_m = 1; g.sa_k = nov;
+  g.B = m.Xv; g.sb_k = nov; g.sb_n = 1;
+  g.C = m.M; g.sc_m = 1; g.sc_n = nov;
+  g.lower_only = true;
+  gemm_f64(ex, g);
+  KScope ks(ex, MOLGW_K_MISC);
+  k_add_diag_sq<<<grid_for(nov), 256, 0, ex.st>>>(m.M, m.D, nov);
+}
+
+// (c) eigenpairs of M; Omega; thin back-transformation to R = B^T (X+Y).
+void stage_rpa_eigensolve(Exec& ex, MolBuf& m, EigWork& w, Scratch& s, bool full_xpy) {
+  const int n = (int)m.nov, na = m.na;
+  tridiagonalize(ex, w, n, m.M);
+  tridiag_eigvals(ex, w, n);
+  {
+    KScope ks(ex, MOLGW_K_MISC);
+    k_omega<<<grid_for(n), 256, 0, ex.st>>>(w.lam, m.Om, n, ex.status);
+  }
+  tridiag_eigvecs(ex, w, n, m.ZT, n);
+  build_wy(ex, w, n, m.M);
+  // Y = Q^T Xv in place (column-major n x na)
+  apply_q(ex, w, n, m.M, m.Xv, 1, n, na, 1);
+  // R[P][s] = sum_t Y[t][P] ZT[t][s] / sqrt(2 Omega_s)
+  GemmF64 g;
+  g.M = na; g.N = n; g.K = n;
+  g.A = m.Xv; g.sa_m = n; g.sa_k = 1;
+  g.B = m.ZT; g.sb_k = n; g.sb_n = 1;
+  g.C = m.R; g.sc_m = n; g.sc_n = 1;
+  g.kclass = MOLGW_K_BACKTRANSFORM;
+  gemm_f64(ex, g);
+  {
+    KScope ks(ex, MOLGW_K_MISC);
+    k_scale_r<<<grid_for((long long)na * n), 256, 0, ex.st>>>(m.R, m.Om, na, n);
+  }
+  if (full_xpy && m.XpY) {
+    // Z = Q Z_T in place in ZT (row-major), then (X+Y)
+    apply_q(ex, w, n, m.M, m.ZT, n, 1, n, 0);
+    KScope ks(ex, MOLGW_K_MISC);
+    k_xpy<<<ceil_div(n, 128), 128, 0, ex.st>>>(m.ZT, m.D, m.Om, n, m.XpY);
+  }
+}
+
+// (d)+(e): w per block of m, the g-weighted copy, S += P W^T; Sigma_c = (S + S^T)/2.
+void stage_sigma(Exec& ex, MolBuf& m, Scratch& s, double eta) {
+  const int nb = m.nb, na = m.na, no = m.no;
+  const int nov = (int)m.nov;
+  const long long nn = (long long)nb * nb;
+  const int mb = std::max(1, std::min(nb, (int)(s.wblk_cap / ((long long)nb * nov))));
+  for (int m0 = 0; m0 < nb; m0 += mb) {
+    const int cnt = std::min(mb, nb - m0);
+    const long long K = (long long)cnt * nov;
+    // Wb[p][mm][s] = sum_P B[P][m][p] R[P][s]
+    GemmF64 g;
+    g.M = nb; g.N = nov; g.K = na; g.batch = cnt;
+    g.A = m.B + (long long)m0 * nb; g.sa_m = 1; g.sa_k = nn; g.sa_b = nb;
+    g.B = m.R; g.sb_k = nov; g.sb_n = 1; g.sb_b = 0;
+    g.C = s.wblk; g.sc_m = K; g.sc_n = 1; g.sc_b = nov;
+    g.kclass = MOLGW_K_SIGMA;
+    gemm_f64(ex, g);
+    {
+      KScope ks(ex, MOLGW_K_SIGMA);
+      k_apply_g<<<grid_for(nb * K), 256, 0, ex.st>>>(s.wblk, m.eps, m.Om, nb, no, m0, cnt, nov, eta, s.pblk);
+    }
+    GemmF64 h;
+    h.M = nb; h.N = nb; h.K = (int)K;
+    h.A = s.pblk; h.sa_m = K; h.sa_k = 1;
+    h.B = s.wblk; h.sb_k = 1; h.sb_n = K;
+    h.C = s.S; h.sc_m = nb; h.sc_n = 1;
+    h.beta = (m0 == 0) ? 0.0 : 1.0;
+    h.ksplit = gemm_f64_pick_split(nb, nb, (int)K, 1, s.splitk_cap);
+    h.work = s.splitk;
+    h.kclass = MOLGW_K_SIGMA;
+    gemm_f64(ex, h);
+  }
+  KScope ks(ex, MOLGW_K_MISC);
+  k_symmetrize<<<grid_for(nn), 256, 0, ex.st>>>(s.S, nb, m.sigc);
+}
+
+void derive_h_from_hf(Exec& ex, MolBuf& m) {
+  KScope ks(ex, MOLGW_K_MISC);
+  k_hf_core<<<grid_for((long long)m.nb * m.nb), 256, 0, ex.st>>>(m.eps, m.J, m.sigx, m.nb, m.hmo);
+}
+
+// h_MO = C^T h_AO C (h_AO row-major in `hao`, result into m.hmo).
+void h_ao_to_mo(Exec& ex, MolBuf& m, const double* hao, Scratch& s) {
+  const int nb = m.nb;
+  GemmF64 g1;   // tmp = h C
+  g1.M = nb; g1.N = nb; g1.K = nb;
+  g1.A = hao; g1.sa_m = nb; g1.sa_k = 1;
+  g1.B = m.C; g1.sb_k = nb; g1.sb_n = 1;
+  g1.C = s.S; g1.sc_m = nb; g1.sc_n = 1;
+  gemm_f64(ex, g1);
+  GemmF64 g2;   // hmo = C^T tmp
+  g2.M = nb; g2.N = nb; g2.K = nb;
+  g2.A = m.C; g2.sa_m = 1; g2.sa_k = nb;
+  g2.B = s.S; g2.sb_k = nb; g2.sb_n = 1;
+  g2.C = m.hmo; g2.sc_m = nb; g2.sc_n = 1;
+  gemm_f64(ex, g2);
+}
+
+// Dense symmetric eigensolver on the device: A (n x n symmetric, destroyed) ->
+// lam (w.lam) and, if Z != NULL, eigenvectors Z row-major (column k = vector k).
+void eigh_dense(Exec& ex, EigWork& w, int n, double* A, double* Z) {
+  tridiagonalize(ex, w, n, A);
+  tridiag_eigvals(ex, w, n);
+  if (!Z) return;
+  tridiag_eigvecs(ex, w, n, Z, n);
+  build_wy(ex, w, n, A);
+  apply_q(ex, w, n, A, Z, n, 1, n, 0);
+  KScope ks(ex, MOLGW_K_MISC);
+  k_gauge_cols<<<ceil_div(n, 128), 128, 0, ex.st>>>(Z, n);
+}
+
+// (f) H = h + J + Sx + Sc; H U = U eps'; C' = C U; h' = U^T h U.
+void stage_qs_update(Exec& ex, MolBuf& m, EigWork& w, Scratch& s) {
+  const int nb = m.nb;
+  const long long nn = (long long)nb * nb;
+  {
+    KScope ks(ex, MOLGW_K_MISC);
+    k_build_h<<<grid_for(nn), 256, 0, ex.st>>>(m.hmo, m.J, m.sigx, m.sigc, nb, s.H);
+  }
+  eigh_dense(ex, w, nb, s.H, s.U);
+  dev_copy(ex, w.lam, m.eps, nb);
+  GemmF64 g1;   // C' = C U  (into S, then copy)
+  g1.M = nb; g1.N = nb; g1.K = nb;
+  g1.A = m.C; g1.sa_m = nb; g1.sa_k = 1;
+  g1.B = s.U; g1.sb_k = nb; g1.sb_n = 1;
+  g1.C = s.S; g1.sc_m = nb; g1.sc_n = 1;
+  gemm_f64(ex, g1);
+  dev_copy(ex, s.S, m.C, nn);
+  GemmF64 g2;   // tmp = h U
+  g2.M = nb; g2.N = nb; g2.K = nb;
+  g2.A = m.hmo; g2.sa_m = nb; g2.sa_k = 1;
+  g2.B = s.U; g2.sb_k = nb; g2.sb_n = 1;
+  g2.C = s.S; g2.sc_m = nb; g2.sc_n = 1;
+  gemm_f64(ex, g2);
+  GemmF64 g3;   // h' = U^T tmp
+  g3.M = nb; g3.N = nb; g3.K = nb;
+  g3.A = s.U; g3.sa_m = 1; g3.sa_k = nb;
+  g3.B = s.S; g3.sb_k = nb; g3.sb_n = 1;
+  g3.C = m.hmo; g3.sc_m = nb; g3.sc_n = 1;
+  gemm_f64(ex, g3);
+}
+
+}  // namespace molgw

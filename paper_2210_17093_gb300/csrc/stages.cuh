@@ -1,0 +1,54 @@
+// Per-molecule device buffers and the stage drivers of one RI-qsGW pass.
+#pragma once
+#include "common.cuh"
+
+namespace molgw {
+
+struct MolBuf {
+  int nb = 0, na = 0, no = 0;
+  int alloc_no = 0;            // n_occ the orbital-size buffers were allocated for
+  long long nov = 0;
+  bool have_ri = false, have_orb = false;
+  bool h_ready = false;        // hmo holds h in the basis of the current MOs
+  bool b_valid = false;        // B for the current orbitals
+  bool jx_valid = false;       // J, Sigma_x for the current orbitals
+  bool rpa_valid = false;      // Omega, R (and ZT) for the current orbitals
+  bool sigma_valid = false;    // Sigma_c for the current orbitals
+  bool have_b = false, have_rpa = false, have_jx = false, have_sigma = false;  // ever computed
+  // inputs / state
+  double *L = nullptr, *eps = nullptr, *C = nullptr, *hmo = nullptr;
+  // intermediates
+  double *B = nullptr, *T1 = nullptr;          // n_aux x nb x nb each
+  double *Xv = nullptr, *D = nullptr;          // n_ov x n_aux (column-major), n_ov
+  double *M = nullptr, *ZT = nullptr;          // n_ov x n_ov each
+  double *Om = nullptr, *R = nullptr;          // n_ov, n_aux x n_ov
+  double *XpY = nullptr;                       // n_ov x n_ov (FULL_XPY only)
+  double *J = nullptr, *sigx = nullptr, *sigc = nullptr;  // nb x nb
+  std::vector<void*> ri_allocs, orb_allocs;
+};
+
+struct Scratch {
+  double* rho = nullptr;        // n_aux
+  double* splitk = nullptr;     // split-K partials
+  size_t splitk_cap = 0;        // doubles
+  double *wblk = nullptr, *pblk = nullptr;   // w and g-weighted w for a block of m
+  size_t wblk_cap = 0;          // doubles per buffer
+  double *S = nullptr, *H = nullptr, *U = nullptr;  // nb x nb
+  int nb_cap = 0, na_cap = 0;
+  void* base = nullptr;
+};
+
+void dev_copy(Exec& ex, const double* a, double* b, long long n);
+void check_finite(Exec& ex, const double* a, long long n);
+void fill_upper(Exec& ex, double* M, long long n);
+void stage_ri_mo_transform(Exec& ex, MolBuf& m);
+void stage_j_sigx(Exec& ex, MolBuf& m, Scratch& s);
+void stage_rpa_build(Exec& ex, MolBuf& m);
+void stage_rpa_eigensolve(Exec& ex, MolBuf& m, EigWork& w, Scratch& s, bool full_xpy);
+void stage_sigma(Exec& ex, MolBuf& m, Scratch& s, double eta);
+void derive_h_from_hf(Exec& ex, MolBuf& m);
+void h_ao_to_mo(Exec& ex, MolBuf& m, const double* hao, Scratch& s);
+void stage_qs_update(Exec& ex, MolBuf& m, EigWork& w, Scratch& s);
+void eigh_dense(Exec& ex, EigWork& w, int n, double* A, double* Z);
+
+}  // namespace molgw

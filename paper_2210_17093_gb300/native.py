@@ -1,0 +1,227 @@
+"""ctypes binding of the RI-qsGW C ABI (include/molgw_gb300.h).
+
+Argument marshalling only: every stage runs inside the CUDA library.  Arrays may
+be torch tensors (CUDA or CPU) or NumPy arrays; they must be float64 and
+C-contiguous.  The library must have been built (``paper_2210_17093_gb300.build``);
+loading fails loudly otherwise -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libmolgw_gb300.so")
+
+PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
+FLAG_FULL_XPY = 1
+FLAG_KTIMING = 2
+FLAG_GRAPH = 4
+
+ITEM = {"B": 0, "Omega": 1, "R": 2, "sigma_x": 3, "sigma_c": 4, "J": 5, "h_mo": 6, "eps": 7, "C": 8}
+KERNELS = ["gemm_f64", "tridiag_panel", "tridiag_syr2k", "bisect", "twisted", "backtransform",
+           "sigma", "gemm_tc", "misc"]
+
+STATUS = {0: "MOLGW_OK", -1: "MOLGW_E_ARG", -2: "MOLGW_E_STATE", -3: "MOLGW_E_NOMEM",
+          -4: "MOLGW_E_CUDA", -5: "MOLGW_E_NOCONV", -6: "MOLGW_E_TIMEOUT", -7: "MOLGW_E_NUMERIC"}
+
+# Every symbol include/molgw_gb300.h declares.
+EXPORTS = ["molgw_b200_create", "molgw_b200_set_ri", "molgw_b200_set_orbitals", "molgw_b200_rpa",
+           "molgw_b200_sigma", "molgw_b200_qs_step", "molgw_b200_sync", "molgw_b200_fetch",
+           "molgw_b200_rpa_matrix", "molgw_b200_eigh", "molgw_b200_kernel_stats",
+           "molgw_b200_launch_count", "molgw_b200_set_timing", "molgw_b200_destroy",
+           "molgw_b200_status_string"]
+
+
+class MolgwError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({status_string(code)})")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("max_mols", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("eta", ctypes.c_double), ("stream", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the shared library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing "
+                           "(run python -m paper_2210_17093_gb300.build)")
+    lib = ctypes.CDLL(path)
+    vp, ip, dp, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
+    sig = {
+        "molgw_b200_create": ([ctypes.POINTER(Opts), ctypes.POINTER(vp)], ip),
+        "molgw_b200_set_ri": ([vp, ip, ip, ip, dp], ip),
+        "molgw_b200_set_orbitals": ([vp, ip, ip, dp, dp, dp], ip),
+        "molgw_b200_rpa": ([vp, ip, dp, dp], ip),
+        "molgw_b200_sigma": ([vp, ip, dp, dp], ip),
+        "molgw_b200_qs_step": ([vp, ip, dp, dp], ip),
+        "molgw_b200_sync": ([vp], ip),
+        "molgw_b200_fetch": ([vp, ip, ip, dp, sz], ip),
+        "molgw_b200_rpa_matrix": ([vp, ip, dp], ip),
+        "molgw_b200_eigh": ([vp, ip, dp, dp, dp], ip),
+        "molgw_b200_kernel_stats": ([vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double), ip], ip),
+        "molgw_b200_launch_count": ([vp], ctypes.c_int64),
+        "molgw_b200_set_timing": ([vp, ctypes.c_uint32], ip),
+        "molgw_b200_destroy": ([vp], ip),
+        "molgw_b200_status_string": ([ip], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    try:
+        return load().molgw_b200_status_string(code).decode()
+    except Exception:  # noqa: BLE001 - only used to decorate an error message
+        return "?"
+
+
+def _ptr(a, n: int | None = None):
+    """Raw data pointer of a float64 C-contiguous torch tensor or NumPy array (or None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("arrays must be float64 and C-contiguous")
+        if n is not None and a.size != n:
+            raise ValueError(f"array has {a.size} elements, expected {n}")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be float64 and contiguous")
+        if n is not None and a.numel() != n:
+            raise ValueError(f"tensor has {a.numel()} elements, expected {n}")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise MolgwError(code, what)
+
+
+class Context:
+    """One library context (include/molgw_gb300.h, molgw_b200_create)."""
+
+    def __init__(self, precision: str = "fp64", max_mols: int = 1, device: int = 0,
+                 eta: float = 1e-3, stream=None, flags: int = 0):
+        self._lib = load()
+        o = Opts()
+        o.struct_size = ctypes.sizeof(Opts)
+        o.precision = PREC[precision]
+        o.max_mols = max_mols
+        o.device = device
+        o.eta = eta
+        if stream is not None and not isinstance(stream, int):
+            stream = stream.cuda_stream
+        o.stream = stream
+        o.flags = flags
+        h = ctypes.c_void_p()
+        _check(self._lib.molgw_b200_create(ctypes.byref(o), ctypes.byref(h)), "molgw_b200_create")
+        self._h = h
+        self.sizes = {}
+
+    def _hh(self):
+        if self._h is None:
+            raise RuntimeError("context is closed")
+        return self._h
+
+    def set_ri(self, mol: int, n_basis: int, n_aux: int, L):
+        _check(self._lib.molgw_b200_set_ri(self._hh(), mol, n_basis, n_aux,
+                                           _ptr(L, n_aux * n_basis * n_basis)), "set_ri")
+        self.sizes[mol] = [n_basis, n_aux, None]
+
+    def set_orbitals(self, mol: int, n_occ: int, eps, C, h_core=None):
+        nb = self.sizes[mol][0] if mol in self.sizes else None
+        nn = None if nb is None else nb * nb
+        _check(self._lib.molgw_b200_set_orbitals(self._hh(), mol, n_occ, _ptr(eps, nb), _ptr(C, nn),
+                                                 _ptr(h_core, nn)), "set_orbitals")
+        self.sizes[mol][2] = n_occ
+
+    def n_ov(self, mol: int):
+        nb, _, no = self.sizes.get(mol, (None, None, None))
+        return None if no is None else no * (nb - no)
+
+    def rpa(self, mol: int, omega=None, xpy=None):
+        n = self.n_ov(mol) if mol >= 0 else None
+        _check(self._lib.molgw_b200_rpa(self._hh(), mol, _ptr(omega, n), _ptr(xpy, None if n is None else n * n)),
+               "rpa")
+
+    def sigma(self, mol: int, sigma_x=None, sigma_c=None):
+        nn = self.sizes[mol][0] ** 2 if mol in self.sizes else None
+        _check(self._lib.molgw_b200_sigma(self._hh(), mol, _ptr(sigma_x, nn), _ptr(sigma_c, nn)), "sigma")
+
+    def qs_step(self, mol: int, eps_out=None, C_out=None):
+        nb = self.sizes[mol][0] if mol in self.sizes else None
+        _check(self._lib.molgw_b200_qs_step(self._hh(), mol, _ptr(eps_out, nb),
+                                            _ptr(C_out, None if nb is None else nb * nb)), "qs_step")
+
+    def sync(self):
+        _check(self._lib.molgw_b200_sync(self._hh()), "sync")
+
+    def fetch(self, mol: int, item: str, out):
+        n = out.size if isinstance(out, np.ndarray) else out.numel()
+        _check(self._lib.molgw_b200_fetch(self._hh(), mol, ITEM[item], _ptr(out), n), f"fetch {item}")
+
+    def rpa_matrix(self, mol: int, out):
+        n = self.n_ov(mol)
+        _check(self._lib.molgw_b200_rpa_matrix(self._hh(), mol, _ptr(out, None if n is None else n * n)),
+               "rpa_matrix")
+
+    def eigh(self, A, w, Z=None):
+        n = w.size if isinstance(w, np.ndarray) else w.numel()
+        _check(self._lib.molgw_b200_eigh(self._hh(), n, _ptr(A, n * n), _ptr(w, n), _ptr(Z, None if Z is None else n * n)),
+               "eigh")
+
+    def kernel_stats(self, reset: bool = False) -> dict:
+        k = len(KERNELS)
+        launches = (ctypes.c_int64 * k)()
+        ms = (ctypes.c_double * k)()
+        _check(self._lib.molgw_b200_kernel_stats(self._hh(), launches, ms, int(reset)), "kernel_stats")
+        return {name: (int(launches[i]), float(ms[i])) for i, name in enumerate(KERNELS)}
+
+    def set_timing(self, classes):
+        """Time the named kernel classes (see KERNELS) with CUDA events; [] turns timing off."""
+        mask = 0
+        for name in classes:
+            mask |= 1 << KERNELS.index(name)
+        _check(self._lib.molgw_b200_set_timing(self._hh(), mask), "set_timing")
+
+    def launch_count(self) -> int:
+        return int(self._lib.molgw_b200_launch_count(self._hh()))
+
+    def close(self):
+        if self._h is not None:
+            h, self._h = self._h, None
+            _check(self._lib.molgw_b200_destroy(h), "destroy")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None) is not None:
+                self._lib.molgw_b200_destroy(self._h)
+                self._h = None
+        except Exception:  # noqa: BLE001
+            pass

@@ -1,0 +1,273 @@
+"""Parity of the float64 CUDA path with the CPU oracle, through the C ABI.
+
+Tolerances (float64 path): Omega_s and quasiparticle energies within 1e-8 Ha;
+Sigma entries max|dSigma| / max|Sigma_oracle| within 1e-6 (the expected error of
+a float64 path is ~1e-11; the bounds are the stated targets).
+"""
+import numpy as np
+import pytest
+
+import synthetic as sy
+from helpers import lib_context, load_mol, rel_max, to_dev
+from oracle import qsgw
+
+pytestmark = pytest.mark.gpu
+
+ETA = sy.ETA
+TOL_OMEGA = 1e-8
+TOL_EPS = 1e-8
+TOL_SIGMA = 1e-6
+
+
+def oracle(m, eta=ETA):
+    return qsgw.qsgw_pass(m["L"], m["eps"], m["C"], m["n_occ"], eta)
+
+
+# ---------------------------------------------------------------------------
+# the symmetric eigensolver on its own
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 64, 65, 127, 130, 257, 600])
+def test_eigh_random(n):
+    import torch
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n))
+    A = A + A.T
+    with lib_context() as ctx:
+        w = torch.empty(n, dtype=torch.float64, device="cuda")
+        Z = torch.empty(n * n, dtype=torch.float64, device="cuda")
+        ctx.eigh(to_dev(A), w, Z)
+        w, Z = w.cpu().numpy(), Z.cpu().numpy().reshape(n, n)
+    ref = np.linalg.eigvalsh(A)
+    scale = max(1.0, np.abs(ref).max())
+    assert np.max(np.abs(w - ref)) <= 1e-12 * scale * max(1, n) ** 0.5
+    assert np.max(np.abs(A @ Z - Z * w[None, :])) <= 1e-11 * scale
+    assert np.max(np.abs(Z.T @ Z - np.eye(n))) <= 1e-10
+
+
+def test_eigh_host_pointers_and_graded_spectrum():
+    """Host arrays in and out; eigenvalues spread over 8 decades (Casida-like)."""
+    n = 300
+    rng = np.random.default_rng(7)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.sort(10.0 ** rng.uniform(-2, 6, n))
+    A = (Q * lam[None, :]) @ Q.T
+    A = 0.5 * (A + A.T)
+    with lib_context() as ctx:
+        w = np.empty(n)
+        Z = np.empty((n, n))
+        ctx.eigh(np.ascontiguousarray(A), w, Z)
+    np.testing.assert_allclose(w, lam, rtol=0, atol=1e-15 * 1e6 * n)
+    assert np.max(np.abs(A @ Z - Z * w[None, :])) <= 1e-9 * 1e6
+
+
+# ---------------------------------------------------------------------------
+# stage by stage at the small workload (nb=24, no=5, na=72)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def small():
+    m = sy.molecule(24, 5, 72, 0)
+    return m, oracle(m)
+
+
+def test_small_stages(small):
+    import torch
+    m, r = small
+    nb, na, no = 24, 72, 5
+    nov = no * (nb - no)
+    with lib_context(flags=1) as ctx:    # FULL_XPY
+        load_mol(ctx, 0, m)
+        M = torch.empty(nov * nov, dtype=torch.float64, device="cuda")
+        ctx.rpa_matrix(0, M)
+        np.testing.assert_allclose(M.cpu().numpy().reshape(nov, nov), r["M"], rtol=1e-13, atol=1e-12)
+        B = torch.empty(na * nb * nb, dtype=torch.float64, device="cuda")
+        ctx.fetch(0, "B", B)
+        np.testing.assert_allclose(B.cpu().numpy().reshape(na, nb, nb), r["B"], atol=1e-14)
+        om = torch.empty(nov, dtype=torch.float64, device="cuda")
+        xpy = torch.empty(nov * nov, dtype=torch.float64, device="cuda")
+        ctx.rpa(0, om, xpy)
+        np.testing.assert_allclose(om.cpu().numpy(), r["Omega"], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(xpy.cpu().numpy().reshape(nov, nov), r["XpY"], atol=1e-10)
+        R = np.empty(na * nov)
+        ctx.fetch(0, "R", R)
+        R = R.reshape(na, nov)
+        # the sign of each column of R is an eigenvector gauge
+        sg = np.sign(np.sum(R * r["R"], axis=0))
+        np.testing.assert_allclose(R * sg[None, :], r["R"], atol=1e-11)
+        sx = np.empty((nb, nb))
+        sc = np.empty((nb, nb))
+        ctx.sigma(0, sx, sc)
+        assert rel_max(sx, r["sigma_x"]) < 1e-13
+        assert rel_max(sc, r["sigma_c"]) < 1e-10
+        J = np.empty((nb, nb))
+        ctx.fetch(0, "J", J)
+        np.testing.assert_allclose(J, r["J"], atol=1e-13)
+        h = np.empty((nb, nb))
+        ctx.fetch(0, "h_mo", h)
+        np.testing.assert_allclose(h, r["h_mo"], atol=1e-12)
+        eps = np.empty(nb)
+        C = np.empty((nb, nb))
+        ctx.qs_step(0, eps, C)
+        np.testing.assert_allclose(eps, r["eps_new"], atol=1e-11)
+        # orbitals up to the sign gauge: compare |C^T C_oracle| = I
+        np.testing.assert_allclose(np.abs(np.sum(C * r["C_new"], axis=0)), 1.0, atol=1e-10)
+
+
+def test_small_golden_file(small):
+    """The GPU reproduces the stored oracle values of tests/golden."""
+    import json
+    import os
+    doc = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "qsgw_nb24_no5_na72_seed0.json")))
+    m, _ = small
+    with lib_context() as ctx:
+        load_mol(ctx, 0, m, device=False)
+        om = np.empty(95)
+        ctx.rpa(0, om)
+        eps = np.empty(24)
+        ctx.qs_step(0, eps)
+    np.testing.assert_allclose(om, doc["Omega"], atol=TOL_OMEGA)
+    np.testing.assert_allclose(eps, doc["eps_new"], atol=TOL_EPS)
+
+
+# ---------------------------------------------------------------------------
+# mid size (several 64-tiles, ragged tails) and iterations
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("nb,no,na,seed", [(100, 20, 300, 1), (71, 13, 150, 2), (40, 39, 17, 3), (33, 1, 9, 4)])
+def test_mid_pass(nb, no, na, seed):
+    m = sy.molecule(nb, no, na, seed)
+    r = oracle(m)
+    nov = no * (nb - no)
+    with lib_context() as ctx:
+        load_mol(ctx, 0, m)
+        om = np.empty(nov)
+        ctx.rpa(0, om)
+        sx = np.empty((nb, nb))
+        sc = np.empty((nb, nb))
+        ctx.sigma(0, sx, sc)
+        eps = np.empty(nb)
+        ctx.qs_step(0, eps)
+    assert np.max(np.abs(om - r["Omega"])) < TOL_OMEGA
+    assert rel_max(sx, r["sigma_x"]) < TOL_SIGMA
+    assert rel_max(sc, r["sigma_c"]) < TOL_SIGMA
+    assert np.max(np.abs(eps - r["eps_new"])) < TOL_EPS
+
+
+def test_three_iterations():
+    m = sy.molecule(80, 16, 240, 5)
+    its = qsgw.qsgw_iterations(m["L"], m["eps"], m["C"], 16, ETA, 3)
+    with lib_context() as ctx:
+        load_mol(ctx, 0, m)
+        for k in range(3):
+            sc = np.empty((80, 80))
+            ctx.sigma(0, None, sc)
+            C_cur = np.empty((80, 80))
+            ctx.fetch(0, "C", C_cur)
+            eps = np.empty(80)
+            ctx.qs_step(0, eps)
+            r = its[k]
+            assert np.max(np.abs(eps - r["eps_new"])) < TOL_EPS, k
+            # Sigma_c in the AO basis is gauge invariant: C Sigma C^T
+            ao_gpu = C_cur @ sc @ C_cur.T
+            C_or = m["C"] if k == 0 else its[k - 1]["C_new"]
+            ao_or = C_or @ r["sigma_c"] @ C_or.T
+            assert rel_max(ao_gpu, ao_or) < TOL_SIGMA, k
+
+
+def test_h_core_given_equals_derived():
+    """Passing h_AO = C h_MO C^T explicitly gives the same step as deriving it."""
+    m = sy.molecule(30, 6, 60, 8)
+    r = oracle(m)
+    h_ao = m["C"] @ r["h_mo"] @ m["C"].T
+    with lib_context() as ctx:
+        load_mol(ctx, 0, m, h_core=h_ao)
+        eps = np.empty(30)
+        ctx.qs_step(0, eps)
+    np.testing.assert_allclose(eps, r["eps_new"], atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# full size of the bench workload (nb=200, no=40, na=600): whole-output parity
+# ---------------------------------------------------------------------------
+def test_bench_size_parity():
+    m = sy.molecule(200, 40, 600, 1)
+    r = oracle(m)
+    with lib_context() as ctx:
+        load_mol(ctx, 0, m)
+        om = np.empty(6400)
+        ctx.rpa(0, om)
+        sx = np.empty((200, 200))
+        sc = np.empty((200, 200))
+        ctx.sigma(0, sx, sc)
+        eps = np.empty(200)
+        ctx.qs_step(0, eps)
+    assert np.max(np.abs(om - r["Omega"])) < TOL_OMEGA
+    assert rel_max(sx, r["sigma_x"]) < TOL_SIGMA
+    assert rel_max(sc, r["sigma_c"]) < TOL_SIGMA
+    assert np.max(np.abs(eps - r["eps_new"])) < TOL_EPS
+
+
+# ---------------------------------------------------------------------------
+# batch, determinism, boundary behaviour
+# ---------------------------------------------------------------------------
+def test_batch_equals_solo_bitwise():
+    mols = [sy.batch_molecule(s) for s in (100, 101, 102)]
+    with lib_context(max_mols=3) as ctx:
+        for k, m in enumerate(mols):
+            load_mol(ctx, k, m)
+        ctx.qs_step(-1)
+        ctx.sync()
+        batch = []
+        for k, m in enumerate(mols):
+            e = np.empty(m["n_basis"])
+            ctx.fetch(k, "eps", e)
+            batch.append(e)
+    for k, m in enumerate(mols):
+        with lib_context() as ctx:
+            load_mol(ctx, 0, m)
+            e = np.empty(m["n_basis"])
+            ctx.qs_step(0, e)
+        assert np.array_equal(e, batch[k]), k
+
+
+def test_repeat_runs_are_bitwise_identical():
+    m = sy.molecule(64, 12, 100, 9)
+    out = []
+    for _ in range(2):
+        with lib_context() as ctx:
+            load_mol(ctx, 0, m)
+            sc = np.empty((64, 64))
+            ctx.sigma(0, None, sc)
+            out.append(sc)
+    assert np.array_equal(out[0], out[1])
+
+
+def test_errors_and_call_order():
+    from paper_2210_17093_gb300 import MolgwError
+    m = sy.molecule(10, 3, 8, 10)
+    with lib_context(max_mols=2) as ctx:
+        with pytest.raises(MolgwError) as e:
+            ctx.rpa(0, np.empty(21))
+        assert e.value.code == -2                          # before set_ri/set_orbitals
+        with pytest.raises(MolgwError) as e:
+            ctx.set_ri(5, 10, 8, m["L"])
+        assert e.value.code == -1                          # molecule index
+        ctx.set_ri(0, 10, 8, m["L"])
+        with pytest.raises(MolgwError) as e:
+            ctx.set_orbitals(0, 10, m["eps"], m["C"])       # n_occ >= n_basis
+        assert e.value.code == -1
+        with pytest.raises(MolgwError) as e:
+            ctx.sigma(0)
+        assert e.value.code == -2
+        ctx.set_orbitals(0, 3, m["eps"], m["C"])
+        with pytest.raises(MolgwError) as e:
+            ctx.rpa(0, None, np.empty(21 * 21))            # xpy without FULL_XPY
+        assert e.value.code == -1
+        bad = m["L"].copy()
+        bad[0, 0, 0] = np.nan
+        ctx.set_ri(1, 10, 8, bad)
+        with pytest.raises(MolgwError) as e:
+            ctx.sync()
+        assert e.value.code == -7                          # non-finite input latched
+        ctx.sync()                                         # cleared after reporting
+        om = np.empty(21)
+        ctx.rpa(0, om)                                     # the context stays usable
+        assert np.all(om > 0)
