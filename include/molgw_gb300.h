@@ -68,7 +68,8 @@ enum molgw_precision {
 enum molgw_flags {
   MOLGW_FLAG_FULL_XPY = 1u << 0, /* keep the full n_ov x n_ov (X+Y) so molgw_b200_rpa can return it */
   MOLGW_FLAG_KTIMING = 1u << 1,  /* record CUDA events around kernels for molgw_b200_kernel_stats  */
-  MOLGW_FLAG_GRAPH = 1u << 2     /* replay each molecule's qs_step from a captured CUDA graph        */
+  MOLGW_FLAG_GRAPH = 1u << 2,    /* replay each molecule's qs_step from a captured CUDA graph        */
+  MOLGW_FLAG_USE_STREAM = 1u << 3 /* run on opts.stream even when it is NULL (the legacy default stream) */
 };
 
 typedef struct {
@@ -77,7 +78,8 @@ typedef struct {
   int32_t max_mols;    /* molecules the context holds, indices 0 .. max_mols-1 (>=1) */
   int32_t device;      /* CUDA device ordinal                                       */
   double eta;          /* broadening eta > 0 of Eq. (Sigma.c.GW), Hartree           */
-  void* stream;        /* cudaStream_t to run on; NULL = a stream the context owns  */
+  void* stream;        /* cudaStream_t to run on; NULL = a stream the context owns,
+                          unless MOLGW_FLAG_USE_STREAM asks for the legacy default stream */
   uint32_t flags;      /* enum molgw_flags                                          */
 } molgw_opts;
 

@@ -192,7 +192,7 @@ int molgw_b200_create(const molgw_opts* o, molgw_ctx* out) {
   c->opts = *o;
   c->device = o->device;
   DeviceGuard g(c->device);
-  if (o->stream) {
+  if (o->stream || (o->flags & MOLGW_FLAG_USE_STREAM)) {
     c->st = (cudaStream_t)o->stream;
   } else {
     if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) { delete c; return MOLGW_E_CUDA; }

@@ -19,6 +19,7 @@ PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
 FLAG_FULL_XPY = 1
 FLAG_KTIMING = 2
 FLAG_GRAPH = 4
+FLAG_USE_STREAM = 8
 
 ITEM = {"B": 0, "Omega": 1, "R": 2, "sigma_x": 3, "sigma_c": 4, "J": 5, "h_mo": 6, "eps": 7, "C": 8}
 KERNELS = ["gemm_f64", "tridiag_panel", "tridiag_syr2k", "bisect", "twisted", "backtransform",
@@ -129,8 +130,11 @@ class Context:
         o.max_mols = max_mols
         o.device = device
         o.eta = eta
-        if stream is not None and not isinstance(stream, int):
-            stream = stream.cuda_stream
+        if stream is not None:
+            # an explicit stream (a torch stream or a raw handle) is always used, even
+            # the legacy default stream whose handle is 0
+            stream = stream if isinstance(stream, int) else stream.cuda_stream
+            flags |= FLAG_USE_STREAM
         o.stream = stream
         o.flags = flags
         h = ctypes.c_void_p()

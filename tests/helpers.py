@@ -8,6 +8,9 @@ def lib_context(**kw):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2210_17093_gb300 import Context
+    # run on torch's current stream so that device outputs are ordered before
+    # any later torch read of them
+    kw.setdefault("stream", torch.cuda.current_stream())
     return Context(**kw)
 
 

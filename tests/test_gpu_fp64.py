@@ -152,24 +152,36 @@ def test_mid_pass(nb, no, na, seed):
 
 
 def test_three_iterations():
+    """Each qsGW step of the GPU equals one oracle step taken from the GPU's own state.
+
+    Trajectories are not compared: with eta = 1e-3 Ha some denominators
+    eps_p - eps_m -/+ Omega_s come within ~1e-6 Ha of a pole, where
+    g(x) = x / (x^2 + eta^2) amplifies an input change by up to 1/eta^2 = 1e6, so
+    rounding-level differences after one step grow to ~1e-6 Ha after the next and
+    to ~1e-2 Ha after three (the synthetic inputs are far from perturbative).
+    """
     m = sy.molecule(80, 16, 240, 5)
     its = qsgw.qsgw_iterations(m["L"], m["eps"], m["C"], 16, ETA, 3)
     with lib_context() as ctx:
         load_mol(ctx, 0, m)
         for k in range(3):
+            eps_in = np.empty(80)
+            C_in = np.empty((80, 80))
+            ctx.fetch(0, "eps", eps_in)
+            ctx.fetch(0, "C", C_in)
+            h_in = None
+            if k > 0:
+                h_in = np.empty((80, 80))
+                ctx.fetch(0, "h_mo", h_in)
             sc = np.empty((80, 80))
             ctx.sigma(0, None, sc)
-            C_cur = np.empty((80, 80))
-            ctx.fetch(0, "C", C_cur)
             eps = np.empty(80)
             ctx.qs_step(0, eps)
-            r = its[k]
+            r = qsgw.qsgw_pass(m["L"], eps_in, C_in, 16, ETA, h_in)
             assert np.max(np.abs(eps - r["eps_new"])) < TOL_EPS, k
-            # Sigma_c in the AO basis is gauge invariant: C Sigma C^T
-            ao_gpu = C_cur @ sc @ C_cur.T
-            C_or = m["C"] if k == 0 else its[k - 1]["C_new"]
-            ao_or = C_or @ r["sigma_c"] @ C_or.T
-            assert rel_max(ao_gpu, ao_or) < TOL_SIGMA, k
+            assert rel_max(sc, r["sigma_c"]) < TOL_SIGMA, k
+        # the first step starts from the same input on both sides
+        assert np.max(np.abs(its[0]["eps_new"] - qsgw.qsgw_pass(m["L"], m["eps"], m["C"], 16, ETA)["eps_new"])) == 0
 
 
 def test_h_core_given_equals_derived():
