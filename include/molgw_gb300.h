@@ -152,6 +152,27 @@ int molgw_b200_rpa_matrix(molgw_ctx ctx, int mol, double* M);
  * the blocked back-transformation, all on the device. */
 int molgw_b200_eigh(molgw_ctx ctx, int n, const double* A, double* w, double* Z);
 
+/* Largest n accepted by molgw_b200_eigh_noalloc. */
+#define MOLGW_NOALLOC_NMAX 256
+
+/* Allocation-free variant of molgw_b200_eigh, for callers that cannot allocate
+ * device memory when they need the decomposition (an application whose own pool
+ * allocator owns all device memory, a latency-bound loop that cannot pay for
+ * cudaMalloc or the device-wide synchronisation of cudaFree, a plug-in running
+ * after the host program has claimed its memory).  The paper has no counterpart:
+ * it is a service of this library.
+ *   n <= MOLGW_NOALLOC_NMAX; A[n][n] symmetric, w[n], Z[n][n] (may be NULL) are
+ *   DEVICE pointers on the current device (else MOLGW_E_ARG); results as for
+ *   molgw_b200_eigh.  stream: the cudaStream_t to run on (NULL = legacy default).
+ *   All workspace is one fixed device array of 4.93 MB inside the library, held
+ *   by every GPU that loads it until the process exits; no call allocates or
+ *   frees.  The first call on a device looks up that array's address (once per
+ *   device, with the device current), so make it before any stream capture.
+ *   The call synchronises `stream` and returns the device status.
+ *   Every call shares the one array: calls that overlap on the GPU (other
+ *   streams, other host threads) race and must be serialised by the caller. */
+int molgw_b200_eigh_noalloc(int n, const double* A, double* w, double* Z, void* stream);
+
 /* Kernel timing collected while MOLGW_FLAG_KTIMING is set: for kernel class k
  * (enum molgw_kernel) the number of launches and their summed event time in ms
  * since the last reset.  names may be NULL.  Synchronises.  reset != 0 clears. */

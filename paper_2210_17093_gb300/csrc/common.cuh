@@ -118,8 +118,22 @@ struct EigWork {
   size_t gk_cap = 0;
   double *tmp1 = nullptr, *tmp2 = nullptr;  // 64 x ncols_max each
   int ncols_max = 0;
+  bool owned = false;          // allocated by eig_work_alloc (freed by eig_work_free)
 };
-size_t eig_work_bytes(int nmax, int ncols_max);
+// Workspace sizes in doubles for matrices up to n and back-transformations of
+// up to ncols (>= 64) columns at a time.
+constexpr size_t eig_part_doubles(size_t n) {
+  return 2 * ((n + 255) / 256 + 1) + ((n + 63) / 64) * 128 + 4 * n * 128 + (((n + 63) / 64 + 7) / 8) * n + 64;
+}
+constexpr size_t eig_gk_doubles(size_t n, size_t ncols) {
+  return (16 * 64 * ncols > 8 * (n / 64 + 1) * 64 * 64) ? 16 * 64 * ncols : 8 * (n / 64 + 1) * 64 * 64;
+}
+constexpr size_t eig_work_doubles(size_t n, size_t ncols) {
+  return 4 * n + n * 64 + eig_part_doubles(n) + 64 + n * n + 2 * (n / 64 + 1) * 64 * 64 + 2 * 64 * ncols +
+         eig_gk_doubles(n, ncols);
+}
+// Lay an EigWork out over caller-provided device memory of eig_work_doubles(n, ncols) doubles.
+void eig_work_carve(EigWork& w, double* base, int nmax, int ncols_max);
 int eig_work_alloc(EigWork& w, int nmax, int ncols_max);
 void eig_work_free(EigWork& w);
 

@@ -183,37 +183,14 @@ __global__ void k_wy_t(const double* Gall, const double* tau, int n, double* Tal
 
 }  // namespace
 
-size_t eig_work_bytes(int nmax, int ncols_max) {
+void eig_work_carve(EigWork& w, double* p, int nmax, int ncols_max) {
   const size_t n = (size_t)std::max(nmax, 2);
-  const size_t nrbt = (n + 63) / 64;
-  const size_t npan = n / 64 + 1;
-  size_t part = 2 * ((n + 255) / 256 + 1) + nrbt * 128 + 4 * n * 128 + ((nrbt + 7) / 8) * n + 64;
-  size_t b = 0;
-  b += 4 * n;                         // d, e, tau, lam
-  b += n * 64;                        // Wp
-  b += part;                          // partials
-  b += 64;                            // scal
-  b += n * n;                         // S2
-  b += npan * 64 * 64;                // Tm
-  b += 2 * (size_t)64 * std::max(ncols_max, 64);   // tmp1, tmp2
-  b += (size_t)16 * 64 * std::max(ncols_max, 64);  // gk (split-K work)
-  b += npan * 64 * 64;                // Gram matrices (in gk region when large enough)
-  return b * sizeof(double);
-}
-
-int eig_work_alloc(EigWork& w, int nmax, int ncols_max) {
-  eig_work_free(w);
-  const size_t n = (size_t)std::max(nmax, 2);
-  const size_t nrbt = (n + 63) / 64;
-  const size_t npan = n / 64 + 1;
+  w = EigWork{};
   w.nmax = (int)n;
   w.ncols_max = std::max(ncols_max, 64);
-  w.part_cap = 2 * ((n + 255) / 256 + 1) + nrbt * 128 + 4 * n * 128 + ((nrbt + 7) / 8) * n + 64;
-  w.gk_cap = std::max((size_t)16 * 64 * w.ncols_max, (size_t)8 * npan * 64 * 64);
-  double* p = nullptr;
-  const size_t total = 4 * n + n * 64 + w.part_cap + 64 + n * n + 2 * npan * 64 * 64 +
-                       2 * (size_t)64 * w.ncols_max + w.gk_cap;
-  if (cudaMalloc(&p, total * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return MOLGW_E_NOMEM; }
+  w.part_cap = eig_part_doubles(n);
+  w.gk_cap = eig_gk_doubles(n, (size_t)w.ncols_max);
+  const size_t npan = n / 64 + 1;
   w.d = p; p += n; w.e = p; p += n; w.tau = p; p += n; w.lam = p; p += n;
   w.Wp = p; p += n * 64;
   w.part = p; p += w.part_cap;
@@ -223,11 +200,20 @@ int eig_work_alloc(EigWork& w, int nmax, int ncols_max) {
   w.tmp1 = p; p += (size_t)64 * w.ncols_max;
   w.tmp2 = p; p += (size_t)64 * w.ncols_max;
   w.gk = p; p += w.gk_cap;
+}
+
+int eig_work_alloc(EigWork& w, int nmax, int ncols_max) {
+  eig_work_free(w);
+  double* p = nullptr;
+  const size_t total = eig_work_doubles((size_t)std::max(nmax, 2), (size_t)std::max(ncols_max, 64));
+  if (cudaMalloc(&p, total * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return MOLGW_E_NOMEM; }
+  eig_work_carve(w, p, nmax, ncols_max);
+  w.owned = true;
   return MOLGW_OK;
 }
 
 void eig_work_free(EigWork& w) {
-  if (w.d) cudaFree(w.d);
+  if (w.owned && w.d) cudaFree(w.d);
   w = EigWork{};
 }
 

@@ -33,7 +33,8 @@ EXPORTS = ["molgw_b200_create", "molgw_b200_set_ri", "molgw_b200_set_orbitals", 
            "molgw_b200_sigma", "molgw_b200_qs_step", "molgw_b200_sync", "molgw_b200_fetch",
            "molgw_b200_rpa_matrix", "molgw_b200_eigh", "molgw_b200_kernel_stats",
            "molgw_b200_launch_count", "molgw_b200_set_timing", "molgw_b200_destroy",
-           "molgw_b200_status_string"]
+           "molgw_b200_status_string", "molgw_b200_eigh_noalloc"]
+NOALLOC_NMAX = 256
 
 
 class MolgwError(RuntimeError):
@@ -77,6 +78,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "molgw_b200_set_timing": ([vp, ctypes.c_uint32], ip),
         "molgw_b200_destroy": ([vp], ip),
         "molgw_b200_status_string": ([ip], ctypes.c_char_p),
+        "molgw_b200_eigh_noalloc": ([ip, dp, dp, dp, vp], ip),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
