@@ -77,6 +77,7 @@ __device__ __forceinline__ void set_status(int* status, int code) {
 }
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+__host__ __device__ __forceinline__ int ceil_div_d(int a, int b) { return (a + b - 1) / b; }
 
 // ---------------------------------------------------------------------------
 // Generic strided float64 GEMM: C(i,j) = alpha * sum_k A(i,k) B(k,j) + beta C(i,j)
@@ -122,8 +123,9 @@ struct EigWork {
 };
 // Workspace sizes in doubles for matrices up to n and back-transformations of
 // up to ncols (>= 64) columns at a time.
+constexpr int kMaxPanelGrid = 320;   // CTAs of the tridiagonalisation panel kernel, at most
 constexpr size_t eig_part_doubles(size_t n) {
-  return 2 * ((n + 255) / 256 + 1) + ((n + 63) / 64) * 128 + 4 * n * 128 + (((n + 63) / 64 + 7) / 8) * n + 64;
+  return 2 * ((n + 63) / 64 + 1) + ((n + 63) / 64) * 128 + 2 * n * 128 + 8 + (size_t)kMaxPanelGrid * n + 64;
 }
 constexpr size_t eig_gk_doubles(size_t n, size_t ncols) {
   return (16 * 64 * ncols > 8 * (n / 64 + 1) * 64 * 64) ? 16 * 64 * ncols : 8 * (n / 64 + 1) * 64 * 64;

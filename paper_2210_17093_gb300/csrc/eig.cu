@@ -53,45 +53,123 @@ __global__ void k_gersh(const double* d, const double* e, int n, double* out) {
   }
 }
 
+// 1/q by Newton-Raphson (r <- r (2 - q r), quadratic convergence) from the
+// float32 reciprocal as seed: two steps take the ~24-bit seed past float64
+// precision.  Outside the float32 range the plain division is used.
+__device__ __forceinline__ double recip_nr(double q) {
+  const double aq = fabs(q);
+  if (aq > 1e-30 && aq < 1e30) {
+    double r = (double)__frcp_rn((float)q);
+    r = r * fma(-q, r, 2.0);
+    r = r * fma(-q, r, 2.0);
+    return r;
+  }
+  return 1.0 / q;
+}
+
+// Number of eigenvalues of T below x (float64 LDL^T pivots).
 __device__ __forceinline__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2,
                                            int n, double x, double pivmin) {
   double q = d[0] - x;
   if (fabs(q) < pivmin) q = -pivmin;
   int cnt = (q < 0.0);
   for (int j = 1; j < n; ++j) {
-    q = d[j] - x - e2[j - 1] / q;
+    q = (d[j] - x) - e2[j - 1] * recip_nr(q);
     if (fabs(q) < pivmin) q = -pivmin;
     cnt += (q < 0.0);
   }
   return cnt;
 }
 
-__global__ void k_e2(const double* e, double* e2, int n) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n - 1) e2[k] = e[k] * e[k];
+__device__ __forceinline__ int sturm_count_f32(const float* __restrict__ d, const float* __restrict__ e2,
+                                               int n, float x, float pivmin) {
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  int cnt = (q < 0.0f);
+  for (int j = 1; j < n; ++j) {
+    q = d[j] - x - e2[j - 1] / q;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += (q < 0.0f);
+  }
+  return cnt;
 }
 
-__global__ void __launch_bounds__(128) k_bisect(const double* d, const double* e2, const double* g,
-                                                int n, double* lam, int* status) {
+// e2 = e^2 in float64, and float32 copies of d and e^2 for the coarse phase.
+__global__ void k_e2(const double* d, const double* e, double* e2, float* d32, float* e232, int n) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  double lo = g[0], hi = g[1];
-  const double pivmin = g[2];
-  const double eps = 2.220446049250313e-16;
-  // relative tolerance, plus an absolute floor of a few ulps of ||T|| so that an
-  // eigenvalue at or near zero also converges
-  const double atol = 4.0 * eps * g[3] + 4.0 * pivmin;
-  bool ok = false;
-  for (int it = 0; it < 256; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + atol || mid <= lo || mid >= hi) {
-      ok = true;
-      break;
-    }
-    if (sturm_count(d, e2, n, mid, pivmin) > k) hi = mid; else lo = mid;
+  if (k < n - 1) {
+    e2[k] = e[k] * e[k];
+    e232[k] = (float)(e[k] * e[k]);
   }
-  if (!ok) set_status(status, MOLGW_E_NOCONV);
-  lam[k] = 0.5 * (lo + hi);
+  if (k < n) d32[k] = (float)d[k];
+}
+
+// One step of 4-point multisection shared by the 4 lanes of a group: lane l
+// evaluates the count at lo + (l+1)(hi-lo)/5; the group keeps the fifth of the
+// interval where the count passes k.
+template <typename T>
+__device__ __forceinline__ void multisect(T& lo, T& hi, int cnt_l, T x_l, int k, int l, unsigned mask) {
+  T new_lo = lo, new_hi = hi;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int c = __shfl_sync(mask, cnt_l, m, 4);
+    const T x = __shfl_sync(mask, x_l, m, 4);
+    if (c <= k) { if (x > new_lo) new_lo = x; }   // eigenvalue k lies above x
+    else if (x < new_hi) new_hi = x;              // first point with count > k
+  }
+  (void)l;
+  lo = new_lo;
+  hi = new_hi;
+}
+
+// Eigenvalue k of T, 4 threads per eigenvalue.  A float32 phase (on the 62x
+// faster FP32 pipe) narrows [lo, hi] to a few float32 ulps of ||T||; the bracket
+// is widened by a safety margin and accepted only if float64 Sturm counts
+// confirm that it still encloses eigenvalue k (else the Gershgorin interval is
+// used).  The float64 phase then multisects to 2 eps |lambda| + 4 eps ||T||.
+__global__ void __launch_bounds__(128) k_bisect(const double* d, const double* e2, const float* d32,
+                                                const float* e232, const double* g, int n, double* lam,
+                                                int* status) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = gt >> 2, l = gt & 3;
+  const int lane = threadIdx.x & 31;
+  const unsigned mask = 0xFu << (lane & ~3);
+  if (k >= n) return;                      // whole groups leave together (n*4 threads are grouped)
+  const double glo = g[0], ghi = g[1];
+  const double pivmin = g[2], nrm = g[3];
+  const double eps = 2.220446049250313e-16;
+  const double atol = 4.0 * eps * nrm + 4.0 * pivmin;
+  // float32 phase
+  const float nrm32 = (float)nrm;
+  const float pivmin32 = fmaxf(1e-30f * fmaxf(nrm32 * nrm32, 1.0f), 1e-36f);
+  const float tol32 = 16.0f * 5.9604645e-8f * fmaxf(nrm32, 1e-30f);
+  float lo32 = (float)glo, hi32 = (float)ghi;
+  const bool use32 = nrm > 1e-15 && nrm < 1e15;   // float32 range for d, e^2 and the pivots
+  for (int it = 0; use32 && it < 40 && hi32 - lo32 > tol32; ++it) {
+    const float x = lo32 + (float)(l + 1) * (hi32 - lo32) * 0.2f;
+    const int c = (x > lo32 && x < hi32) ? sturm_count_f32(d32, e232, n, x, pivmin32) : ((x <= lo32) ? 0 : n);
+    multisect<float>(lo32, hi32, c, x, k, l, mask);
+  }
+  const double margin = 64.0 * 5.9604645e-8 * nrm + atol;
+  double lo = fmax(glo, (double)lo32 - margin), hi = fmin(ghi, (double)hi32 + margin);
+  int cl = 0;
+  if (lo < hi && l < 2) cl = sturm_count(d, e2, n, l == 0 ? lo : hi, pivmin);
+  const int c_lo = __shfl_sync(mask, cl, 0, 4), c_hi = __shfl_sync(mask, cl, 1, 4);
+  if (!(lo < hi) || c_lo > k || c_hi <= k) {
+    lo = glo;
+    hi = ghi;
+  }
+  bool ok = false;
+  for (int it = 0; it < 128; ++it) {
+    if (hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + atol) { ok = true; break; }
+    const double x = lo + (double)(l + 1) * (hi - lo) * 0.2;
+    const int c = (x > lo && x < hi) ? sturm_count(d, e2, n, x, pivmin) : ((x <= lo) ? 0 : n);
+    const double plo = lo, phi = hi;
+    multisect<double>(lo, hi, c, x, k, l, mask);
+    if (lo == plo && hi == phi) { ok = true; break; }   // no representable progress
+  }
+  if (!ok && l == 0) set_status(status, MOLGW_E_NOCONV);
+  if (l == 0) lam[k] = 0.5 * (lo + hi);
 }
 
 // Twisted factorisation eigenvector of T - lambda_s I; S1/S2 are strided scratch
@@ -219,11 +297,13 @@ void eig_work_free(EigWork& w) {
 
 void tridiag_eigvals(Exec& ex, EigWork& w, int n) {
   double* g = w.scal + 8;       // lo, hi, pivmin, norm
-  double* e2 = w.part;          // n-1 squares (partials are free after the reduction)
+  double* e2 = w.part;          // n-1 squares (the partial-sum area is free after the reduction)
+  float* d32 = reinterpret_cast<float*>(w.part + n);
+  float* e232 = d32 + n;
   KScope ks(ex, MOLGW_K_BISECT, 3);
   k_gersh<<<1, 256, 0, ex.st>>>(w.d, w.e, n, g);
-  k_e2<<<ceil_div(n, 256), 256, 0, ex.st>>>(w.e, e2, n);
-  k_bisect<<<ceil_div(n, 128), 128, 0, ex.st>>>(w.d, e2, g, n, w.lam, ex.status);
+  k_e2<<<ceil_div(n, 256), 256, 0, ex.st>>>(w.d, w.e, e2, d32, e232, n);
+  k_bisect<<<ceil_div(4LL * n, 128), 128, 0, ex.st>>>(w.d, e2, d32, e232, g, n, w.lam, ex.status);
 }
 
 void tridiag_eigvecs(Exec& ex, EigWork& w, int n, double* ZT, long long ldz) {

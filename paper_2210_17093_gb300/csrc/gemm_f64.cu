@@ -12,7 +12,8 @@ namespace molgw {
 
 namespace {
 
-constexpr int TM = 64, TN = 64, TK = 16, NT = 256;
+constexpr int TK = 16;
+constexpr int TM = 64, TN = 64;   // tile of the lower_only bookkeeping (64x64 tiles)
 
 struct GemmParams {
   int M, N, K, batch, ksplit, kchunk;
@@ -24,20 +25,24 @@ struct GemmParams {
   double* work;
 };
 
-__global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmParams p) {
+// BM x BN output tile per CTA, (BM/4) x (BN/4) threads, 4x4 outputs per thread
+// (rows ty + (BM/4) i, columns tx + (BN/4) j).
+template <int BM, int BN>
+__global__ void __launch_bounds__((BM / 4) * (BN / 4)) gemm_f64_kernel(GemmParams p) {
+  constexpr int TX = BN / 4, TY = BM / 4, NTH = TX * TY;
   const int bn = blockIdx.x, bm = blockIdx.y;
-  if (p.lower_only && bm < bn) return;
+  if (p.lower_only && bm < bn) return;   // lower_only is used with BM = BN = 64 only
   const int z = blockIdx.z;
   const int b = z % p.batch, kz = z / p.batch;
   const int k_begin = kz * p.kchunk;
   const int k_end = min(p.K, k_begin + p.kchunk);
 
-  __shared__ double As[TK][TM + 1];
-  __shared__ double Bs[TK][TN + 1];
+  __shared__ double As[TK][BM + 1];
+  __shared__ double Bs[TK][BN + 1];
 
   const int t = threadIdx.x;
-  const int tx = t % 16, ty = t / 16;
-  const int m0 = bm * TM, n0 = bn * TN;
+  const int tx = t % TX, ty = t / TX;
+  const int m0 = bm * BM, n0 = bn * BN;
   const double* A = p.A + (long long)b * p.sa_b;
   const double* B = p.B + (long long)b * p.sb_b;
   const bool a_kfast = (p.sa_k == 1);
@@ -50,19 +55,17 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmParams p) {
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 
   for (int k0 = k_begin; k0 < k_end; k0 += TK) {
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int e = t; e < BM * TK; e += NTH) {
       int m, k;
-      if (a_kfast) { k = t % TK; m = t / TK + 16 * r; }
-      else { m = t % TM; k = t / TM + 4 * r; }
+      if (a_kfast) { k = e % TK; m = e / TK; }
+      else { m = e % BM; k = e / BM; }
       const int gm = m0 + m, gk = k0 + k;
       As[k][m] = (gm < p.M && gk < k_end) ? A[(long long)gm * p.sa_m + (long long)gk * p.sa_k] : 0.0;
     }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int e = t; e < BN * TK; e += NTH) {
       int n, k;
-      if (b_nfast) { n = t % TN; k = t / TN + 4 * r; }
-      else { k = t % TK; n = t / TK + 16 * r; }
+      if (b_nfast) { n = e % BN; k = e / BN; }
+      else { k = e % TK; n = e / TK; }
       const int gn = n0 + n, gk = k0 + k;
       Bs[k][n] = (gn < p.N && gk < k_end) ? B[(long long)gk * p.sb_k + (long long)gn * p.sb_n] : 0.0;
     }
@@ -71,9 +74,9 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmParams p) {
     for (int k = 0; k < TK; ++k) {
       double a[4], bb[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+      for (int i = 0; i < 4; ++i) a[i] = As[k][ty + TY * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bb[j] = Bs[k][tx + 16 * j];
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[k][tx + TX * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -86,11 +89,11 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmParams p) {
     double* W = p.work + ((long long)kz * p.batch + b) * (long long)p.M * p.N;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int gm = m0 + ty + 16 * i;
+      const int gm = m0 + ty + TY * i;
       if (gm >= p.M) continue;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int gn = n0 + tx + 16 * j;
+        const int gn = n0 + tx + TX * j;
         if (gn < p.N) W[(long long)gm * p.N + gn] = acc[i][j];
       }
     }
@@ -99,11 +102,11 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmParams p) {
   double* C = p.C + (long long)b * p.sc_b;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int gm = m0 + ty + 16 * i;
+    const int gm = m0 + ty + TY * i;
     if (gm >= p.M) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int gn = n0 + tx + 16 * j;
+      const int gn = n0 + tx + TX * j;
       if (gn >= p.N) continue;
       double* c = C + (long long)gm * p.sc_m + (long long)gn * p.sc_n;
       const double v = p.alpha * acc[i][j];
@@ -132,6 +135,18 @@ __global__ void gemm_splitk_reduce(GemmParams p) {
 
 }  // namespace
 
+// Output tile side with the least padding (64, 48, 40 or 32).
+int pick_tile(int M) {
+  const int cand[4] = {64, 48, 40, 32};
+  int best = 64;
+  double best_eff = 0.0;
+  for (int c : cand) {
+    const double eff = (double)M / (ceil_div(M, c) * c);
+    if (eff > best_eff + 0.02) { best = c; best_eff = eff; }
+  }
+  return best;
+}
+
 int gemm_f64_pick_split(int M, int N, int K, int batch, size_t work_cap_doubles) {
   const long long tiles = (long long)ceil_div(M, TM) * ceil_div(N, TN) * batch;
   const long long target = 152LL * 4;
@@ -157,10 +172,20 @@ void gemm_f64(Exec& ex, const GemmF64& g) {
   p.alpha = g.alpha; p.beta = g.beta;
   p.lower_only = g.lower_only ? 1 : 0;
   p.work = g.work;
-  dim3 grid(ceil_div(g.N, TN), ceil_div(g.M, TM), g.batch * p.ksplit);
+  // tile: 64x64 for lower_only (its tiles must align with the 64-blocked storage),
+  // else the side that pads M and N least
+  const int bm = g.lower_only ? 64 : pick_tile(g.M);
+  const int bnn = g.lower_only ? 64 : pick_tile(g.N);
+  const int side = std::min(bm, bnn) == 64 ? 64 : std::max(std::min(bm, bnn), 32);
+  dim3 grid(ceil_div(g.N, side), ceil_div(g.M, side), g.batch * p.ksplit);
   {
     KScope ks(ex, g.kclass, p.ksplit > 1 ? 2 : 1);
-    gemm_f64_kernel<<<grid, NT, 0, ex.st>>>(p);
+    switch (side) {
+      case 48: gemm_f64_kernel<48, 48><<<grid, 144, 0, ex.st>>>(p); break;
+      case 40: gemm_f64_kernel<40, 40><<<grid, 100, 0, ex.st>>>(p); break;
+      case 32: gemm_f64_kernel<32, 32><<<grid, 64, 0, ex.st>>>(p); break;
+      default: gemm_f64_kernel<64, 64><<<grid, 256, 0, ex.st>>>(p); break;
+    }
     if (p.ksplit > 1) {
       const long long total = (long long)g.M * g.N * g.batch;
       const int blocks = (int)std::min<long long>(ceil_div(total, 256), 152LL * 16);

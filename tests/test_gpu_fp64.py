@@ -154,6 +154,10 @@ def test_mid_pass(nb, no, na, seed):
 def test_three_iterations():
     """Each qsGW step of the GPU equals one oracle step taken from the GPU's own state.
 
+    The bar for the energies is 1e-8 Ha, or ten times the spread of the oracle's
+    own step under a 2-ulp change of its input energies when that is larger (late
+    iterations reach |eps| ~ 1600 Ha with denominators within 1e-6 Ha of a pole).
+
     Trajectories are not compared: with eta = 1e-3 Ha some denominators
     eps_p - eps_m -/+ Omega_s come within ~1e-6 Ha of a pole, where
     g(x) = x / (x^2 + eta^2) amplifies an input change by up to 1/eta^2 = 1e6, so
@@ -178,7 +182,11 @@ def test_three_iterations():
             eps = np.empty(80)
             ctx.qs_step(0, eps)
             r = qsgw.qsgw_pass(m["L"], eps_in, C_in, 16, ETA, h_in)
-            assert np.max(np.abs(eps - r["eps_new"])) < TOL_EPS, k
+            # the oracle's own conditioning: the same step from energies moved by 2 ulps
+            rng = np.random.default_rng(k)
+            eps_pert = eps_in * (1.0 + 4.4e-16 * rng.choice([-1.0, 1.0], eps_in.shape))
+            spread = np.max(np.abs(qsgw.qsgw_pass(m["L"], eps_pert, C_in, 16, ETA, h_in)["eps_new"] - r["eps_new"]))
+            assert np.max(np.abs(eps - r["eps_new"])) < max(TOL_EPS, 10.0 * spread), (k, spread)
             assert rel_max(sc, r["sigma_c"]) < TOL_SIGMA, k
         # the first step starts from the same input on both sides
         assert np.max(np.abs(its[0]["eps_new"] - qsgw.qsgw_pass(m["L"], m["eps"], m["C"], 16, ETA)["eps_new"])) == 0
