@@ -309,7 +309,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="B")
-    ap.add_argument("--precision", choices=["fp64", "bf16x3", "tf32x3"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "bf16x3", "tf32x3", "bf16x6"], default="fp64")
     ap.add_argument("--dominant", default="sigma", help="kernel class reported in 'roofline'")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -62,14 +62,22 @@ enum molgw_status {
 enum molgw_precision {
   MOLGW_PREC_FP64 = 0,    /* float64 on the CUDA cores                                   */
   MOLGW_PREC_BF16X3 = 1,  /* tcgen05 BF16 products, 3-term hi/lo split, FP32 accumulate  */
-  MOLGW_PREC_TF32X3 = 2   /* tcgen05 TF32 products, 3-term hi/lo split, FP32 accumulate  */
+  MOLGW_PREC_TF32X3 = 2,  /* tcgen05 TF32 products, 3-term hi/lo split, FP32 accumulate  */
+  MOLGW_PREC_BF16X6 = 3   /* tcgen05 BF16 products, 3 slices hi+mid+lo, 6 products, FP32 */
 };
+/* With BF16X3, TF32X3 or BF16X6 the residue and self-energy contractions (d),
+ * (e) run on the tensor cores (the residues in float32 chunks of 64 auxiliary
+ * functions summed in float64); (a) and (b) do too only with MOLGW_FLAG_TC_AB.
+ * Near a pole (|eps_p - eps_m -/+ Omega_s| ~ eta) Sigma_c responds to an error
+ * in Omega_s with a factor up to 1/eta^2, and the split products of (a), (b)
+ * leave relative errors of 1e-6 to 1e-5 in M. */
 
 enum molgw_flags {
   MOLGW_FLAG_FULL_XPY = 1u << 0, /* keep the full n_ov x n_ov (X+Y) so molgw_b200_rpa can return it */
   MOLGW_FLAG_KTIMING = 1u << 1,  /* record CUDA events around kernels for molgw_b200_kernel_stats  */
   MOLGW_FLAG_GRAPH = 1u << 2,    /* replay each molecule's qs_step from a captured CUDA graph        */
-  MOLGW_FLAG_USE_STREAM = 1u << 3 /* run on opts.stream even when it is NULL (the legacy default stream) */
+  MOLGW_FLAG_USE_STREAM = 1u << 3, /* run on opts.stream even when it is NULL (the legacy default stream) */
+  MOLGW_FLAG_TC_AB = 1u << 4       /* with BF16X3/TF32X3: stages (a) and (b) on the tensor cores too */
 };
 
 typedef struct {

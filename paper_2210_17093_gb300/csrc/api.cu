@@ -17,6 +17,7 @@ struct molgw_ctx_s {
   KTimer timer;
   Exec ex;
   std::vector<MolBuf> mols;
+  std::vector<TcBufs> tcb;   // split operands of the tensor-core path (precision != FP64)
   Scratch scr;
   EigWork eig;
   int eig_n = 0, eig_cols = 0;
@@ -127,6 +128,19 @@ int ensure_scratch(molgw_ctx c, int nb, int na, long long nov) {
 
 bool mol_ok(molgw_ctx c, int mol) { return c && mol >= 0 && mol < (int)c->mols.size(); }
 
+bool use_tc(molgw_ctx c) { return c->opts.precision != MOLGW_PREC_FP64; }
+int tc_prec(molgw_ctx c) {
+  if (c->opts.precision == MOLGW_PREC_TF32X3) return TC_TF32X3;
+  if (c->opts.precision == MOLGW_PREC_BF16X6) return TC_BF16X6;
+  return TC_BF16X3;
+}
+
+// m values per self-energy block: w and g*w (hi and lo each) within about 1 GB
+int tc_mblock(int prec, int nb, long long nov) {
+  const long long per_m = 2LL * tc_slices(prec) * nb * tc_pad(nov, prec) * tc_elem_bytes(prec);
+  return (int)std::max<long long>(1, std::min<long long>(nb, (1LL << 30) / std::max<long long>(per_m, 1)));
+}
+
 // Run the pass of one molecule up to a stage: 'b' (M), 'c' (rpa), 'e' (sigma), 'f' (qs step).
 int run_pass(molgw_ctx c, int mol, char upto) {
   MolBuf& m = c->mols[mol];
@@ -137,8 +151,16 @@ int run_pass(molgw_ctx c, int mol, char upto) {
                          std::max<int>(std::max(m.na, m.nb), full ? (int)m.nov : 0));
   if (r) return r;
   Exec& ex = c->ex;
+  const bool tc = use_tc(c);
+  const bool tc_ab = tc && (c->opts.flags & MOLGW_FLAG_TC_AB);
+  TcBufs& tb = c->tcb[mol];
   if (!m.b_valid) {
-    stage_ri_mo_transform(ex, m);
+    if (tc_ab) {
+      r = stage_ri_mo_transform_tc(ex, m, tb);
+      if (r) return r;
+    } else {
+      stage_ri_mo_transform(ex, m);
+    }
     m.b_valid = m.have_b = true;
   }
   if (!m.h_ready) {
@@ -148,12 +170,22 @@ int run_pass(molgw_ctx c, int mol, char upto) {
     m.h_ready = true;
   }
   if (upto == 'b') {
-    stage_rpa_build(ex, m);
+    if (tc_ab) {
+      r = stage_rpa_build_tc(ex, m, tb);
+      if (r) return r;
+    } else {
+      stage_rpa_build(ex, m);
+    }
     m.rpa_valid = false;
     return launch_status();
   }
   if (!m.rpa_valid) {
-    stage_rpa_build(ex, m);
+    if (tc_ab) {
+      r = stage_rpa_build_tc(ex, m, tb);
+      if (r) return r;
+    } else {
+      stage_rpa_build(ex, m);
+    }
     stage_rpa_eigensolve(ex, m, c->eig, c->scr, full);
     m.rpa_valid = m.have_rpa = true;
   }
@@ -162,7 +194,12 @@ int run_pass(molgw_ctx c, int mol, char upto) {
       stage_j_sigx(ex, m, c->scr);
       m.jx_valid = m.have_jx = true;
     }
-    stage_sigma(ex, m, c->scr, c->opts.eta);
+    if (tc) {
+      r = stage_sigma_tc(ex, m, tb, c->scr, c->opts.eta);
+      if (r) return r;
+    } else {
+      stage_sigma(ex, m, c->scr, c->opts.eta);
+    }
     m.sigma_valid = m.have_sigma = true;
   }
   if (upto == 'f') {
@@ -182,7 +219,7 @@ int molgw_b200_create(const molgw_opts* o, molgw_ctx* out) {
   if (!out) return MOLGW_E_ARG;
   *out = nullptr;
   if (!o || o->struct_size != (int32_t)sizeof(molgw_opts)) return MOLGW_E_ARG;
-  if (o->precision < MOLGW_PREC_FP64 || o->precision > MOLGW_PREC_TF32X3) return MOLGW_E_ARG;
+  if (o->precision < MOLGW_PREC_FP64 || o->precision > MOLGW_PREC_BF16X6) return MOLGW_E_ARG;
   if (o->max_mols < 1 || !(o->eta > 0.0)) return MOLGW_E_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) { cudaGetLastError(); return MOLGW_E_CUDA; }
@@ -208,6 +245,7 @@ int molgw_b200_create(const molgw_opts* o, molgw_ctx* out) {
   }
   cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st);
   c->mols.resize(o->max_mols);
+  c->tcb.resize(o->max_mols);
   c->timer.enabled = (o->flags & MOLGW_FLAG_KTIMING) != 0;
   c->timer.mask = c->timer.enabled ? 0xffffffffu : 0u;
   c->ex.st = c->st;
@@ -238,11 +276,19 @@ int molgw_b200_set_ri(molgw_ctx c, int mol, int n_basis, int n_aux, const double
     m.L = dalloc(m.ri_allocs, nl, &err);
     m.B = dalloc(m.ri_allocs, nl, &err);
     m.T1 = dalloc(m.ri_allocs, nl, &err);
-    if (err) { free_all(m.ri_allocs); m.nb = m.na = 0; return err; }
+    TcBufs& tb = c->tcb[mol];
+    free_all(tb.ri_allocs);
+    free_all(tb.orb_allocs);
+    if (use_tc(c) && (c->opts.flags & MOLGW_FLAG_TC_AB)) {
+      double* base = dalloc(tb.ri_allocs, tc_ri_doubles(tc_prec(c), n_basis, n_aux), &err);
+      if (!err) tc_ri_carve(tb, tc_prec(c), n_basis, n_aux, base);
+    }
+    if (err) { free_all(m.ri_allocs); free_all(tb.ri_allocs); m.nb = m.na = 0; return err; }
   }
   int r = copy_in(c, m.L, L, nl);
   if (r) return r;
   check_finite(c->ex, m.L, (long long)nl);
+  if (use_tc(c) && (c->opts.flags & MOLGW_FLAG_TC_AB)) tc_split_ri(c->ex, m, c->tcb[mol]);
   m.have_ri = true;
   return launch_status();
 }
@@ -276,7 +322,20 @@ int molgw_b200_set_orbitals(molgw_ctx c, int mol, int n_occ, const double* eps, 
     m.M = dalloc(m.orb_allocs, (size_t)nov * nov, &err);
     m.ZT = dalloc(m.orb_allocs, (size_t)nov * nov, &err);
     m.XpY = full ? dalloc(m.orb_allocs, (size_t)nov * nov, &err) : nullptr;
-    if (err) { free_all(m.orb_allocs); m.eps = nullptr; m.alloc_no = 0; return err; }
+    TcBufs& tb = c->tcb[mol];
+    free_all(tb.orb_allocs);
+    if (use_tc(c) && !err) {
+      const int prec = tc_prec(c);
+      const int mb = tc_mblock(prec, nb, nov);
+      const size_t nd = tc_orb_doubles(prec, nb, na, nov, mb, tc_pad(nov, prec));
+      double* base = dalloc(tb.orb_allocs, nd, &err);
+      if (!err) {
+        // padding columns that no kernel writes (X beyond nb, w and g*w beyond n_ov) must read as zero
+        cudaMemsetAsync(base, 0, nd * sizeof(double), c->st);
+        tc_bufs_carve(tb, prec, nb, na, nov, mb, base);
+      }
+    }
+    if (err) { free_all(m.orb_allocs); free_all(tb.orb_allocs); m.eps = nullptr; m.alloc_no = 0; return err; }
     m.alloc_no = n_occ;
   }
   m.no = n_occ;
@@ -476,6 +535,7 @@ int molgw_b200_destroy(molgw_ctx c) {
     DeviceGuard g(c->device);
     s = read_status(c);
     for (auto& m : c->mols) { free_all(m.ri_allocs); free_all(m.orb_allocs); }
+    for (auto& t : c->tcb) { free_all(t.ri_allocs); free_all(t.orb_allocs); }
     if (c->scr.base) cudaFree(c->scr.base);
     eig_work_free(c->eig);
     cudaFree(c->d_status);

@@ -235,14 +235,21 @@ void stage_j_sigx(Exec& ex, MolBuf& m, Scratch& s) {
   gemm_f64(ex, g);
 }
 
+void gather_xv(Exec& ex, MolBuf& m) {
+  KScope ks(ex, MOLGW_K_MISC);
+  k_gather_xv<<<grid_for(m.nov * m.na), 256, 0, ex.st>>>(m.B, m.eps, m.nb, m.no, m.na, m.Xv, m.D);
+}
+
+void symmetrize(Exec& ex, const double* S, int n, double* out) {
+  KScope ks(ex, MOLGW_K_MISC);
+  k_symmetrize<<<grid_for((long long)n * n), 256, 0, ex.st>>>(S, n, out);
+}
+
 // (b) M = diag(D^2) + Xv Xv^T, Xv = 2 D^1/2 B_ia^T (n_ov x n_aux, column-major).
 void stage_rpa_build(Exec& ex, MolBuf& m) {
-  const int nb = m.nb, na = m.na, no = m.no;
+  const int na = m.na;
   const long long nov = m.nov;
-  {
-    KScope ks(ex, MOLGW_K_MISC);
-    k_gather_xv<<<grid_for(nov * na), 256, 0, ex.st>>>(m.B, m.eps, nb, no, na, m.Xv, m.D);
-  }
+  gather_xv(ex, m);
   GemmF64 g;
   g.M = (int)nov; g.N = (int)nov; g.K = na;
   g.A = m.Xv; g.sa_m = 1; g.sa_k = nov;

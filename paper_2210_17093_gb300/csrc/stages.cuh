@@ -1,6 +1,7 @@
 // Per-molecule device buffers and the stage drivers of one RI-qsGW pass.
 #pragma once
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace molgw {
 
@@ -27,6 +28,23 @@ struct MolBuf {
   std::vector<void*> ri_allocs, orb_allocs;
 };
 
+// Split operands of the tensor-core path (hi/lo pairs, K-major, padded).
+struct TcBufs {
+  int prec = TC_BF16X3;
+  int mb = 0;            // m values per self-energy block
+  long long sp = 0;      // padded n_ov
+  TcMat L;               // (n_aux*nb) x nb: L[P][nu][mu]       (per set_ri)
+  TcMat Ct, X, Xv, Rt, Bt, W, P;                  // per set_orbitals
+  float* wpart = nullptr;                         // float32 K-chunk partials of w
+  long long wpart_floats = 0;
+  std::vector<void*> ri_allocs, orb_allocs;
+};
+
+size_t tc_ri_doubles(int prec, int nb, int na);
+size_t tc_orb_doubles(int prec, int nb, int na, long long nov, int mb, long long sp);
+void tc_ri_carve(TcBufs& t, int prec, int nb, int na, double* base);
+void tc_bufs_carve(TcBufs& t, int prec, int nb, int na, long long nov, int mb, double* base);
+
 struct Scratch {
   double* rho = nullptr;        // n_aux
   double* splitk = nullptr;     // split-K partials
@@ -50,5 +68,13 @@ void derive_h_from_hf(Exec& ex, MolBuf& m);
 void h_ao_to_mo(Exec& ex, MolBuf& m, const double* hao, Scratch& s);
 void stage_qs_update(Exec& ex, MolBuf& m, EigWork& w, Scratch& s);
 void eigh_dense(Exec& ex, EigWork& w, int n, double* A, double* Z);
+void gather_xv(Exec& ex, MolBuf& m);
+void symmetrize(Exec& ex, const double* S, int n, double* out);
+
+// tensor-core (split precision) versions of stages (a), (b), (d)+(e)
+void tc_split_ri(Exec& ex, MolBuf& m, TcBufs& t);
+int stage_ri_mo_transform_tc(Exec& ex, MolBuf& m, TcBufs& t);
+int stage_rpa_build_tc(Exec& ex, MolBuf& m, TcBufs& t);
+int stage_sigma_tc(Exec& ex, MolBuf& m, TcBufs& t, Scratch& s, double eta);
 
 }  // namespace molgw

@@ -1,0 +1,220 @@
+// Stages (a), (b), (d)+(e) on the split-precision tensor-core engine.
+//
+// (a) X_P = C^T L_P (batched over P, split output), B_P = X_P C (float64 output);
+// (b) M = Xv Xv^T + D^2 with Xv = 2 D^1/2 B_ia^T, float64 epilogue, lower tiles;
+// (d)+(e) for each block of m: w_m = B_m^T R (rows (m, p), columns s), whose
+//     epilogue takes the float64 differences eps_p - eps_m -/+ Omega_s, forms
+//     g = x / (x^2 + eta^2) and writes w and g*w as split operands laid out
+//     [p][m*sp + s]; then S += (g w) w^T over K = (m, s) with split-K float32
+//     partials reduced in a fixed order in float64.
+// The eigensolvers (c), (f) and the back-transformation stay in float64.
+#include "stages.cuh"
+#include "tc.cuh"
+
+namespace molgw {
+
+namespace {
+
+constexpr int kW = 64;                              // K elements per float32 chunk of w
+constexpr long long kWpartDoubles = 1LL << 27;      // 1 GB of float32 chunk partials
+
+TcMat carve(double*& base_bytes_as_double, long long rows, long long ld, int prec) {
+  // carve the slices (each rows x ld elements) from a byte arena kept in doubles
+  TcMat m;
+  m.rows = rows;
+  m.ld = ld;
+  const long long bytes = rows * ld * tc_elem_bytes(prec);
+  const long long words = (bytes + 255) / 256 * 32;   // 256-byte aligned, in doubles
+  m.hi = base_bytes_as_double;
+  base_bytes_as_double += words;
+  m.lo = base_bytes_as_double;
+  base_bytes_as_double += words;
+  if (tc_slices(prec) == 3) {
+    m.lo2 = base_bytes_as_double;
+    base_bytes_as_double += words;
+  }
+  return m;
+}
+
+long long carve_doubles(long long rows, long long ld, int prec) {
+  const long long bytes = rows * ld * tc_elem_bytes(prec);
+  return tc_slices(prec) * ((bytes + 255) / 256 * 32);
+}
+
+// w = sum of the float32 chunk partials in float64; x = (eps_p - eps_m) -/+ Omega_s in
+// float64; g = x / (x^2 + eta^2); w and g*w stored as split operands [p][mm*sp + s].
+template <int PREC>
+__global__ void k_sigma_combine(const float* __restrict__ part, int kw, long long rows, long long nov,
+                                const double* __restrict__ eps, const double* __restrict__ omega, int nb, int no,
+                                int m0, long long sp, double eta, TcMat W, TcMat P) {
+  const long long total = rows * nov;
+  const double eta2 = eta * eta;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    double w = 0.0;
+    for (int k = 0; k < kw; ++k) w += (double)part[(long long)k * total + idx];
+    const long long row = idx / nov, sidx = idx % nov;
+    const int mm = (int)(row / nb), pp = (int)(row % nb), m = m0 + mm;
+    const double x = (eps[pp] - eps[m]) + ((m < no) ? omega[sidx] : -omega[sidx]);
+    const double g = x / (x * x + eta2);
+    const long long o = (long long)pp * W.ld + (long long)mm * sp + sidx;
+    tc_store_split<PREC>(W, o, w);
+    tc_store_split<PREC>(P, o, w * g);
+  }
+}
+
+}  // namespace
+
+size_t tc_ri_doubles(int prec, int nb, int na) {
+  return (size_t)carve_doubles((long long)na * nb, tc_pad(nb, prec), prec);
+}
+
+size_t tc_orb_doubles(int prec, int nb, int na, long long nov, int mb, long long sp) {
+  const long long nbp = tc_pad(nb, prec), nap = tc_pad(na, prec);
+  size_t t = 0;
+  t += carve_doubles(nb, nbp, prec);                 // C^T
+  t += carve_doubles((long long)na * nb, nbp, prec); // X
+  t += carve_doubles(nov, nap, prec);                // Xv
+  t += carve_doubles(nov, nap, prec);                // R^T
+  t += carve_doubles((long long)nb * nb, nap, prec); // B^T per m
+  t += 2 * carve_doubles(nb, (long long)mb * sp, prec);   // w, g*w
+  t += kWpartDoubles;                                       // float32 chunk partials of w
+  return t;
+}
+
+void tc_bufs_carve(TcBufs& t, int prec, int nb, int na, long long nov, int mb, double* base) {
+  const long long nbp = tc_pad(nb, prec), nap = tc_pad(na, prec);
+  t.prec = prec;
+  t.mb = mb;
+  t.sp = tc_pad(nov, prec);
+  double* p = base;
+  t.Ct = carve(p, nb, nbp, prec);
+  t.X = carve(p, (long long)na * nb, nbp, prec);
+  t.Xv = carve(p, nov, nap, prec);
+  t.Rt = carve(p, nov, nap, prec);
+  t.Bt = carve(p, (long long)nb * nb, nap, prec);
+  t.W = carve(p, nb, (long long)mb * t.sp, prec);
+  t.P = carve(p, nb, (long long)mb * t.sp, prec);
+  t.wpart = reinterpret_cast<float*>(p);
+  t.wpart_floats = 2 * kWpartDoubles;
+  p += kWpartDoubles;
+}
+
+void tc_ri_carve(TcBufs& t, int prec, int nb, int na, double* base) {
+  double* p = base;
+  t.prec = prec;
+  t.L = carve(p, (long long)na * nb, tc_pad(nb, prec), prec);
+}
+
+// Split of L, once per set of RI factors: rows (P, nu), K = mu (L symmetric in mu nu).
+void tc_split_ri(Exec& ex, MolBuf& m, TcBufs& t) {
+  tc_split(ex, t.prec, m.L, (long long)m.na * m.nb, m.nb, m.nb, 1, nullptr, t.L);
+}
+
+int stage_ri_mo_transform_tc(Exec& ex, MolBuf& m, TcBufs& t) {
+  const int nb = m.nb, na = m.na;
+  const long long nbp = tc_pad(nb, t.prec);
+  // C^T: element (p, mu) = C[mu][p]
+  tc_split(ex, t.prec, m.C, nb, nb, 1, nb, nullptr, t.Ct);
+  // X_P[q][nu] = sum_mu C[mu][q] L_P[nu][mu]
+  TcGemm g1;
+  g1.prec = t.prec;
+  g1.M = nb; g1.N = nb; g1.K = (int)nbp;
+  g1.A = t.Ct; g1.B = t.L;
+  g1.batch = na; g1.a_batch_rows = 0; g1.b_batch_rows = nb; g1.out_batch_rows = nb;
+  g1.epi.mode = TC_EPI_SPLIT;
+  g1.epi.out_split = t.X;
+  int r = tc_gemm(ex, g1);
+  if (r) return r;
+  // B[(P,q)][p] = sum_nu X[(P,q)][nu] C[nu][p]
+  TcGemm g2;
+  g2.prec = t.prec;
+  g2.M = na * nb; g2.N = nb; g2.K = (int)nbp;
+  g2.A = t.X; g2.B = t.Ct;
+  g2.epi.mode = TC_EPI_F64;
+  g2.epi.out_f64 = m.B;
+  g2.epi.out_ld = nb;
+  return tc_gemm(ex, g2);
+}
+
+int stage_rpa_build_tc(Exec& ex, MolBuf& m, TcBufs& t) {
+  const int na = m.na;
+  const long long nov = m.nov;
+  gather_xv(ex, m);                                    // float64 Xv (column-major) and D
+  tc_split(ex, t.prec, m.Xv, nov, na, 1, nov, nullptr, t.Xv);
+  TcGemm g;
+  g.prec = t.prec;
+  g.M = (int)nov; g.N = (int)nov; g.K = (int)tc_pad(na, t.prec);
+  g.A = t.Xv; g.B = t.Xv;
+  g.lower_only = true;
+  g.epi.mode = TC_EPI_RPA;
+  g.epi.out_f64 = m.M;
+  g.epi.out_ld = nov;
+  g.epi.diag = m.D;
+  return tc_gemm(ex, g);
+}
+
+int stage_sigma_tc(Exec& ex, MolBuf& m, TcBufs& t, Scratch& s, double eta) {
+  const int nb = m.nb, na = m.na, no = m.no;
+  const long long nov = m.nov, nn = (long long)nb * nb;
+  const long long nap = tc_pad(na, t.prec);
+  // R^T: element (s, P) = R[P][s];  B^T: element ((m, p), P) = B[P][m][p]
+  tc_split(ex, t.prec, m.R, nov, na, 1, nov, nullptr, t.Rt);
+  tc_split(ex, t.prec, m.B, nn, na, 1, nn, nullptr, t.Bt);
+  const int es = tc_elem_bytes(t.prec);
+  // w in K chunks of KW elements (float32 on the tensor cores), combined in float64
+  const int kb = tc_kblock(t.prec);
+  const int nkw = (int)(nap / kb);
+  const int kw = tc_ksplit_of(nkw, ceil_div(nkw, std::max(1, kW / kb)));
+  const long long per_m = (long long)kw * nb * nov;   // floats of partials per m
+  const int mstep = (int)std::max<long long>(1, std::min<long long>(t.mb, t.wpart_floats / std::max<long long>(per_m, 1)));
+  for (int m0 = 0; m0 < nb; m0 += mstep) {
+    const int cnt = std::min(mstep, nb - m0);
+    TcGemm gw;
+    gw.prec = t.prec;
+    gw.M = cnt * nb; gw.N = (int)nov; gw.K = (int)nap;
+    gw.A = t.Bt;
+    gw.A.hi = (char*)t.Bt.hi + (long long)m0 * nb * nap * es;
+    gw.A.lo = (char*)t.Bt.lo + (long long)m0 * nb * nap * es;
+    gw.A.rows = (long long)cnt * nb;
+    gw.B = t.Rt;
+    gw.ksplit = kw;
+    gw.epi.mode = TC_EPI_F32_PARTIAL;
+    gw.epi.out_f32 = t.wpart;
+    int r = tc_gemm(ex, gw);
+    if (r) return r;
+    {
+      const long long total = (long long)cnt * nb * nov;
+      const int blocks = (int)std::min<long long>(ceil_div(total, 256), 152LL * 16);
+      KScope ks(ex, MOLGW_K_SIGMA);
+      if (t.prec == TC_BF16X3)
+        k_sigma_combine<TC_BF16X3><<<blocks, 256, 0, ex.st>>>(t.wpart, kw, (long long)cnt * nb, nov, m.eps, m.Om, nb,
+                                                             no, m0, t.sp, eta, t.W, t.P);
+      else if (t.prec == TC_TF32X3)
+        k_sigma_combine<TC_TF32X3><<<blocks, 256, 0, ex.st>>>(t.wpart, kw, (long long)cnt * nb, nov, m.eps, m.Om, nb,
+                                                             no, m0, t.sp, eta, t.W, t.P);
+      else
+        k_sigma_combine<TC_BF16X6><<<blocks, 256, 0, ex.st>>>(t.wpart, kw, (long long)cnt * nb, nov, m.eps, m.Om, nb,
+                                                             no, m0, t.sp, eta, t.W, t.P);
+    }
+    TcGemm gs;
+    gs.prec = t.prec;
+    gs.M = nb; gs.N = nb; gs.K = (int)(cnt * t.sp);
+    gs.A = t.P; gs.B = t.W;
+    // split K = (m, s) into chunks of ~1024 products: the tensor cores accumulate
+    // in float32, the partials are summed in float64
+    int ks = std::max(1, gs.K / 1024);
+    ks = std::min(ks, (int)(s.splitk_cap * 2 / std::max<long long>(nn, 1)));   // float partials in the double arena
+    ks = tc_ksplit_of(gs.K / kb, std::max(ks, 1));
+    gs.ksplit = ks;
+    gs.epi.mode = TC_EPI_F32_PARTIAL;
+    gs.epi.out_f32 = reinterpret_cast<float*>(s.splitk);
+    r = tc_gemm(ex, gs);
+    if (r) return r;
+    tc_reduce_partials(ex, reinterpret_cast<float*>(s.splitk), ks, nb, nb, s.S, nb, m0 == 0 ? 0.0 : 1.0);
+  }
+  symmetrize(ex, s.S, nb, m.sigc);
+  return MOLGW_OK;
+}
+
+}  // namespace molgw

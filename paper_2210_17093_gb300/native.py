@@ -15,11 +15,12 @@ import numpy as np
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libmolgw_gb300.so")
 
-PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
+PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2, "bf16x6": 3}
 FLAG_FULL_XPY = 1
 FLAG_KTIMING = 2
 FLAG_GRAPH = 4
 FLAG_USE_STREAM = 8
+FLAG_TC_AB = 16
 
 ITEM = {"B": 0, "Omega": 1, "R": 2, "sigma_x": 3, "sigma_c": 4, "J": 5, "h_mo": 6, "eps": 7, "C": 8}
 KERNELS = ["gemm_f64", "tridiag_panel", "tridiag_syr2k", "bisect", "twisted", "backtransform",
