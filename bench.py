@@ -47,11 +47,17 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def workload_flops(nb, no, na):
-    """Useful float64 flops per qsGW iteration, per kernel class (one product = 2 flops)."""
+    """Useful float64 flops per qsGW iteration (one product = 2 flops).
+
+    Keys are the library's kernel classes where one class does the work.
+    """
     n = no * (nb - no)
     return {
         "sigma": 2.0 * nb * nb * na * n + 2.0 * nb ** 3 * n,      # w^s_pm per m block + S += (w g) w^T
-        "tridiag": 4.0 / 3.0 * n ** 3,                              # Householder reduction of M
+        # Householder reduction of M: symmetric matrix-vector products (2n^3/3) in the
+        # panel kernel, rank-2k trailing updates of the lower triangle (2n^3/3) in the GEMM
+        "tridiag_panel": 2.0 / 3.0 * n ** 3 + 2.0 * 64 * n * n,
+        "tridiag_syr2k": 2.0 / 3.0 * n ** 3,
         "backtransform": 4.0 * na * n * n,                          # Q^T Xv and R = Y^T Z_T
         "rpa_build": 1.0 * na * n * n,                              # lower half of Xv Xv^T
         "ri_mo_transform": 4.0 * na * nb ** 3,
@@ -265,13 +271,48 @@ def run_ours(args, wl):
         t_e2e = (time.perf_counter() - t0) / e2e_steps
         barrier(dist)
         t_e2e = max_over_ranks(dist, t_e2e)
+        eps_fp64_step1 = eps_o.numpy().copy()     # float64 step from the input orbitals
+
+    mixed = None
+    if not args.no_mixed:
+        # the split-precision path on the same molecule: time per step, and its first
+        # step against the float64 GPU path (which matches the CPU oracle to 1e-8 Ha)
+        with Context(precision=args.mixed, device=local, eta=sy.ETA, stream=st) as mctx:
+            mctx.set_ri(0, nb, na, L_d)
+            mctx.set_orbitals(0, no, eps_d, C_d)
+            e1 = torch.empty(nb, dtype=torch.float64).pin_memory()
+            mctx.qs_step(0, e1)
+            for _ in range(max(0, args.warmup - 1)):
+                mctx.qs_step(0)
+            mctx.sync()
+            m0 = torch.cuda.Event(enable_timing=True)
+            m1 = torch.cuda.Event(enable_timing=True)
+            barrier(dist)
+            torch.cuda.synchronize()
+            m0.record(st)
+            for _ in range(args.steps):
+                mctx.qs_step(0)
+            m1.record(st)
+            torch.cuda.synchronize()
+            t_mixed = max_over_ranks(dist, m0.elapsed_time(m1) / 1e3)
+            mctx.set_timing(["gemm_f64", "tridiag_panel", "tridiag_syr2k", "bisect", "twisted",
+                             "backtransform", "sigma", "gemm_tc", "misc"])
+            mctx.kernel_stats(reset=True)
+            mctx.qs_step(0)
+            mbreak = mctx.kernel_stats(reset=True)
+        err = float(np.max(np.abs(e1.numpy() - eps_fp64_step1)))
+        mixed = {"precision": args.mixed, "stages": "(d)+(e) on tcgen05 tensor cores; (a)-(c), (f) float64",
+                 "ms_per_step": t_mixed / args.steps * 1e3,
+                 "speedup_vs_fp64": (t_max / args.steps) / (t_mixed / args.steps),
+                 "qp_error_vs_fp64_meV": err * 27211.386,
+                 "meets_1meV": bool(err * 27211.386 <= 1.0),
+                 "stages_ms": {k: round(v[1], 3) for k, v in mbreak.items() if v[0]}}
 
     if rank != 0:
         return 0
     value = t_max / (args.steps * world)
     nl, kms = kstats[dominant]
-    dom_flops = {"sigma": flops["sigma"], "tridiag_panel": flops["tridiag"] / 2,
-                 "tridiag_syr2k": flops["tridiag"] / 2, "backtransform": flops["backtransform"]}.get(dominant)
+    dom_flops = flops.get(dominant)
     achieved = dom_flops * args.steps / (kms / 1e3) / 1e12 if (dom_flops and kms > 0) else None
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -288,6 +329,7 @@ def run_ours(args, wl):
             "launches": nl, "event_ms": kms,
         },
         "stages_ms": {k: round(v[1], 3) for k, v in breakdown.items() if v[0]},
+        "mixed": mixed,
         "e2e": {"value": t_e2e, "unit": "s",
                 "h2d_bytes_per_step": int((na * nb * nb + nb + nb * nb) * 8),
                 "d2h_bytes_per_step": int((nb + nb * nb) * 8)},
@@ -310,7 +352,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="B")
     ap.add_argument("--precision", choices=["fp64", "bf16x3", "tf32x3", "bf16x6"], default="fp64")
-    ap.add_argument("--dominant", default="sigma", help="kernel class reported in 'roofline'")
+    ap.add_argument("--dominant", default="tridiag_panel", help="kernel class reported in 'roofline'")
+    ap.add_argument("--mixed", choices=["bf16x3", "tf32x3", "bf16x6"], default="bf16x3",
+                    help="precision of the split-precision path reported under 'mixed'")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -172,7 +172,7 @@ int molgw_b200_eigh(molgw_ctx ctx, int n, const double* A, double* w, double* Z)
  *   n <= MOLGW_NOALLOC_NMAX; A[n][n] symmetric, w[n], Z[n][n] (may be NULL) are
  *   DEVICE pointers on the current device (else MOLGW_E_ARG); results as for
  *   molgw_b200_eigh.  stream: the cudaStream_t to run on (NULL = legacy default).
- *   All workspace is one fixed device array of 4.93 MB inside the library, held
+ *   All workspace is one fixed device array of 5.07 MB inside the library, held
  *   by every GPU that loads it until the process exits; no call allocates or
  *   frees.  The first call on a device looks up that array's address (once per
  *   device, with the device current), so make it before any stream capture.

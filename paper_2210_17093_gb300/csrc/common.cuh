@@ -125,7 +125,8 @@ struct EigWork {
 // up to ncols (>= 64) columns at a time.
 constexpr int kMaxPanelGrid = 320;   // CTAs of the tridiagonalisation panel kernel, at most
 constexpr size_t eig_part_doubles(size_t n) {
-  return 2 * ((n + 63) / 64 + 1) + ((n + 63) / 64) * 128 + 2 * n * 128 + 8 + (size_t)kMaxPanelGrid * n + 64;
+  return 2 * ((n + 31) / 32 + 1) + ((n + 31) / 32 + 1) * 128 + 128 + 2 * n * 128 + 8 +
+         ((n + 63) / 64) * ((n + 63) / 64 + 1) / 2 * 64 + (size_t)kMaxPanelGrid * n + 64;
 }
 constexpr size_t eig_gk_doubles(size_t n, size_t ncols) {
   return (16 * 64 * ncols > 8 * (n / 64 + 1) * 64 * 64) ? 16 * 64 * ncols : 8 * (n / 64 + 1) * 64 * 64;

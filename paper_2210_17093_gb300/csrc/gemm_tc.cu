@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256, 1)
       issued = i + 1;
     }
     // copies still in flight (only on an error path) land before the CTA leaves
-    for (int i = std::max(0, issued - STAGES); i < issued; ++i) mbar_wait(&full[i % STAGES], (i / STAGES) & 1);
+    for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; ++i) mbar_wait(&full[i % STAGES], (i / STAGES) & 1);
   } else if (warp == 1 && lane == 0) {
     // D F32 (bit 4); A, B type at bits 7-9 / 10-12 (BF16 = 1, TF32 = 2); K-major; N>>3 at 17; M>>4 at 24
     const uint32_t ty = (PREC == TC_TF32X3) ? 2u : 1u;

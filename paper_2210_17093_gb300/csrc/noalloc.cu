@@ -11,8 +11,8 @@
 // lives in one file-scope device array of fixed size, so the call allocates
 // nothing.  The caller passes device pointers for the input and the outputs.
 //
-// The array is sized for n <= MOLGW_NOALLOC_NMAX (256): 616,356 doubles
-// (4.93 MB, the status slot included), held by every GPU that loads the library
+// The array is sized for n <= MOLGW_NOALLOC_NMAX (256): 633,914 doubles
+// (5.07 MB, the status slot included), held by every GPU that loads the library
 // until the process exits.
 #include "stages.cuh"
 

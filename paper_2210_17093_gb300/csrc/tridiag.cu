@@ -37,7 +37,7 @@ namespace {
 constexpr int NBP = 64;     // panel width
 constexpr int TB = 64;      // tile size of the symmetric matrix-vector product
 constexpr int RT = 256;     // threads per CTA; rows per work item of the panel-end packing
-constexpr int RC = 64;      // rows per work item in P1/P3 (four threads per row)
+constexpr int RC = 32;      // rows per work item in P1/P3 (eight threads per row)
 
 struct GridBar {
   unsigned int count;
@@ -53,8 +53,10 @@ struct PanelParams {
   double* d; double* e; double* tau;
   double* scal;             // [0] alpha, [3] uncorrected W(i+1, j)
   double* p_ss;             // P1 partials
-  double* p_vw;             // P2: per row block, 2*NBP values
+  double* p_vw;             // P1: per 32-row chunk, 2*NBP dot-product partials
+  double* vwf;              // P2: the finished V^T v and W^T v (2*NBP)
   double* p_y;              // P2: per CTA, partial y over the row blocks its tile range covers
+  double* p_t;              // P2: per lower tile, transposed partial of y (64 values)
   double* p_wv;             // P3 partials
   double* VW; double* WV;   // packed [V W] and [W V] of rows >= k1
   GridBar* bar;
@@ -153,9 +155,9 @@ __device__ __forceinline__ double vval(const PanelParams& p, int i, int r, doubl
 __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
   __shared__ double sh[40];
   __shared__ double Wi[NBP], Vi[NBP], vtv[NBP], wtv[NBP];
+  __shared__ double dots[RT / 32][2 * NBP];
   __shared__ double tile[TB * (TB + 1)];
-  __shared__ double vJ[TB];
-  __shared__ double red[4][TB];
+  __shared__ double vJ[TB], vR[TB];
   const int n = p.n, k0 = p.k0;
   const long long ld = n;
   double* A = p.A;
@@ -177,34 +179,67 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
       Vi[c] = ldg_cg(A + i + (long long)(k0 + c) * ld);
     }
     __syncthreads();
-    // 64 rows per chunk, four lanes per row share the loop over the panel's columns
-    const int rl = t >> 2, q4 = t & 3;
+    // 32 rows per chunk, eight lanes per row share the loop over the panel's columns.
+    // Besides the update, each chunk adds up V(r,:) a(r) and W(r,:) a(r) over its
+    // rows r >= i+2 (a = the updated, still unscaled column): the dot products
+    // V^T v and W^T v of P3 are these sums times the reflector's scale plus the
+    // row i+1 terms (v(i+1) = 1).
+    const int rl = t >> 3, q8 = t & 7, wl = t >> 5;
     const int n1 = ceil_div_d(n - i, RC);
     for (int ch = blockIdx.x; ch < n1; ch += gridDim.x) {
       const int r = i + ch * RC + rl;
       double upd = 0.0, wcorr = 0.0;
-      if (r < n) {
-        if (j > 0) wcorr = ldg_cg(p.Wp + r + (long long)(j - 1) * ld) + alpha_w * ldg_cg(A + r + (long long)(i - 1) * ld);
-#pragma unroll 4
-        for (int c = q4; c < j; c += 4) {
-          const double vr = ldg_cg(A + r + (long long)(k0 + c) * ld);
-          const double wr = (c == j - 1) ? wcorr : ldg_cg(p.Wp + r + (long long)c * ld);
-          upd += vr * Wi[c] + wr * Vi[c];
+      double vs[NBP / 8], ws[NBP / 8];
+      if (r < n && j > 0)
+        wcorr = ldg_cg(p.Wp + r + (long long)(j - 1) * ld) + alpha_w * ldg_cg(A + r + (long long)(i - 1) * ld);
+#pragma unroll
+      for (int k = 0; k < NBP / 8; ++k) {
+        const int c = q8 + 8 * k;
+        vs[k] = 0.0;
+        ws[k] = 0.0;
+        if (r < n && c < j) {
+          vs[k] = ldg_cg(A + r + (long long)(k0 + c) * ld);
+          ws[k] = (c == j - 1) ? wcorr : ldg_cg(p.Wp + r + (long long)c * ld);
+          upd += vs[k] * Wi[c] + ws[k] * Vi[c];
         }
       }
       upd += __shfl_xor_sync(0xffffffffu, upd, 1);
       upd += __shfl_xor_sync(0xffffffffu, upd, 2);
+      upd += __shfl_xor_sync(0xffffffffu, upd, 4);
+      double a = 0.0;
+      if (r < n) a = ldg_cg(A + r + (long long)i * ld) - upd;
       double sq = 0.0;
-      if (r < n && q4 == 0) {
+      if (r < n && q8 == 0) {
         if (j > 0) p.Wp[r + (long long)(j - 1) * ld] = wcorr;
-        const double a = ldg_cg(A + r + (long long)i * ld) - upd;
         A[r + (long long)i * ld] = a;
         if (r == i) p.d[i] = a;
         if (r == i + 1) p.scal[0] = a;
         if (r >= i + 2) sq = a * a;
       }
-      const double s = blk_reduce_sum(sq, sh);
+      // dot partials over the chunk's rows: lanes of one q8 hold 8 columns each
+      const double aa = (r < n && r >= i + 2) ? a : 0.0;
+#pragma unroll
+      for (int k = 0; k < NBP / 8; ++k) {
+        double dv = vs[k] * aa, dw = ws[k] * aa;
+        dv += __shfl_xor_sync(0xffffffffu, dv, 8);
+        dv += __shfl_xor_sync(0xffffffffu, dv, 16);
+        dw += __shfl_xor_sync(0xffffffffu, dw, 8);
+        dw += __shfl_xor_sync(0xffffffffu, dw, 16);
+        if ((t & 31) < 8) {
+          dots[wl][q8 + 8 * k] = dv;
+          dots[wl][NBP + q8 + 8 * k] = dw;
+        }
+      }
+      const double s = blk_reduce_sum(sq, sh);   // includes a __syncthreads after the dots
       if (t == 0) p.p_ss[ch] = s;
+      for (int c = t; c < 2 * j; c += blockDim.x) {
+        const int col = (c < j) ? c : NBP + (c - j);
+        double d2 = 0.0;
+#pragma unroll
+        for (int w8 = 0; w8 < RT / 32; ++w8) d2 += dots[w8][col];
+        p.p_vw[(long long)ch * (2 * NBP) + c] = d2;
+      }
+      __syncthreads();
     }
     if (!grid_sync(p.bar, p.status)) return;
 
@@ -213,22 +248,48 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
     const int lo = i + 1;
     const int rb0 = lo / TB;
     const int nrb = nrbt - rb0;
-    // the nrb x nrb tiles of A22, row-major, split into equal contiguous ranges
-    const long long T = (long long)nrb * nrb;
+    {
+      // V^T v = V(i+1,:) + scale * (sum over the P1 chunks), the same for W^T v:
+      // the first CTAs finish these 2j sums (one warp per value) for P3
+      const int warp = t >> 5, lane = t & 31;
+      const int c = blockIdx.x * (RT / 32) + warp;
+      if (c < 2 * j) {
+        double s2 = 0.0;
+        for (int ch = lane; ch < n1; ch += 32) s2 += ldg_cg(p.p_vw + (long long)ch * (2 * NBP) + c);
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        if (lane == 0) {
+          const double row1 = (c < j) ? ldg_cg(A + lo + (long long)(k0 + c) * ld) : ldg_cg(p.Wp + lo + (long long)(c - j) * ld);
+          p.vwf[c] = row1 + h.scale * s2;
+        }
+      }
+    }
+    // The stored (lower and diagonal) tiles of A22 in row-major order (R, J <= R),
+    // split into equal contiguous ranges.  Each tile is read once and used twice:
+    // y_R += A_RJ v_J (accumulated per thread along the row, stored per CTA and row
+    // block) and, below the diagonal, y_J += A_RJ^T v_R (reduced over the four lanes
+    // that share a column, stored per tile).
+    const long long T = (long long)nrb * (nrb + 1) / 2;
     const long long f0 = (long long)blockIdx.x * T / gridDim.x;
     const long long f1 = (long long)(blockIdx.x + 1) * T / gridDim.x;
     if (f0 < f1) {
       const int rr = t % TB, cq = t / TB;
-      const int q = t / TB, x = t % TB;
+      const int x = t >> 2, q = t & 3;          // row / column x of the tile, quarter q of the other index
       double nxt[16];
       double vnxt = 0.0;
-      auto load_tile = [&](long long f) {
-        const int R = rb0 + (int)(f / nrb), J = rb0 + (int)(f % nrb);
-        const int tr = (J >= R) ? J : R, tc = (J >= R) ? R : J;   // stored tile (tr >= tc)
-        const int gr = tr * TB + rr;
+      // (R, J) of the first tile of the range: R - rb0 = the largest a with a(a+1)/2 <= f0
+      // (integer search; later tiles advance J, then R)
+      int R0 = rb0, J0 = rb0;
+      {
+        long long a = 0;
+        while ((a + 1) * (a + 2) / 2 <= f0) ++a;
+        R0 = rb0 + (int)a;
+        J0 = rb0 + (int)(f0 - a * (a + 1) / 2);
+      }
+      auto load_tile = [&](int R, int J) {
+        const int gr = R * TB + rr;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-          const int gc = tc * TB + cq + 4 * k;
+          const int gc = J * TB + cq + 4 * k;
           nxt[k] = (gr < n && gc < n) ? ldg_cg(A + gr + (long long)gc * ld) : 0.0;
         }
         if (t < TB) {
@@ -236,74 +297,61 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
           vnxt = (r >= lo && r < n) ? vval(p, i, r, h.scale) : 0.0;
         }
       };
-      load_tile(f0);
-      double acc = 0.0;
-      bool dots = false;
+      load_tile(R0, J0);
+      double acc = 0.0;          // y_R partial of row x, this thread's column quarter
+      int Rcur = -1;
+      int R = R0, J = J0;
       for (long long f = f0; f < f1; ++f) {
-        const int R = rb0 + (int)(f / nrb), J = rb0 + (int)(f % nrb);
+        int Rn = R, Jn = J + 1;             // next tile
+        if (Jn > Rn) { ++Rn; Jn = rb0; }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < 16; ++k) tile[(cq + 4 * k) * (TB + 1) + rr] = nxt[k];
-        if (t < TB) vJ[t] = vnxt;
+        if (t < TB) {
+          vJ[t] = vnxt;
+          if (R != Rcur) {
+            const int r = R * TB + t;
+            vR[t] = (r >= lo && r < n) ? vval(p, i, r, h.scale) : 0.0;
+          }
+        }
+        Rcur = R;
         __syncthreads();
-        if (f + 1 < f1) load_tile(f + 1);   // in flight while this tile is used
-        double s = 0.0;
-        if (J <= R) {
+        if (f + 1 < f1) load_tile(Rn, Jn);   // in flight while this tile is used
+        double s1 = 0.0, s2 = 0.0;
 #pragma unroll
-          for (int c = q * 16; c < q * 16 + 16; ++c) s += tile[c * (TB + 1) + x] * vJ[c];
-        } else {
-#pragma unroll
-          for (int r = q * 16; r < q * 16 + 16; ++r) s += tile[x * (TB + 1) + r] * vJ[r];
+        for (int k = 0; k < 16; ++k) {
+          const int c = q + 4 * k;
+          s1 += tile[c * (TB + 1) + x] * vJ[c];          // (A_RJ v_J)[x]
+          if (J < R) s2 += tile[x * (TB + 1) + c] * vR[c];  // (A_RJ^T v_R)[x]
         }
-        acc += s;
-        if (J == rb0) dots = true;
-        if (f + 1 == f1 || (f + 1) % nrb == 0) {
-          // end of this CTA's part of row block R: store its partial of y_R
-          __syncthreads();
-          red[q][x] = acc;
-          if (dots && t < TB) {
-            const int r = R * TB + t;
-            vJ[t] = (r >= lo && r < n) ? vval(p, i, r, h.scale) : 0.0;
+        acc += s1;
+        if (J < R) {
+          s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
+          s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
+          if (q == 0) {
+            const long long ft = (long long)(R - rb0) * (R - rb0 + 1) / 2 + (J - rb0);
+            p.p_t[ft * TB + x] = s2;
           }
-          __syncthreads();
-          if (t < TB) {
-            const int r = R * TB + t;
-            if (r < n) p.p_y[(long long)blockIdx.x * n + r] = red[0][t] + red[1][t] + red[2][t] + red[3][t];
-          }
-          if (dots) {
-            // V^T v and W^T v over row block R: one warp per column, two rows per lane
-            const int warp = t >> 5, lane = t & 31;
-            for (int c = warp; c < 2 * j; c += RT / 32) {
-              const int cc = (c < j) ? c : c - j;
-              const double* col = (c < j) ? A + (long long)(k0 + cc) * ld : p.Wp + (long long)cc * ld;
-              double d2 = 0.0;
-#pragma unroll
-              for (int h2 = 0; h2 < 2; ++h2) {
-                const int rr2 = lane + 32 * h2;
-                const int r = R * TB + rr2;
-                if (r >= lo && r < n) d2 += ldg_cg(col + r) * vJ[rr2];
-              }
-              for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-              if (lane == 0) p.p_vw[(long long)(R - rb0) * (2 * NBP) + c] = d2;
-            }
-          }
+        }
+        if (f + 1 == f1 || J == R) {
+          // end of this CTA's part of row block R
+          double y = acc;
+          y += __shfl_xor_sync(0xffffffffu, y, 1);
+          y += __shfl_xor_sync(0xffffffffu, y, 2);
+          const int r = R * TB + x;
+          if (q == 0 && r < n) p.p_y[(long long)blockIdx.x * n + r] = y;
           acc = 0.0;
-          dots = false;
         }
+        R = Rn;
+        J = Jn;
       }
     }
     if (!grid_sync(p.bar, p.status)) return;
 
     // ---------------- P3: W column ----------------
-    {
-      // sum the per-row-block partials: one warp per column, lanes stride over blocks
-      const int warp = t >> 5, lane = t & 31;
-      for (int c = warp; c < 2 * j; c += RT / 32) {
-        double s = 0.0;
-        for (int R = lane; R < nrb; R += 32) s += ldg_cg(p.p_vw + (long long)R * (2 * NBP) + c);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) { if (c < j) vtv[c] = s; else wtv[c - j] = s; }
-      }
+    for (int c = t; c < 2 * j; c += blockDim.x) {
+      const double v = ldg_cg(p.vwf + c);
+      if (c < j) vtv[c] = v; else wtv[c - j] = v;
     }
     __syncthreads();
     const int n3 = ceil_div_d(n - i - 1, RC);
@@ -311,25 +359,33 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
       const int r = lo + ch * RC + rl;
       double y = 0.0;
       if (r < n) {
-        // partials of y_r from the CTAs whose tile ranges cover row block R
-        const long long T = (long long)nrb * nrb;
-        const long long fa = (long long)(r / TB - rb0) * nrb, fb = fa + nrb - 1;
+        // y_r = (direct partials of the CTAs whose ranges cover row block R)
+        //     + (transposed partials of the tiles (R', R) below it)
+        const int Rr = r / TB, a = Rr - rb0;
+        const long long T = (long long)nrb * (nrb + 1) / 2;
+        const long long fa = (long long)a * (a + 1) / 2, fb = fa + a;
         const int ca = (int)(((fa + 1) * gridDim.x - 1) / T), cb = (int)(((fb + 1) * gridDim.x - 1) / T);
-        for (int c = ca + q4; c <= cb; c += 4) {
+        for (int c = ca + q8; c <= cb; c += 8) {
           // CTAs with an empty tile range wrote nothing
           if ((long long)c * T / gridDim.x == (long long)(c + 1) * T / gridDim.x) continue;
           y += ldg_cg(p.p_y + (long long)c * n + r);
         }
 #pragma unroll 4
-        for (int c = q4; c < j; c += 4) {
+        for (int R2 = Rr + 1 + q8; R2 < nrbt; R2 += 8) {
+          const long long ft = (long long)(R2 - rb0) * (R2 - rb0 + 1) / 2 + a;
+          y += ldg_cg(p.p_t + ft * TB + (r - Rr * TB));
+        }
+#pragma unroll 4
+        for (int c = q8; c < j; c += 8) {
           y -= ldg_cg(p.Wp + r + (long long)c * ld) * vtv[c];
           y -= ldg_cg(A + r + (long long)(k0 + c) * ld) * wtv[c];
         }
       }
       y += __shfl_xor_sync(0xffffffffu, y, 1);
       y += __shfl_xor_sync(0xffffffffu, y, 2);
+      y += __shfl_xor_sync(0xffffffffu, y, 4);
       double part = 0.0;
-      if (r < n && q4 == 0) {
+      if (r < n && q8 == 0) {
         const double w = h.tau * y;
         p.Wp[r + (long long)j * ld] = w;
         if (r == lo) p.scal[3] = w;
@@ -412,10 +468,12 @@ void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
   double* base = w.part;
   p.p_ss = base;   base += ceil_div(n, RC) + 1;
   p.p_wv = base;   base += ceil_div(n, RC) + 1;
-  p.p_vw = base;   base += (long long)nrbt * 2 * NBP;
+  p.p_vw = base;   base += ((long long)ceil_div(n, RC) + 1) * 2 * NBP;
+  p.vwf = base;    base += 2 * NBP;
   p.VW = base;     base += (long long)n * 2 * NBP;
   p.WV = base;     base += (long long)n * 2 * NBP;
   p.bar = reinterpret_cast<GridBar*>(base);   base += 2;
+  p.p_t = base;    base += (long long)nrbt * (nrbt + 1) / 2 * TB;
   p.p_y = base;
   const int cap = g_num_sms * g_coop_blocks_per_sm;
   const int ncols = n - 1;
@@ -424,8 +482,9 @@ void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
     const int k1 = k0 + nbp;
     p.k0 = k0; p.nbp = nbp; p.k1 = k1;
     const int nrb = nrbt - (k0 + 1) / TB;
-    const long long tiles = (long long)nrb * nrb;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(cap, std::max<long long>(tiles, ceil_div(n - k0, RC))));
+    const long long tiles = (long long)nrb * (nrb + 1) / 2;
+    const int grid = (int)std::max<long long>(2 * NBP / (RT / 32),
+                                               std::min<long long>(cap, std::max<long long>(tiles, ceil_div(n - k0, RC))));
     {
       KScope ks(ex, MOLGW_K_TRIDIAG_PANEL, 1);
       cudaMemsetAsync(p.bar, 0, sizeof(GridBar), ex.st);

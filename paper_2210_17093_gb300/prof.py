@@ -1,0 +1,72 @@
+"""Small drivers to profile the library's kernels (e.g. under ncu).
+
+    python -m paper_2210_17093_gb300.prof eigh N [REPS]
+        float64 symmetric eigensolve of a random N x N matrix (tridiagonalisation,
+        bisection, twisted vectors, full back-transformation) through molgw_b200_eigh;
+    python -m paper_2210_17093_gb300.prof qsgw NB NO NA PRECISION [REPS]
+        qsGW iterations of one synthetic molecule (seed 1) at the given precision.
+
+Each prints the per-kernel-class event times of every repetition.
+"""
+from __future__ import annotations
+
+import os
+import sys
+import time
+
+
+def _stats(ctx):
+    return {k: round(v[1], 2) for k, v in ctx.kernel_stats(reset=True).items() if v[0]}
+
+
+def eigh(n: int, reps: int = 1) -> None:
+    import torch
+
+    from . import Context, FLAG_KTIMING
+    g = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randn(n, n, dtype=torch.float64, device="cuda", generator=g)
+    A = (A + A.T).contiguous()
+    w = torch.empty(n, dtype=torch.float64, device="cuda")
+    Z = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    with Context(stream=torch.cuda.current_stream(), flags=FLAG_KTIMING) as ctx:
+        for r in range(reps):
+            ctx.kernel_stats(reset=True)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            ctx.eigh(A, w, Z)
+            torch.cuda.synchronize()
+            print(f"eigh n={n} rep {r}: {(time.perf_counter() - t) * 1e3:.1f} ms", _stats(ctx), flush=True)
+
+
+def qsgw(nb: int, no: int, na: int, precision: str, reps: int = 2) -> None:
+    import numpy as np
+    import torch
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import synthetic as sy
+
+    from . import Context, FLAG_KTIMING
+    m = sy.molecule(nb, no, na, 1)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    with Context(precision=precision, stream=torch.cuda.current_stream(), flags=FLAG_KTIMING, eta=sy.ETA) as ctx:
+        ctx.set_ri(0, nb, na, d(m["L"]))
+        ctx.set_orbitals(0, no, d(m["eps"]), d(m["C"]))
+        for r in range(reps):
+            ctx.kernel_stats(reset=True)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            ctx.qs_step(0)
+            ctx.sync()
+            print(f"qs_step nb={nb} {precision} rep {r}: {(time.perf_counter() - t) * 1e3:.1f} ms", _stats(ctx),
+                  flush=True)
+
+
+if __name__ == "__main__":
+    a = sys.argv[1:]
+    if a and a[0] == "eigh":
+        eigh(int(a[1]), int(a[2]) if len(a) > 2 else 1)
+    elif a and a[0] == "qsgw":
+        qsgw(int(a[1]), int(a[2]), int(a[3]), a[4], int(a[5]) if len(a) > 5 else 2)
+    else:
+        print(__doc__)
+        sys.exit(2)
