@@ -44,6 +44,15 @@ WORKLOADS = {
 # float64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 # (NVIDIA lists 1.25 TFLOP/s FP64 for this part; a register-only DFMA loop measured 1.20).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes the tridiagonalisation panel kernel moves per algorithmic byte (the lower
+# triangle of the trailing matrix once per column), from one ncu capture of the panel of
+# columns 192..255 at n = 6400: 10.13 GB measured for 9.77 GB algorithmic.
+PANEL_TRAFFIC_RATIO = 10.13 / 9.77
+
+
+def panel_bytes(n):
+    """Algorithmic DRAM bytes of one reduction of M: sum over columns of the lower triangle."""
+    return sum(4.0 * (n - i - 1) ** 2 for i in range(n - 1))
 
 
 def workload_flops(nb, no, na):
@@ -314,6 +323,10 @@ def run_ours(args, wl):
     nl, kms = kstats[dominant]
     dom_flops = flops.get(dominant)
     achieved = dom_flops * args.steps / (kms / 1e3) / 1e12 if (dom_flops and kms > 0) else None
+    traffic = None
+    if dominant == "tridiag_panel" and nl:
+        # measured bytes per algorithmic byte x algorithmic bytes, per launch (all panel launches)
+        traffic = PANEL_TRAFFIC_RATIO * panel_bytes(n) * args.steps / nl
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": False,
@@ -325,7 +338,9 @@ def run_ours(args, wl):
         "roofline": {
             "kernel": dominant, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-            "traffic": None, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+            "traffic": traffic, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+            "traffic_source": "ncu dram__bytes_read+write of one panel launch (n=6400, columns 192-255), "
+                              "scaled by the algorithmic bytes per launch",
             "launches": nl, "event_ms": kms,
         },
         "stages_ms": {k: round(v[1], 3) for k, v in breakdown.items() if v[0]},
