@@ -89,6 +89,8 @@ int read_status(molgw_ctx c) {
   return s;
 }
 
+bool use_tc_ctx(molgw_ctx c) { return c->opts.precision != MOLGW_PREC_FP64; }
+
 int ensure_eig(molgw_ctx c, int n, int ncols) {
   if (n <= c->eig_n && ncols <= c->eig_cols) return MOLGW_OK;
   const int nn = std::max(n, c->eig_n), nc = std::max(ncols, c->eig_cols);
@@ -99,17 +101,44 @@ int ensure_eig(molgw_ctx c, int n, int ncols) {
   return MOLGW_OK;
 }
 
+// Packed residue buffers of the float64 path, when the device has room for them
+// (they halve the residue flops); otherwise the blocked route without them is used.
+void ensure_packed(molgw_ctx c, int nb, int na, long long nov) {
+  Scratch& s = c->scr;
+  const size_t npair = (size_t)nb * (nb + 1) / 2;
+  const size_t want_w = npair * nov, want_b = npair * na;
+  if (want_w <= s.wpk_cap && want_b <= s.bpt_cap) return;
+  cudaStreamSynchronize(c->st);
+  if (s.pk_base) cudaFree(s.pk_base);
+  s.pk_base = nullptr; s.wpk = s.bpt = nullptr; s.wpk_cap = s.bpt_cap = 0;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); return; }
+  const size_t bytes = (want_w + want_b) * sizeof(double);
+  if (bytes > fr / 3) return;
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return; }
+  s.pk_base = p;
+  s.wpk = (double*)p;
+  s.bpt = s.wpk + want_w;
+  s.wpk_cap = want_w;
+  s.bpt_cap = want_b;
+}
+
 int ensure_scratch(molgw_ctx c, int nb, int na, long long nov) {
   Scratch& s = c->scr;
   const size_t want_w = std::max<size_t>((size_t)nb * nov,
                                          std::min<size_t>((size_t)nb * nb * nov, (size_t)48 << 20));
+  if (!use_tc_ctx(c)) ensure_packed(c, nb, na, nov);
   if (nb <= s.nb_cap && na <= s.na_cap && want_w <= s.wblk_cap) return MOLGW_OK;
   cudaStreamSynchronize(c->st);
   const int nbc = std::max(nb, s.nb_cap), nac = std::max(na, s.na_cap);
   const size_t wc = std::max(want_w, s.wblk_cap);
   const size_t skc = (size_t)16 << 20;
   if (s.base) cudaFree(s.base);
+  void* pk = s.pk_base; double* wpk = s.wpk; double* bpt = s.bpt;
+  const size_t wcap = s.wpk_cap, bcap = s.bpt_cap;
   s = Scratch{};
+  s.pk_base = pk; s.wpk = wpk; s.bpt = bpt; s.wpk_cap = wcap; s.bpt_cap = bcap;
   const size_t nn = (size_t)nbc * nbc;
   const size_t total = nac + skc + 2 * wc + 3 * nn;
   void* p = nullptr;
@@ -537,6 +566,7 @@ int molgw_b200_destroy(molgw_ctx c) {
     for (auto& m : c->mols) { free_all(m.ri_allocs); free_all(m.orb_allocs); }
     for (auto& t : c->tcb) { free_all(t.ri_allocs); free_all(t.orb_allocs); }
     if (c->scr.base) cudaFree(c->scr.base);
+    if (c->scr.pk_base) cudaFree(c->scr.pk_base);
     eig_work_free(c->eig);
     cudaFree(c->d_status);
     cudaFreeHost(c->h_status);

@@ -117,6 +117,49 @@ __global__ void k_apply_g(const double* Wb, const double* eps, const double* Om,
   }
 }
 
+// Packed pairs m <= p, row-major over m: k(m, p) = m*nb - m(m-1)/2 + (p - m).
+__device__ __forceinline__ long long pair_index(int m, int p, int nb) {
+  if (m > p) { const int t = m; m = p; p = t; }
+  return (long long)m * nb - (long long)m * (m - 1) / 2 + (p - m);
+}
+
+// BpT[P][k] = B[P][m][p] for the packed pairs k = (m <= p).
+__global__ void k_gather_bpair(const double* B, int nb, int na, double* BpT) {
+  const long long npair = (long long)nb * (nb + 1) / 2;
+  const long long nn = (long long)nb * nb;
+  const long long total = npair * na;
+  for (long long idx = gtid(); idx < total; idx += gstride()) {
+    const long long k = idx % npair;
+    const int P = (int)(idx / npair);
+    // row m of the packed triangle holding k
+    int m = (int)((2.0 * nb + 1.0 - sqrt((2.0 * nb + 1.0) * (2.0 * nb + 1.0) - 8.0 * (double)k)) * 0.5);
+    if (m < 0) m = 0;
+    while (m > 0 && (long long)m * nb - (long long)m * (m - 1) / 2 > k) --m;
+    while ((long long)(m + 1) * nb - (long long)(m + 1) * m / 2 <= k) ++m;
+    const int p = m + (int)(k - ((long long)m * nb - (long long)m * (m - 1) / 2));
+    BpT[idx] = B[(long long)P * nn + (long long)m * nb + p];
+  }
+}
+
+// Wb[p][mm][s] = w^s_{p m} from the packed residues (w symmetric in p, m), and
+// Pb = Wb * g(eps_p - eps_m -/+ Omega_s) (float64 subtraction), m = m0 + mm.
+__global__ void k_gather_w_apply_g(const double* Wpk, const double* eps, const double* Om, int nb, int no, int m0,
+                                   int mb, int nov, double eta, double* Wb, double* Pb) {
+  const long long K = (long long)mb * nov;
+  const long long total = (long long)nb * K;
+  const double eta2 = eta * eta;
+  for (long long idx = gtid(); idx < total; idx += gstride()) {
+    const int p = (int)(idx / K);
+    const long long k = idx % K;
+    const int mm = (int)(k / nov), sidx = (int)(k % nov);
+    const int m = m0 + mm;
+    const double w = Wpk[pair_index(m, p, nb) * nov + sidx];
+    const double x = (m < no) ? (eps[p] - eps[m]) + Om[sidx] : (eps[p] - eps[m]) - Om[sidx];
+    Wb[idx] = w;
+    Pb[idx] = w * (x / (x * x + eta2));
+  }
+}
+
 // out = 1/2 (S + S^T)
 __global__ void k_symmetrize(const double* S, int n, double* out) {
   const long long nn = (long long)n * n;
@@ -299,19 +342,39 @@ void stage_sigma(Exec& ex, MolBuf& m, Scratch& s, double eta) {
   const int nb = m.nb, na = m.na, no = m.no;
   const int nov = (int)m.nov;
   const long long nn = (long long)nb * nb;
+  const long long npair = (long long)nb * (nb + 1) / 2;
   const int mb = std::max(1, std::min(nb, (int)(s.wblk_cap / ((long long)nb * nov))));
+  const bool packed = s.wpk && s.wpk_cap >= npair * nov && s.bpt_cap >= npair * na;
+  if (packed) {
+    // w^s_pm = w^s_mp: one GEMM over the pairs m <= p (half of the residue flops)
+    {
+      KScope ks(ex, MOLGW_K_SIGMA);
+      k_gather_bpair<<<grid_for(npair * na), 256, 0, ex.st>>>(m.B, nb, na, s.bpt);
+    }
+    GemmF64 g;
+    g.M = (int)npair; g.N = nov; g.K = na;
+    g.A = s.bpt; g.sa_m = 1; g.sa_k = npair;
+    g.B = m.R; g.sb_k = nov; g.sb_n = 1;
+    g.C = s.wpk; g.sc_m = nov; g.sc_n = 1;
+    g.kclass = MOLGW_K_SIGMA;
+    gemm_f64(ex, g);
+  }
   for (int m0 = 0; m0 < nb; m0 += mb) {
     const int cnt = std::min(mb, nb - m0);
     const long long K = (long long)cnt * nov;
-    // Wb[p][mm][s] = sum_P B[P][m][p] R[P][s]
-    GemmF64 g;
-    g.M = nb; g.N = nov; g.K = na; g.batch = cnt;
-    g.A = m.B + (long long)m0 * nb; g.sa_m = 1; g.sa_k = nn; g.sa_b = nb;
-    g.B = m.R; g.sb_k = nov; g.sb_n = 1; g.sb_b = 0;
-    g.C = s.wblk; g.sc_m = K; g.sc_n = 1; g.sc_b = nov;
-    g.kclass = MOLGW_K_SIGMA;
-    gemm_f64(ex, g);
-    {
+    if (packed) {
+      KScope ks(ex, MOLGW_K_SIGMA);
+      k_gather_w_apply_g<<<grid_for(nb * K), 256, 0, ex.st>>>(s.wpk, m.eps, m.Om, nb, no, m0, cnt, nov, eta, s.wblk,
+                                                               s.pblk);
+    } else {
+      // Wb[p][mm][s] = sum_P B[P][m][p] R[P][s]
+      GemmF64 g;
+      g.M = nb; g.N = nov; g.K = na; g.batch = cnt;
+      g.A = m.B + (long long)m0 * nb; g.sa_m = 1; g.sa_k = nn; g.sa_b = nb;
+      g.B = m.R; g.sb_k = nov; g.sb_n = 1; g.sb_b = 0;
+      g.C = s.wblk; g.sc_m = K; g.sc_n = 1; g.sc_b = nov;
+      g.kclass = MOLGW_K_SIGMA;
+      gemm_f64(ex, g);
       KScope ks(ex, MOLGW_K_SIGMA);
       k_apply_g<<<grid_for(nb * K), 256, 0, ex.st>>>(s.wblk, m.eps, m.Om, nb, no, m0, cnt, nov, eta, s.pblk);
     }

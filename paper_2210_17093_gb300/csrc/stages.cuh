@@ -54,6 +54,10 @@ struct Scratch {
   double *S = nullptr, *H = nullptr, *U = nullptr;  // nb x nb
   int nb_cap = 0, na_cap = 0;
   void* base = nullptr;
+  // packed residues w over the pairs m <= p (float64 path), and the packed B^T
+  double *wpk = nullptr, *bpt = nullptr;
+  size_t wpk_cap = 0, bpt_cap = 0;
+  void* pk_base = nullptr;
 };
 
 void dev_copy(Exec& ex, const double* a, double* b, long long n);
