@@ -31,6 +31,10 @@
  *     out) are latched in a device status word and returned by the next call
  *     that synchronises (a call with a host output, molgw_b200_sync or
  *     molgw_b200_destroy).
+ *   - Batches: mol = -1 runs every ready molecule.  The molecules are spread
+ *     over concurrent streams of the context (opts.lanes), which fork from the
+ *     context stream and are joined back into it before the call returns, so
+ *     that all work stays ordered on the context stream.
  *   - A context is not thread-safe; distinct contexts are independent.
  */
 #ifndef MOLGW_GB300_H
@@ -75,7 +79,9 @@ enum molgw_precision {
 enum molgw_flags {
   MOLGW_FLAG_FULL_XPY = 1u << 0, /* keep the full n_ov x n_ov (X+Y) so molgw_b200_rpa can return it */
   MOLGW_FLAG_KTIMING = 1u << 1,  /* record CUDA events around kernels for molgw_b200_kernel_stats  */
-  MOLGW_FLAG_GRAPH = 1u << 2,    /* replay each molecule's qs_step from a captured CUDA graph        */
+  MOLGW_FLAG_GRAPH = 1u << 2,    /* qs_step from the state a qs_step leaves: captured once into a CUDA
+                                    graph (all lanes of mol = -1 in one graph) and replayed while the
+                                    buffers and the set of molecules stay the same                  */
   MOLGW_FLAG_USE_STREAM = 1u << 3, /* run on opts.stream even when it is NULL (the legacy default stream) */
   MOLGW_FLAG_TC_AB = 1u << 4       /* with BF16X3/TF32X3: stages (a) and (b) on the tensor cores too */
 };
@@ -89,6 +95,8 @@ typedef struct {
   void* stream;        /* cudaStream_t to run on; NULL = a stream the context owns,
                           unless MOLGW_FLAG_USE_STREAM asks for the legacy default stream */
   uint32_t flags;      /* enum molgw_flags                                          */
+  int32_t lanes;       /* mol = -1: molecules run on up to this many concurrent streams
+                          (0 = 8, the maximum), assigned longest pass first          */
 } molgw_opts;
 
 /* Create a context.  Returns MOLGW_E_ARG for a bad opts, MOLGW_E_CUDA if the
@@ -196,8 +204,14 @@ int molgw_b200_kernel_stats(molgw_ctx ctx, int64_t* launches, double* ms, int re
  * Synchronises and returns the latched device status. */
 int molgw_b200_set_timing(molgw_ctx ctx, uint32_t class_mask);
 
-/* Number of device kernels this context has launched since creation. */
+/* Number of device kernels this context has launched since creation (a graph
+ * replay counts the kernels the graph holds). */
 int64_t molgw_b200_launch_count(molgw_ctx ctx);
+
+/* Library extension (the paper has no counterpart): number of qs_step calls
+ * served by replaying a captured graph (MOLGW_FLAG_GRAPH); -1 once a capture
+ * failed and the context went back to issuing the launches one by one. */
+int64_t molgw_b200_graph_replays(molgw_ctx ctx);
 
 /* Free every resource of the context (synchronises first).  Returns the
  * latched device status.  ctx may be NULL. */

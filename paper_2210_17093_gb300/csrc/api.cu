@@ -7,6 +7,25 @@
 
 using namespace molgw;
 
+// One execution lane: a stream with its own scratch, eigensolver workspace and
+// tensor-core operand arena.  Lane 0 runs on the context stream; a batch call
+// (mol = -1) forks further lanes from it and joins them back with events.
+struct Lane {
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  cudaEvent_t done = nullptr;
+  Exec ex;
+  Scratch scr;
+  EigWork eig;
+  int eig_n = 0, eig_cols = 0;
+  TcBufs tco;                 // orbital-size split operands, carved per molecule
+  void* tco_base = nullptr;
+  size_t tco_cap = 0;         // doubles
+  size_t pk_fail = 0;         // packed-residue request that did not fit (not retried)
+};
+
+constexpr int kMaxLanes = 8;
+
 struct molgw_ctx_s {
   molgw_opts opts{};
   int device = 0;
@@ -15,12 +34,19 @@ struct molgw_ctx_s {
   int* d_status = nullptr;
   int* h_status = nullptr;   // pinned mirror
   KTimer timer;
-  Exec ex;
   std::vector<MolBuf> mols;
-  std::vector<TcBufs> tcb;   // split operands of the tensor-core path (precision != FP64)
-  Scratch scr;
-  EigWork eig;
-  int eig_n = 0, eig_cols = 0;
+  std::vector<TcBufs> tcb;   // per molecule: split L of the tensor-core path (MOLGW_FLAG_TC_AB)
+  std::vector<Lane> lanes;   // lanes[0] is the context stream
+  cudaEvent_t fork = nullptr;
+  uint64_t gen = 1;          // bumped whenever a buffer a captured graph may use is (re)allocated
+  // captured qs_step (MOLGW_FLAG_GRAPH)
+  cudaGraphExec_t gexec = nullptr;
+  int graph_mol = -2;
+  uint64_t graph_gen = 0;
+  std::vector<char> graph_set;   // molecules the graph covers (mol = -1)
+  int64_t graph_launches[MOLGW_K_COUNT] = {0};
+  bool graph_off = false;        // capture failed once: run eagerly from then on
+  int64_t graph_replays = 0;
 };
 
 namespace {
@@ -89,34 +115,87 @@ int read_status(molgw_ctx c) {
   return s;
 }
 
-bool use_tc_ctx(molgw_ctx c) { return c->opts.precision != MOLGW_PREC_FP64; }
+bool use_tc(molgw_ctx c) { return c->opts.precision != MOLGW_PREC_FP64; }
+bool use_tc_ab(molgw_ctx c) { return use_tc(c) && (c->opts.flags & MOLGW_FLAG_TC_AB); }
+int tc_prec(molgw_ctx c) {
+  if (c->opts.precision == MOLGW_PREC_TF32X3) return TC_TF32X3;
+  if (c->opts.precision == MOLGW_PREC_BF16X6) return TC_BF16X6;
+  return TC_BF16X3;
+}
 
-int ensure_eig(molgw_ctx c, int n, int ncols) {
-  if (n <= c->eig_n && ncols <= c->eig_cols) return MOLGW_OK;
-  const int nn = std::max(n, c->eig_n), nc = std::max(ncols, c->eig_cols);
-  cudaStreamSynchronize(c->st);
-  int r = eig_work_alloc(c->eig, nn, nc);
-  if (r) { c->eig_n = c->eig_cols = 0; return r; }
-  c->eig_n = nn; c->eig_cols = nc;
+// m values per self-energy block: w and g*w (hi and lo each) within about 1 GB
+int tc_mblock(int prec, int nb, long long nov) {
+  const long long per_m = 2LL * tc_slices(prec) * nb * tc_pad(nov, prec) * tc_elem_bytes(prec);
+  return (int)std::max<long long>(1, std::min<long long>(nb, (1LL << 30) / std::max<long long>(per_m, 1)));
+}
+
+bool mol_ok(molgw_ctx c, int mol) { return c && mol >= 0 && mol < (int)c->mols.size(); }
+
+// Lane k, created on first use (lane 0 is the context stream).
+int lane_get(molgw_ctx c, int k, Lane** out) {
+  while ((int)c->lanes.size() <= k) {
+    Lane l;
+    const int idx = (int)c->lanes.size();
+    if (idx == 0) {
+      l.st = c->st;
+    } else {
+      if (cudaStreamCreateWithFlags(&l.st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return MOLGW_E_CUDA; }
+      l.own_stream = true;
+      if (cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamDestroy(l.st);
+        return MOLGW_E_CUDA;
+      }
+    }
+    l.ex.st = l.st;
+    l.ex.status = c->d_status;
+    l.ex.timer = &c->timer;
+    c->lanes.push_back(l);
+  }
+  *out = &c->lanes[k];
+  return MOLGW_OK;
+}
+
+void lane_free(Lane& l) {
+  if (l.scr.base) cudaFree(l.scr.base);
+  if (l.scr.pk_base) cudaFree(l.scr.pk_base);
+  if (l.tco_base) cudaFree(l.tco_base);
+  eig_work_free(l.eig);
+  if (l.done) cudaEventDestroy(l.done);
+  if (l.own_stream) cudaStreamDestroy(l.st);
+}
+
+int ensure_eig(molgw_ctx c, Lane& l, int n, int ncols) {
+  if (n <= l.eig_n && ncols <= l.eig_cols) return MOLGW_OK;
+  if (l.ex.capturing) return MOLGW_E_STATE;
+  const int nn = std::max(n, l.eig_n), nc = std::max(ncols, l.eig_cols);
+  cudaStreamSynchronize(l.st);
+  ++c->gen;
+  int r = eig_work_alloc(l.eig, nn, nc);
+  if (r) { l.eig_n = l.eig_cols = 0; return r; }
+  l.eig_n = nn; l.eig_cols = nc;
   return MOLGW_OK;
 }
 
 // Packed residue buffers of the float64 path, when the device has room for them
 // (they halve the residue flops); otherwise the blocked route without them is used.
-void ensure_packed(molgw_ctx c, int nb, int na, long long nov) {
-  Scratch& s = c->scr;
+void ensure_packed(molgw_ctx c, Lane& l, int nb, int na, long long nov) {
+  Scratch& s = l.scr;
   const size_t npair = (size_t)nb * (nb + 1) / 2;
   const size_t want_w = npair * nov, want_b = npair * na;
   if (want_w <= s.wpk_cap && want_b <= s.bpt_cap) return;
-  cudaStreamSynchronize(c->st);
+  if (l.pk_fail && want_w >= l.pk_fail) return;   // did not fit before: stay on the blocked route
+  if (l.ex.capturing) return;
+  cudaStreamSynchronize(l.st);
+  ++c->gen;
   if (s.pk_base) cudaFree(s.pk_base);
   s.pk_base = nullptr; s.wpk = s.bpt = nullptr; s.wpk_cap = s.bpt_cap = 0;
   size_t fr = 0, tot = 0;
-  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); return; }
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); l.pk_fail = want_w; return; }
   const size_t bytes = (want_w + want_b) * sizeof(double);
-  if (bytes > fr / 3) return;
+  if (bytes > fr / 3) { l.pk_fail = want_w; return; }
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return; }
+  if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); l.pk_fail = want_w; return; }
   s.pk_base = p;
   s.wpk = (double*)p;
   s.bpt = s.wpk + want_w;
@@ -124,13 +203,15 @@ void ensure_packed(molgw_ctx c, int nb, int na, long long nov) {
   s.bpt_cap = want_b;
 }
 
-int ensure_scratch(molgw_ctx c, int nb, int na, long long nov) {
-  Scratch& s = c->scr;
+int ensure_scratch(molgw_ctx c, Lane& l, int nb, int na, long long nov) {
+  Scratch& s = l.scr;
   const size_t want_w = std::max<size_t>((size_t)nb * nov,
                                          std::min<size_t>((size_t)nb * nb * nov, (size_t)48 << 20));
-  if (!use_tc_ctx(c)) ensure_packed(c, nb, na, nov);
+  if (!use_tc(c)) ensure_packed(c, l, nb, na, nov);
   if (nb <= s.nb_cap && na <= s.na_cap && want_w <= s.wblk_cap) return MOLGW_OK;
-  cudaStreamSynchronize(c->st);
+  if (l.ex.capturing) return MOLGW_E_STATE;
+  cudaStreamSynchronize(l.st);
+  ++c->gen;
   const int nbc = std::max(nb, s.nb_cap), nac = std::max(na, s.na_cap);
   const size_t wc = std::max(want_w, s.wblk_cap);
   const size_t skc = (size_t)16 << 20;
@@ -155,34 +236,54 @@ int ensure_scratch(molgw_ctx c, int nb, int na, long long nov) {
   return MOLGW_OK;
 }
 
-bool mol_ok(molgw_ctx c, int mol) { return c && mol >= 0 && mol < (int)c->mols.size(); }
-
-bool use_tc(molgw_ctx c) { return c->opts.precision != MOLGW_PREC_FP64; }
-int tc_prec(molgw_ctx c) {
-  if (c->opts.precision == MOLGW_PREC_TF32X3) return TC_TF32X3;
-  if (c->opts.precision == MOLGW_PREC_BF16X6) return TC_BF16X6;
-  return TC_BF16X3;
+// Arena of the orbital-size split operands (tensor-core path).
+int ensure_tco(molgw_ctx c, Lane& l, int nb, int na, long long nov) {
+  if (!use_tc(c)) return MOLGW_OK;
+  const int prec = tc_prec(c);
+  const size_t want = tc_orb_doubles(prec, nb, na, nov, tc_mblock(prec, nb, nov));
+  if (want <= l.tco_cap) return MOLGW_OK;
+  if (l.ex.capturing) return MOLGW_E_STATE;
+  cudaStreamSynchronize(l.st);
+  ++c->gen;
+  if (l.tco_base) cudaFree(l.tco_base);
+  l.tco_base = nullptr;
+  l.tco_cap = 0;
+  if (cudaMalloc(&l.tco_base, want * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    l.tco_base = nullptr;
+    return MOLGW_E_NOMEM;
+  }
+  l.tco_cap = want;
+  return MOLGW_OK;
 }
 
-// m values per self-energy block: w and g*w (hi and lo each) within about 1 GB
-int tc_mblock(int prec, int nb, long long nov) {
-  const long long per_m = 2LL * tc_slices(prec) * nb * tc_pad(nov, prec) * tc_elem_bytes(prec);
-  return (int)std::max<long long>(1, std::min<long long>(nb, (1LL << 30) / std::max<long long>(per_m, 1)));
+// Every buffer one pass of molecule m needs on lane l.
+int lane_fit(molgw_ctx c, Lane& l, const MolBuf& m) {
+  const bool full = (c->opts.flags & MOLGW_FLAG_FULL_XPY) != 0;
+  int r = ensure_scratch(c, l, m.nb, m.na, m.nov);
+  if (!r) r = ensure_eig(c, l, (int)std::max<long long>(m.nov, m.nb),
+                         std::max<int>(std::max(m.na, m.nb), full ? (int)m.nov : 0));
+  if (!r) r = ensure_tco(c, l, m.nb, m.na, m.nov);
+  return r;
 }
 
-// Run the pass of one molecule up to a stage: 'b' (M), 'c' (rpa), 'e' (sigma), 'f' (qs step).
-int run_pass(molgw_ctx c, int mol, char upto) {
+// Run the pass of one molecule on lane l up to a stage: 'b' (M), 'c' (rpa),
+// 'e' (sigma), 'f' (qs step).
+int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
   MolBuf& m = c->mols[mol];
   if (!m.have_ri || !m.have_orb) return MOLGW_E_STATE;
   const bool full = (c->opts.flags & MOLGW_FLAG_FULL_XPY) != 0;
-  int r = ensure_scratch(c, m.nb, m.na, m.nov);
-  if (!r) r = ensure_eig(c, (int)std::max<long long>(m.nov, m.nb),
-                         std::max<int>(std::max(m.na, m.nb), full ? (int)m.nov : 0));
+  int r = lane_fit(c, l, m);
   if (r) return r;
-  Exec& ex = c->ex;
+  Exec& ex = l.ex;
   const bool tc = use_tc(c);
-  const bool tc_ab = tc && (c->opts.flags & MOLGW_FLAG_TC_AB);
-  TcBufs& tb = c->tcb[mol];
+  const bool tc_ab = use_tc_ab(c);
+  TcBufs& tb = l.tco;
+  if (tc) {
+    const int prec = tc_prec(c);
+    tc_bufs_carve(tb, prec, m.nb, m.na, m.nov, tc_mblock(prec, m.nb, m.nov), (double*)l.tco_base);
+    tb.L = c->tcb[mol].L;
+  }
   if (!m.b_valid) {
     if (tc_ab) {
       r = stage_ri_mo_transform_tc(ex, m, tb);
@@ -193,7 +294,7 @@ int run_pass(molgw_ctx c, int mol, char upto) {
     m.b_valid = m.have_b = true;
   }
   if (!m.h_ready) {
-    stage_j_sigx(ex, m, c->scr);
+    stage_j_sigx(ex, m, l.scr);
     derive_h_from_hf(ex, m);
     m.jx_valid = m.have_jx = true;
     m.h_ready = true;
@@ -215,30 +316,212 @@ int run_pass(molgw_ctx c, int mol, char upto) {
     } else {
       stage_rpa_build(ex, m);
     }
-    stage_rpa_eigensolve(ex, m, c->eig, c->scr, full);
+    stage_rpa_eigensolve(ex, m, l.eig, l.scr, full);
     m.rpa_valid = m.have_rpa = true;
   }
   if (upto >= 'e' && !m.sigma_valid) {
     if (!m.jx_valid) {
-      stage_j_sigx(ex, m, c->scr);
+      stage_j_sigx(ex, m, l.scr);
       m.jx_valid = m.have_jx = true;
     }
     if (tc) {
-      r = stage_sigma_tc(ex, m, tb, c->scr, c->opts.eta);
+      r = stage_sigma_tc(ex, m, tb, l.scr, c->opts.eta);
       if (r) return r;
     } else {
-      stage_sigma(ex, m, c->scr, c->opts.eta);
+      stage_sigma(ex, m, l.scr, c->opts.eta);
     }
     m.sigma_valid = m.have_sigma = true;
   }
   if (upto == 'f') {
-    stage_qs_update(ex, m, c->eig, c->scr);
+    stage_qs_update(ex, m, l.eig, l.scr);
     m.b_valid = m.jx_valid = m.rpa_valid = m.sigma_valid = false;
   }
   return launch_status();
 }
 
 bool ready(const MolBuf& m) { return m.have_ri && m.have_orb; }
+
+// The state a qs_step leaves behind: the next qs_step issues exactly the same
+// launches, so a graph captured from one replays the next.
+bool steady(const MolBuf& m) {
+  return ready(m) && m.h_ready && !m.b_valid && !m.jx_valid && !m.rpa_valid && !m.sigma_valid;
+}
+
+// Relative cost of one pass: the n_ov^3 eigensolve and the residue contraction.
+double pass_cost(const MolBuf& m) {
+  const double n = (double)m.nov;
+  return n * n * n + 2.0 * m.nb * (double)m.nb * n * m.na;
+}
+
+struct Plan {
+  std::vector<std::vector<int>> lane_mols;   // molecules of each lane, in issue order
+};
+
+// Longest-processing-time-first assignment of molecules to at most `lanes` lanes.
+Plan plan_batch(molgw_ctx c, const std::vector<int>& mols) {
+  int want = c->opts.lanes > 0 ? c->opts.lanes : kMaxLanes;
+  want = std::max(1, std::min(std::min(want, kMaxLanes), (int)mols.size()));
+  std::vector<int> order(mols);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return pass_cost(c->mols[a]) > pass_cost(c->mols[b]); });
+  Plan p;
+  p.lane_mols.resize(want);
+  std::vector<double> load(want, 0.0);
+  for (int k : order) {
+    int best = 0;
+    for (int j = 1; j < want; ++j)
+      if (load[j] < load[best]) best = j;
+    p.lane_mols[best].push_back(k);
+    load[best] += pass_cost(c->mols[k]);
+  }
+  return p;
+}
+
+// Create the lanes of a plan and size their buffers for their molecules (no
+// allocation happens while the passes are issued).
+int plan_fit(molgw_ctx c, const Plan& p) {
+  for (int k = 0; k < (int)p.lane_mols.size(); ++k) {
+    Lane* l = nullptr;
+    int r = lane_get(c, k, &l);
+    if (r) return r;
+    for (int mol : p.lane_mols[k]) {
+      r = lane_fit(c, c->lanes[k], c->mols[mol]);
+      if (r) return r;
+    }
+  }
+  return MOLGW_OK;
+}
+
+// Issue the passes of a plan: the lanes fork from the context stream, each runs
+// its molecules in order (issued round robin across lanes), and the context
+// stream waits for all of them.  With several lanes each persistent panel
+// launch is limited to an equal share of the co-resident CTAs.
+int issue_plan(molgw_ctx c, const Plan& p, char upto) {
+  const int nl = (int)p.lane_mols.size();
+  const int share = nl > 1 ? tridiag_coop_capacity() / nl : 0;
+  for (int k = 0; k < nl; ++k) c->lanes[k].ex.coop_cap = share;
+  if (nl > 1) {
+    cudaEventRecord(c->fork, c->st);
+    for (int k = 1; k < nl; ++k) cudaStreamWaitEvent(c->lanes[k].st, c->fork, 0);
+  }
+  int r = MOLGW_OK;
+  size_t depth = 0;
+  for (const auto& v : p.lane_mols) depth = std::max(depth, v.size());
+  for (size_t i = 0; i < depth && !r; ++i)
+    for (int k = 0; k < nl && !r; ++k)
+      if (i < p.lane_mols[k].size()) r = run_pass(c, c->lanes[k], p.lane_mols[k][i], upto);
+  if (nl > 1) {
+    // join even after an error, so that no lane is left outside the context stream's order
+    for (int k = 1; k < nl; ++k) {
+      cudaEventRecord(c->lanes[k].done, c->lanes[k].st);
+      cudaStreamWaitEvent(c->st, c->lanes[k].done, 0);
+    }
+  }
+  for (int k = 0; k < nl; ++k) c->lanes[k].ex.coop_cap = 0;
+  if (!r) r = launch_status();
+  return r;
+}
+
+void graph_drop(molgw_ctx c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->graph_mol = -2;
+  c->graph_gen = 0;
+  c->graph_set.clear();
+}
+
+std::vector<char> mol_set(molgw_ctx c, const std::vector<int>& mols) {
+  std::vector<char> v(c->mols.size(), 0);
+  for (int k : mols) v[k] = 1;
+  return v;
+}
+
+struct Flags {
+  bool h_ready, b_valid, jx_valid, rpa_valid, sigma_valid, have_b, have_rpa, have_jx, have_sigma;
+};
+Flags get_flags(const MolBuf& m) {
+  return {m.h_ready, m.b_valid, m.jx_valid, m.rpa_valid, m.sigma_valid, m.have_b, m.have_rpa, m.have_jx, m.have_sigma};
+}
+void put_flags(MolBuf& m, const Flags& f) {
+  m.h_ready = f.h_ready; m.b_valid = f.b_valid; m.jx_valid = f.jx_valid; m.rpa_valid = f.rpa_valid;
+  m.sigma_valid = f.sigma_valid; m.have_b = f.have_b; m.have_rpa = f.have_rpa; m.have_jx = f.have_jx;
+  m.have_sigma = f.have_sigma;
+}
+
+// Capture the qs_step passes of a plan into c->gexec.  Returns false (and turns
+// graphs off for the context) when the capture or the instantiation fails; the
+// caller then issues the passes directly.
+bool graph_capture(molgw_ctx c, int mol, const std::vector<int>& mols, const Plan& p) {
+  graph_drop(c);
+  std::vector<Flags> saved;
+  for (int k : mols) saved.push_back(get_flags(c->mols[k]));
+  int64_t before[MOLGW_K_COUNT];
+  for (int k = 0; k < MOLGW_K_COUNT; ++k) before[k] = c->timer.launches[k];
+  const int64_t total_before = c->timer.total_launches;
+  bool ok = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  cudaGraph_t g = nullptr;
+  if (ok) {
+    for (auto& l : c->lanes) l.ex.capturing = true;
+    const int r = issue_plan(c, p, 'f');
+    for (auto& l : c->lanes) l.ex.capturing = false;
+    const cudaError_t e = cudaStreamEndCapture(c->st, &g);
+    ok = (r == MOLGW_OK) && e == cudaSuccess && g != nullptr;
+  }
+  for (size_t i = 0; i < mols.size(); ++i) put_flags(c->mols[mols[i]], saved[i]);
+  for (int k = 0; k < MOLGW_K_COUNT; ++k) {
+    c->graph_launches[k] = c->timer.launches[k] - before[k];
+    c->timer.launches[k] = before[k];
+  }
+  c->timer.total_launches = total_before;
+  if (ok) ok = cudaGraphInstantiate(&c->gexec, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();
+    c->gexec = nullptr;
+    c->graph_off = true;
+    return false;
+  }
+  c->graph_mol = mol;
+  c->graph_gen = c->gen;
+  c->graph_set = mol_set(c, mols);
+  return true;
+}
+
+// Stages up to `upto` for molecule `mol`, or for every ready molecule (mol = -1)
+// spread over concurrent lanes.  With MOLGW_FLAG_GRAPH a qs_step from the steady
+// state is captured once and replayed while the buffers and the set of molecules
+// stay the same.
+int run_mols(molgw_ctx c, int mol, char upto) {
+  std::vector<int> mols;
+  if (mol == -1) {
+    for (int k = 0; k < (int)c->mols.size(); ++k)
+      if (ready(c->mols[k])) mols.push_back(k);
+    if (mols.empty()) return MOLGW_E_STATE;
+  } else {
+    if (!ready(c->mols[mol])) return MOLGW_E_STATE;
+    mols.push_back(mol);
+  }
+  Plan p = plan_batch(c, mols);
+  int r = plan_fit(c, p);
+  if (r) return r;
+  bool graph = upto == 'f' && (c->opts.flags & MOLGW_FLAG_GRAPH) && !c->graph_off;
+  for (int k : mols) graph = graph && steady(c->mols[k]);
+  if (!graph) return issue_plan(c, p, upto);
+  const bool match = c->gexec && c->graph_mol == mol && c->graph_gen == c->gen && c->graph_set == mol_set(c, mols);
+  if (!match && !graph_capture(c, mol, mols, p)) return issue_plan(c, p, upto);
+  if (cudaGraphLaunch(c->gexec, c->st) != cudaSuccess) return cuda_status(cudaGetLastError());
+  ++c->graph_replays;
+  for (int k : mols) {
+    MolBuf& m = c->mols[k];
+    m.have_b = m.have_rpa = m.have_jx = m.have_sigma = true;
+    m.b_valid = m.jx_valid = m.rpa_valid = m.sigma_valid = false;
+  }
+  for (int k = 0; k < MOLGW_K_COUNT; ++k) {
+    c->timer.launches[k] += c->graph_launches[k];
+    c->timer.total_launches += c->graph_launches[k];
+  }
+  return MOLGW_OK;
+}
 
 }  // namespace
 
@@ -249,7 +532,7 @@ int molgw_b200_create(const molgw_opts* o, molgw_ctx* out) {
   *out = nullptr;
   if (!o || o->struct_size != (int32_t)sizeof(molgw_opts)) return MOLGW_E_ARG;
   if (o->precision < MOLGW_PREC_FP64 || o->precision > MOLGW_PREC_BF16X6) return MOLGW_E_ARG;
-  if (o->max_mols < 1 || !(o->eta > 0.0)) return MOLGW_E_ARG;
+  if (o->max_mols < 1 || !(o->eta > 0.0) || o->lanes < 0) return MOLGW_E_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) { cudaGetLastError(); return MOLGW_E_CUDA; }
   if (o->device < 0 || o->device >= ndev) return MOLGW_E_ARG;
@@ -277,9 +560,12 @@ int molgw_b200_create(const molgw_opts* o, molgw_ctx* out) {
   c->tcb.resize(o->max_mols);
   c->timer.enabled = (o->flags & MOLGW_FLAG_KTIMING) != 0;
   c->timer.mask = c->timer.enabled ? 0xffffffffu : 0u;
-  c->ex.st = c->st;
-  c->ex.status = c->d_status;
-  c->ex.timer = &c->timer;
+  Lane* l0 = nullptr;
+  if (cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess || lane_get(c, 0, &l0) != MOLGW_OK) {
+    cudaGetLastError();
+    molgw_b200_destroy(c);
+    return MOLGW_E_CUDA;
+  }
   *out = c;
   return MOLGW_OK;
 }
@@ -296,6 +582,7 @@ int molgw_b200_set_ri(molgw_ctx c, int mol, int n_basis, int n_aux, const double
   m.h_ready = false;
   if (m.ri_allocs.empty() || m.nb != n_basis || m.na != n_aux) {
     cudaStreamSynchronize(c->st);
+    ++c->gen;
     free_all(m.ri_allocs);
     free_all(m.orb_allocs);   // orbital-size buffers depend on n_basis and n_aux
     m.eps = nullptr;
@@ -307,8 +594,7 @@ int molgw_b200_set_ri(molgw_ctx c, int mol, int n_basis, int n_aux, const double
     m.T1 = dalloc(m.ri_allocs, nl, &err);
     TcBufs& tb = c->tcb[mol];
     free_all(tb.ri_allocs);
-    free_all(tb.orb_allocs);
-    if (use_tc(c) && (c->opts.flags & MOLGW_FLAG_TC_AB)) {
+    if (use_tc_ab(c)) {
       double* base = dalloc(tb.ri_allocs, tc_ri_doubles(tc_prec(c), n_basis, n_aux), &err);
       if (!err) tc_ri_carve(tb, tc_prec(c), n_basis, n_aux, base);
     }
@@ -316,8 +602,9 @@ int molgw_b200_set_ri(molgw_ctx c, int mol, int n_basis, int n_aux, const double
   }
   int r = copy_in(c, m.L, L, nl);
   if (r) return r;
-  check_finite(c->ex, m.L, (long long)nl);
-  if (use_tc(c) && (c->opts.flags & MOLGW_FLAG_TC_AB)) tc_split_ri(c->ex, m, c->tcb[mol]);
+  Exec& ex = c->lanes[0].ex;
+  check_finite(ex, m.L, (long long)nl);
+  if (use_tc_ab(c)) tc_split_ri(ex, m, c->tcb[mol]);
   m.have_ri = true;
   return launch_status();
 }
@@ -334,6 +621,7 @@ int molgw_b200_set_orbitals(molgw_ctx c, int mol, int n_occ, const double* eps, 
   const bool full = (c->opts.flags & MOLGW_FLAG_FULL_XPY) != 0;
   if (m.orb_allocs.empty() || m.alloc_no != n_occ) {
     cudaStreamSynchronize(c->st);
+    ++c->gen;
     free_all(m.orb_allocs);
     m.have_orb = false;
     int err = 0;
@@ -351,20 +639,7 @@ int molgw_b200_set_orbitals(molgw_ctx c, int mol, int n_occ, const double* eps, 
     m.M = dalloc(m.orb_allocs, (size_t)nov * nov, &err);
     m.ZT = dalloc(m.orb_allocs, (size_t)nov * nov, &err);
     m.XpY = full ? dalloc(m.orb_allocs, (size_t)nov * nov, &err) : nullptr;
-    TcBufs& tb = c->tcb[mol];
-    free_all(tb.orb_allocs);
-    if (use_tc(c) && !err) {
-      const int prec = tc_prec(c);
-      const int mb = tc_mblock(prec, nb, nov);
-      const size_t nd = tc_orb_doubles(prec, nb, na, nov, mb, tc_pad(nov, prec));
-      double* base = dalloc(tb.orb_allocs, nd, &err);
-      if (!err) {
-        // padding columns that no kernel writes (X beyond nb, w and g*w beyond n_ov) must read as zero
-        cudaMemsetAsync(base, 0, nd * sizeof(double), c->st);
-        tc_bufs_carve(tb, prec, nb, na, nov, mb, base);
-      }
-    }
-    if (err) { free_all(m.orb_allocs); free_all(tb.orb_allocs); m.eps = nullptr; m.alloc_no = 0; return err; }
+    if (err) { free_all(m.orb_allocs); m.eps = nullptr; m.alloc_no = 0; return err; }
     m.alloc_no = n_occ;
   }
   m.no = n_occ;
@@ -372,33 +647,23 @@ int molgw_b200_set_orbitals(molgw_ctx c, int mol, int n_occ, const double* eps, 
   int r = copy_in(c, m.eps, eps, nb);
   if (!r) r = copy_in(c, m.C, C, (size_t)nb * nb);
   if (r) return r;
-  check_finite(c->ex, m.eps, nb);
-  check_finite(c->ex, m.C, (long long)nb * nb);
+  Exec& ex = c->lanes[0].ex;
+  check_finite(ex, m.eps, nb);
+  check_finite(ex, m.C, (long long)nb * nb);
   m.have_orb = true;
   m.b_valid = m.jx_valid = m.rpa_valid = m.sigma_valid = false;
   m.have_b = m.have_rpa = m.have_jx = m.have_sigma = false;
   m.h_ready = false;
   if (h_core) {
-    r = ensure_scratch(c, nb, na, nov);
+    r = ensure_scratch(c, c->lanes[0], nb, na, nov);
     if (r) return r;
     // stage h_AO in the T1 buffer (n_aux*nb*nb >= nb*nb), then h_MO = C^T h C
     r = copy_in(c, m.T1, h_core, (size_t)nb * nb);
     if (r) return r;
-    h_ao_to_mo(c->ex, m, m.T1, c->scr);
+    h_ao_to_mo(ex, m, m.T1, c->lanes[0].scr);
     m.h_ready = true;
   }
   return launch_status();
-}
-
-static int for_each_ready(molgw_ctx c, char upto) {
-  int any = 0;
-  for (int k = 0; k < (int)c->mols.size(); ++k) {
-    if (!ready(c->mols[k])) continue;
-    any = 1;
-    int r = run_pass(c, k, upto);
-    if (r) return r;
-  }
-  return any ? MOLGW_OK : MOLGW_E_STATE;
 }
 
 int molgw_b200_rpa(molgw_ctx c, int mol, double* omega, double* xpy) {
@@ -406,13 +671,13 @@ int molgw_b200_rpa(molgw_ctx c, int mol, double* omega, double* xpy) {
   DeviceGuard g(c->device);
   if (mol == -1) {
     if (omega || xpy) return MOLGW_E_ARG;
-    return for_each_ready(c, 'c');
+    return run_mols(c, -1, 'c');
   }
   if (!mol_ok(c, mol)) return MOLGW_E_ARG;
   if (xpy && !(c->opts.flags & MOLGW_FLAG_FULL_XPY)) return MOLGW_E_ARG;
   MolBuf& m = c->mols[mol];
   if (!ready(m)) return MOLGW_E_STATE;
-  int r = run_pass(c, mol, 'c');
+  int r = run_mols(c, mol, 'c');
   if (r) return r;
   bool sync = false;
   if (omega) r = copy_out(c, omega, m.Om, m.nov, &sync);
@@ -426,12 +691,12 @@ int molgw_b200_sigma(molgw_ctx c, int mol, double* sigma_x, double* sigma_c) {
   DeviceGuard g(c->device);
   if (mol == -1) {
     if (sigma_x || sigma_c) return MOLGW_E_ARG;
-    return for_each_ready(c, 'e');
+    return run_mols(c, -1, 'e');
   }
   if (!mol_ok(c, mol)) return MOLGW_E_ARG;
   MolBuf& m = c->mols[mol];
   if (!ready(m)) return MOLGW_E_STATE;
-  int r = run_pass(c, mol, 'e');
+  int r = run_mols(c, mol, 'e');
   if (r) return r;
   bool sync = false;
   const size_t nn = (size_t)m.nb * m.nb;
@@ -446,12 +711,12 @@ int molgw_b200_qs_step(molgw_ctx c, int mol, double* eps_out, double* C_out) {
   DeviceGuard g(c->device);
   if (mol == -1) {
     if (eps_out || C_out) return MOLGW_E_ARG;
-    return for_each_ready(c, 'f');
+    return run_mols(c, -1, 'f');
   }
   if (!mol_ok(c, mol)) return MOLGW_E_ARG;
   MolBuf& m = c->mols[mol];
   if (!ready(m)) return MOLGW_E_STATE;
-  int r = run_pass(c, mol, 'f');
+  int r = run_mols(c, mol, 'f');
   if (r) return r;
   bool sync = false;
   if (eps_out) r = copy_out(c, eps_out, m.eps, m.nb, &sync);
@@ -499,10 +764,10 @@ int molgw_b200_rpa_matrix(molgw_ctx c, int mol, double* M) {
   DeviceGuard g(c->device);
   MolBuf& m = c->mols[mol];
   if (!ready(m)) return MOLGW_E_STATE;
-  int r = run_pass(c, mol, 'b');
+  int r = run_mols(c, mol, 'b');
   if (r) return r;
   // the build keeps the lower 64x64 tiles and full diagonal tiles: mirror them
-  fill_upper(c->ex, m.M, m.nov);
+  fill_upper(c->lanes[0].ex, m.M, m.nov);
   bool sync = false;
   r = copy_out(c, M, m.M, (size_t)m.nov * m.nov, &sync);
   if (r) return r;
@@ -512,7 +777,8 @@ int molgw_b200_rpa_matrix(molgw_ctx c, int mol, double* M) {
 int molgw_b200_eigh(molgw_ctx c, int n, const double* A, double* w, double* Z) {
   if (!c || n < 1 || !A || !w) return MOLGW_E_ARG;
   DeviceGuard g(c->device);
-  int r = ensure_eig(c, n, n);
+  Lane& l = c->lanes[0];
+  int r = ensure_eig(c, l, n, n);
   if (r) return r;
   std::vector<void*> tmp;
   int err = 0;
@@ -521,11 +787,11 @@ int molgw_b200_eigh(molgw_ctx c, int n, const double* A, double* w, double* Z) {
   if (err) { free_all(tmp); return err; }
   r = copy_in(c, dA, A, (size_t)n * n);
   if (!r) {
-    eigh_dense(c->ex, c->eig, n, dA, dZ);
+    eigh_dense(l.ex, l.eig, n, dA, dZ);
     r = launch_status();
   }
   bool sync = false;
-  if (!r) r = copy_out(c, w, c->eig.lam, n, &sync);
+  if (!r) r = copy_out(c, w, l.eig.lam, n, &sync);
   if (!r && Z) r = copy_out(c, Z, dZ, (size_t)n * n, &sync);
   int s = read_status(c);   // the temporaries are freed below: always synchronise
   free_all(tmp);
@@ -548,6 +814,11 @@ int molgw_b200_kernel_stats(molgw_ctx c, int64_t* launches, double* ms, int rese
 
 int64_t molgw_b200_launch_count(molgw_ctx c) { return c ? c->timer.total_launches : 0; }
 
+int64_t molgw_b200_graph_replays(molgw_ctx c) {
+  if (!c) return 0;
+  return c->graph_off ? -1 : c->graph_replays;
+}
+
 int molgw_b200_set_timing(molgw_ctx c, uint32_t class_mask) {
   if (!c) return MOLGW_E_ARG;
   DeviceGuard g(c->device);
@@ -564,10 +835,10 @@ int molgw_b200_destroy(molgw_ctx c) {
     DeviceGuard g(c->device);
     s = read_status(c);
     for (auto& m : c->mols) { free_all(m.ri_allocs); free_all(m.orb_allocs); }
-    for (auto& t : c->tcb) { free_all(t.ri_allocs); free_all(t.orb_allocs); }
-    if (c->scr.base) cudaFree(c->scr.base);
-    if (c->scr.pk_base) cudaFree(c->scr.pk_base);
-    eig_work_free(c->eig);
+    for (auto& t : c->tcb) free_all(t.ri_allocs);
+    graph_drop(c);
+    for (auto& l : c->lanes) lane_free(l);
+    if (c->fork) cudaEventDestroy(c->fork);
     cudaFree(c->d_status);
     cudaFreeHost(c->h_status);
     if (c->own_stream) cudaStreamDestroy(c->st);

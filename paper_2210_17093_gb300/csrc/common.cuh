@@ -46,7 +46,9 @@ struct Exec {
   cudaStream_t st = nullptr;
   int* status = nullptr;   // device status word (0 = OK, else a molgw_status)
   KTimer* timer = nullptr;
-  bool capturing = false;  // inside stream capture: no events
+  bool capturing = false;  // inside stream capture: no events, no allocation
+  int coop_cap = 0;        // CTAs a cooperative launch may use (0: the whole device);
+                           // concurrent lanes split the device between them
 };
 
 // Scoped marker: records a start/stop event pair around the kernels launched in
@@ -140,6 +142,8 @@ void eig_work_carve(EigWork& w, double* base, int nmax, int ncols_max);
 int eig_work_alloc(EigWork& w, int nmax, int ncols_max);
 void eig_work_free(EigWork& w);
 
+// CTAs of the persistent panel kernel that are co-resident on the device.
+int tridiag_coop_capacity();
 // Reduce A (column-major, ld = n) to tridiagonal T = Q^T A Q (d, e), keeping the
 // Householder vectors in A (column i, rows i+1.., unit at row i+1 made explicit,
 // zeros above) and tau.

@@ -28,20 +28,22 @@ struct MolBuf {
   std::vector<void*> ri_allocs, orb_allocs;
 };
 
-// Split operands of the tensor-core path (hi/lo pairs, K-major, padded).
+// Split operands of the tensor-core path (hi/lo pairs, K-major, padded).  L is
+// kept per molecule (it changes only with set_ri); the orbital-size operands are
+// rebuilt in every pass and are carved from the arena of the lane running it.
 struct TcBufs {
   int prec = TC_BF16X3;
   int mb = 0;            // m values per self-energy block
   long long sp = 0;      // padded n_ov
   TcMat L;               // (n_aux*nb) x nb: L[P][nu][mu]       (per set_ri)
-  TcMat Ct, X, Xv, Rt, Bt, W, P;                  // per set_orbitals
+  TcMat Ct, X, Xv, Rt, Bt, W, P;                  // per pass (lane arena)
   float* wpart = nullptr;                         // float32 K-chunk partials of w
   long long wpart_floats = 0;
-  std::vector<void*> ri_allocs, orb_allocs;
+  std::vector<void*> ri_allocs;
 };
 
 size_t tc_ri_doubles(int prec, int nb, int na);
-size_t tc_orb_doubles(int prec, int nb, int na, long long nov, int mb, long long sp);
+size_t tc_orb_doubles(int prec, int nb, int na, long long nov, int mb);
 void tc_ri_carve(TcBufs& t, int prec, int nb, int na, double* base);
 void tc_bufs_carve(TcBufs& t, int prec, int nb, int na, long long nov, int mb, double* base);
 

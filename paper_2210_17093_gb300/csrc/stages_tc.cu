@@ -16,7 +16,22 @@ namespace molgw {
 namespace {
 
 constexpr int kW = 64;                              // K elements per float32 chunk of w
-constexpr long long kWpartDoubles = 1LL << 27;      // 1 GB of float32 chunk partials
+constexpr long long kWpartFloats = 1LL << 28;       // float32 chunk partials of w: at most 1 GB
+
+// Float32 K chunks of w = B_m^T R: one per kW elements of n_aux, fewer when the
+// partials of one m would not fit in kWpartFloats.
+int sigma_kw(int prec, int nb, int na, long long nov) {
+  const int kb = tc_kblock(prec);
+  const int nkw = (int)(tc_pad(na, prec) / kb);
+  const long long fit = std::max<long long>(1, kWpartFloats / std::max<long long>((long long)nb * nov, 1));
+  const int want = (int)std::min<long long>(ceil_div(nkw, std::max(1, kW / kb)), fit);
+  return tc_ksplit_of(nkw, std::max(want, 1));
+}
+
+long long wpart_floats_for(int prec, int nb, int na, long long nov, int mb) {
+  const long long per_m = (long long)sigma_kw(prec, nb, na, nov) * nb * nov;
+  return std::min<long long>(std::max<long long>(per_m, (long long)mb * per_m), std::max(kWpartFloats, per_m));
+}
 
 TcMat carve(double*& base_bytes_as_double, long long rows, long long ld, int prec) {
   // carve the slices (each rows x ld elements) from a byte arena kept in doubles
@@ -47,17 +62,25 @@ template <int PREC>
 __global__ void k_sigma_combine(const float* __restrict__ part, int kw, long long rows, long long nov,
                                 const double* __restrict__ eps, const double* __restrict__ omega, int nb, int no,
                                 int m0, long long sp, double eta, TcMat W, TcMat P) {
-  const long long total = rows * nov;
+  // every padded column sidx in [n_ov, sp) is written as zero: the operands are
+  // carved from a lane arena that other molecules also use
+  const long long total = rows * sp, ptotal = rows * nov;
   const double eta2 = eta * eta;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    double w = 0.0;
-    for (int k = 0; k < kw; ++k) w += (double)part[(long long)k * total + idx];
-    const long long row = idx / nov, sidx = idx % nov;
+    const long long row = idx / sp, sidx = idx % sp;
     const int mm = (int)(row / nb), pp = (int)(row % nb), m = m0 + mm;
+    const long long o = (long long)pp * W.ld + (long long)mm * sp + sidx;
+    if (sidx >= nov) {
+      tc_store_split<PREC>(W, o, 0.0);
+      tc_store_split<PREC>(P, o, 0.0);
+      continue;
+    }
+    const long long pidx = row * nov + sidx;
+    double w = 0.0;
+    for (int k = 0; k < kw; ++k) w += (double)part[(long long)k * ptotal + pidx];
     const double x = (eps[pp] - eps[m]) + ((m < no) ? omega[sidx] : -omega[sidx]);
     const double g = x / (x * x + eta2);
-    const long long o = (long long)pp * W.ld + (long long)mm * sp + sidx;
     tc_store_split<PREC>(W, o, w);
     tc_store_split<PREC>(P, o, w * g);
   }
@@ -69,8 +92,8 @@ size_t tc_ri_doubles(int prec, int nb, int na) {
   return (size_t)carve_doubles((long long)na * nb, tc_pad(nb, prec), prec);
 }
 
-size_t tc_orb_doubles(int prec, int nb, int na, long long nov, int mb, long long sp) {
-  const long long nbp = tc_pad(nb, prec), nap = tc_pad(na, prec);
+size_t tc_orb_doubles(int prec, int nb, int na, long long nov, int mb) {
+  const long long nbp = tc_pad(nb, prec), nap = tc_pad(na, prec), sp = tc_pad(nov, prec);
   size_t t = 0;
   t += carve_doubles(nb, nbp, prec);                 // C^T
   t += carve_doubles((long long)na * nb, nbp, prec); // X
@@ -78,7 +101,7 @@ size_t tc_orb_doubles(int prec, int nb, int na, long long nov, int mb, long long
   t += carve_doubles(nov, nap, prec);                // R^T
   t += carve_doubles((long long)nb * nb, nap, prec); // B^T per m
   t += 2 * carve_doubles(nb, (long long)mb * sp, prec);   // w, g*w
-  t += kWpartDoubles;                                       // float32 chunk partials of w
+  t += (wpart_floats_for(prec, nb, na, nov, mb) + 63) / 64 * 32;   // float32 chunk partials of w
   return t;
 }
 
@@ -96,8 +119,7 @@ void tc_bufs_carve(TcBufs& t, int prec, int nb, int na, long long nov, int mb, d
   t.W = carve(p, nb, (long long)mb * t.sp, prec);
   t.P = carve(p, nb, (long long)mb * t.sp, prec);
   t.wpart = reinterpret_cast<float*>(p);
-  t.wpart_floats = 2 * kWpartDoubles;
-  p += kWpartDoubles;
+  t.wpart_floats = wpart_floats_for(prec, nb, na, nov, mb);
 }
 
 void tc_ri_carve(TcBufs& t, int prec, int nb, int na, double* base) {
@@ -124,6 +146,14 @@ int stage_ri_mo_transform_tc(Exec& ex, MolBuf& m, TcBufs& t) {
   g1.batch = na; g1.a_batch_rows = 0; g1.b_batch_rows = nb; g1.out_batch_rows = nb;
   g1.epi.mode = TC_EPI_SPLIT;
   g1.epi.out_split = t.X;
+  if (nbp > nb) {
+    // the epilogue writes columns < nb; the K padding of X must read as zero
+    const int es = tc_elem_bytes(t.prec);
+    void* sl[3] = {t.X.hi, t.X.lo, t.X.lo2};
+    for (int k = 0; k < tc_slices(t.prec); ++k)
+      cudaMemset2DAsync((char*)sl[k] + (size_t)nb * es, (size_t)nbp * es, 0, (size_t)(nbp - nb) * es,
+                        (size_t)na * nb, ex.st);
+  }
   int r = tc_gemm(ex, g1);
   if (r) return r;
   // B[(P,q)][p] = sum_nu X[(P,q)][nu] C[nu][p]
@@ -162,10 +192,9 @@ int stage_sigma_tc(Exec& ex, MolBuf& m, TcBufs& t, Scratch& s, double eta) {
   tc_split(ex, t.prec, m.R, nov, na, 1, nov, nullptr, t.Rt);
   tc_split(ex, t.prec, m.B, nn, na, 1, nn, nullptr, t.Bt);
   const int es = tc_elem_bytes(t.prec);
-  // w in K chunks of KW elements (float32 on the tensor cores), combined in float64
+  // w in K chunks of kW elements (float32 on the tensor cores), combined in float64
   const int kb = tc_kblock(t.prec);
-  const int nkw = (int)(nap / kb);
-  const int kw = tc_ksplit_of(nkw, ceil_div(nkw, std::max(1, kW / kb)));
+  const int kw = sigma_kw(t.prec, nb, na, nov);
   const long long per_m = (long long)kw * nb * nov;   // floats of partials per m
   const int mstep = (int)std::max<long long>(1, std::min<long long>(t.mb, t.wpart_floats / std::max<long long>(per_m, 1)));
   for (int m0 = 0; m0 < nb; m0 += mstep) {
@@ -184,7 +213,7 @@ int stage_sigma_tc(Exec& ex, MolBuf& m, TcBufs& t, Scratch& s, double eta) {
     int r = tc_gemm(ex, gw);
     if (r) return r;
     {
-      const long long total = (long long)cnt * nb * nov;
+      const long long total = (long long)cnt * nb * t.sp;
       const int blocks = (int)std::min<long long>(ceil_div(total, 256), 152LL * 16);
       KScope ks(ex, MOLGW_K_SIGMA);
       if (t.prec == TC_BF16X3)

@@ -450,8 +450,7 @@ int g_num_sms = 0;
 
 }  // namespace
 
-void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
-  if (n <= 0) return;
+int tridiag_coop_capacity() {
   if (g_coop_blocks_per_sm < 0) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -461,6 +460,12 @@ void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
     g_coop_blocks_per_sm = std::max(1, std::min(occ, 2));
     g_coop_blocks_per_sm = std::min(g_coop_blocks_per_sm, kMaxPanelGrid / std::max(g_num_sms, 1));
   }
+  return g_num_sms * g_coop_blocks_per_sm;
+}
+
+void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
+  if (n <= 0) return;
+  tridiag_coop_capacity();
   PanelParams p{};
   p.n = n; p.A = A; p.Wp = w.Wp; p.d = w.d; p.e = w.e; p.tau = w.tau; p.scal = w.scal;
   p.status = ex.status;
@@ -475,7 +480,10 @@ void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
   p.bar = reinterpret_cast<GridBar*>(base);   base += 2;
   p.p_t = base;    base += (long long)nrbt * (nrbt + 1) / 2 * TB;
   p.p_y = base;
-  const int cap = g_num_sms * g_coop_blocks_per_sm;
+  // Concurrent lanes each take a share of the co-resident CTAs, so that the
+  // persistent panels of all lanes fit on the device at the same time.
+  int cap = g_num_sms * g_coop_blocks_per_sm;
+  if (ex.coop_cap > 0) cap = std::max(2 * NBP / (RT / 32), std::min(cap, ex.coop_cap));
   const int ncols = n - 1;
   for (int k0 = 0; k0 < ncols; k0 += NBP) {
     const int nbp = std::min(NBP, ncols - k0);

@@ -34,7 +34,7 @@ EXPORTS = ["molgw_b200_create", "molgw_b200_set_ri", "molgw_b200_set_orbitals", 
            "molgw_b200_sigma", "molgw_b200_qs_step", "molgw_b200_sync", "molgw_b200_fetch",
            "molgw_b200_rpa_matrix", "molgw_b200_eigh", "molgw_b200_kernel_stats",
            "molgw_b200_launch_count", "molgw_b200_set_timing", "molgw_b200_destroy",
-           "molgw_b200_status_string", "molgw_b200_eigh_noalloc"]
+           "molgw_b200_status_string", "molgw_b200_eigh_noalloc", "molgw_b200_graph_replays"]
 NOALLOC_NMAX = 256
 
 
@@ -47,7 +47,8 @@ class MolgwError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("max_mols", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("eta", ctypes.c_double), ("stream", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+                ("eta", ctypes.c_double), ("stream", ctypes.c_void_p), ("flags", ctypes.c_uint32),
+                ("lanes", ctypes.c_int32)]
 
 
 _lib = None
@@ -76,6 +77,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "molgw_b200_eigh": ([vp, ip, dp, dp, dp], ip),
         "molgw_b200_kernel_stats": ([vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double), ip], ip),
         "molgw_b200_launch_count": ([vp], ctypes.c_int64),
+        "molgw_b200_graph_replays": ([vp], ctypes.c_int64),
         "molgw_b200_set_timing": ([vp, ctypes.c_uint32], ip),
         "molgw_b200_destroy": ([vp], ip),
         "molgw_b200_status_string": ([ip], ctypes.c_char_p),
@@ -125,7 +127,7 @@ class Context:
     """One library context (include/molgw_gb300.h, molgw_b200_create)."""
 
     def __init__(self, precision: str = "fp64", max_mols: int = 1, device: int = 0,
-                 eta: float = 1e-3, stream=None, flags: int = 0):
+                 eta: float = 1e-3, stream=None, flags: int = 0, lanes: int = 0):
         self._lib = load()
         o = Opts()
         o.struct_size = ctypes.sizeof(Opts)
@@ -140,6 +142,7 @@ class Context:
             flags |= FLAG_USE_STREAM
         o.stream = stream
         o.flags = flags
+        o.lanes = lanes
         h = ctypes.c_void_p()
         _check(self._lib.molgw_b200_create(ctypes.byref(o), ctypes.byref(h)), "molgw_b200_create")
         self._h = h
@@ -213,6 +216,10 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self._lib.molgw_b200_launch_count(self._hh()))
+
+    def graph_replays(self) -> int:
+        """qs_step calls served from a captured graph (-1: capture failed, graphs off)."""
+        return int(self._lib.molgw_b200_graph_replays(self._hh()))
 
     def close(self):
         if self._h is not None:

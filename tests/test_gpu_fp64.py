@@ -229,8 +229,9 @@ def test_bench_size_parity():
 # batch, determinism, boundary behaviour
 # ---------------------------------------------------------------------------
 def test_batch_equals_solo_bitwise():
+    # one lane: the batch issues exactly the launches of the solo calls
     mols = [sy.batch_molecule(s) for s in (100, 101, 102)]
-    with lib_context(max_mols=3) as ctx:
+    with lib_context(max_mols=3, lanes=1) as ctx:
         for k, m in enumerate(mols):
             load_mol(ctx, k, m)
         ctx.qs_step(-1)
