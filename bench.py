@@ -44,6 +44,18 @@ WORKLOADS = {
 # float64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 # (NVIDIA lists 1.25 TFLOP/s FP64 for this part; a register-only DFMA loop measured 1.20).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def measured_peaks() -> dict:
+    """Copy bandwidth and BF16 GEMM peaks measured on this GPU model (MEASURED_PEAKS.json
+    beside this file), else one earlier GB300 measurement (6.8 TB/s, 1.9 PFLOP/s)."""
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "kind": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "kind": "fallback"}
 # DRAM bytes the tridiagonalisation panel kernel moves per algorithmic byte (the lower
 # triangle of the trailing matrix once per column), from one ncu capture of the panel of
 # columns 192..255 at n = 6400: 10.13 GB measured for 9.77 GB algorithmic.
@@ -310,7 +322,20 @@ def run_ours(args, wl):
             mctx.qs_step(0)
             mbreak = mctx.kernel_stats(reset=True)
         err = float(np.max(np.abs(e1.numpy() - eps_fp64_step1)))
+        tc_ms = mbreak.get("gemm_tc", (0, 0.0))[1]
+        peaks = measured_peaks()
+        nov = n
+        tc_exec = None
+        if args.mixed == "bf16x10" and tc_ms > 0:
+            # ten BF16 slice products per useful multiply-add: w = B_m^T R (K = n_aux padded
+            # to 64) and S = (g w) w^T (K = n_basis x n_ov padded to 64)
+            pad = lambda k: -(-k // 64) * 64
+            ex_flops = 10 * 2 * (nb * nb * nov * pad(na) + nb * nb * nb * pad(nov))
+            tc_exec = {"executed_tflops": ex_flops / (tc_ms / 1e3) / 1e12,
+                       "frac_of_bf16_peak": ex_flops / (tc_ms / 1e3) / 1e12 / peaks["bf16_tflops"],
+                       "peak_tflops": peaks["bf16_tflops"], "peak_kind": peaks["kind"] + " bf16 burst"}
         mixed = {"precision": args.mixed, "stages": "(d)+(e) on tcgen05 tensor cores; (a)-(c), (f) float64",
+                 "tensor": tc_exec,
                  "ms_per_step": t_mixed / args.steps * 1e3,
                  "speedup_vs_fp64": (t_max / args.steps) / (t_mixed / args.steps),
                  "qp_error_vs_fp64_meV": err * 27211.386,
@@ -366,9 +391,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="B")
-    ap.add_argument("--precision", choices=["fp64", "bf16x3", "tf32x3", "bf16x6"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "bf16x3", "tf32x3", "bf16x6", "bf16x10"], default="fp64")
     ap.add_argument("--dominant", default="tridiag_panel", help="kernel class reported in 'roofline'")
-    ap.add_argument("--mixed", choices=["bf16x3", "tf32x3", "bf16x6"], default="bf16x3",
+    ap.add_argument("--mixed", choices=["bf16x3", "tf32x3", "bf16x6", "bf16x10"], default="bf16x10",
                     help="precision of the split-precision path reported under 'mixed'")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -67,7 +67,10 @@ enum molgw_precision {
   MOLGW_PREC_FP64 = 0,    /* float64 on the CUDA cores                                   */
   MOLGW_PREC_BF16X3 = 1,  /* tcgen05 BF16 products, 3-term hi/lo split, FP32 accumulate  */
   MOLGW_PREC_TF32X3 = 2,  /* tcgen05 TF32 products, 3-term hi/lo split, FP32 accumulate  */
-  MOLGW_PREC_BF16X6 = 3   /* tcgen05 BF16 products, 3 slices hi+mid+lo, 6 products, FP32 */
+  MOLGW_PREC_BF16X6 = 3,  /* tcgen05 BF16 products, 3 slices hi+mid+lo, 6 products, FP32 */
+  MOLGW_PREC_BF16X10 = 4  /* tcgen05 BF16 products of 4 fixed-point slices (10 products),
+                             exact FP32 sums per 256-element chunk, one FP64 rounding per
+                             1024-element group; (d) and (e) only (no MOLGW_FLAG_TC_AB)  */
 };
 /* With BF16X3, TF32X3 or BF16X6 the residue and self-energy contractions (d),
  * (e) run on the tensor cores (the residues in float32 chunks of 64 auxiliary
@@ -207,6 +210,13 @@ int molgw_b200_set_timing(molgw_ctx ctx, uint32_t class_mask);
 /* Number of device kernels this context has launched since creation (a graph
  * replay counts the kernels the graph holds). */
 int64_t molgw_b200_launch_count(molgw_ctx ctx);
+
+/* Library extension (the paper has no counterpart): the split-precision GEMM
+ * of the context's precision (not MOLGW_PREC_FP64, else MOLGW_E_ARG) on its own,
+ * C[m][n] = sum_k A[m][k] B[n][k] for row-major float64 A[M][K], B[N][K], C[M][N]
+ * (host or device memory), so that the tensor-core arithmetic of (d) and (e) can
+ * be checked against float64.  Allocates temporaries and synchronises. */
+int molgw_b200_tc_gemm(molgw_ctx ctx, int M, int N, int K, const double* A, const double* B, double* C);
 
 /* Library extension (the paper has no counterpart): number of qs_step calls
  * served by replaying a captured graph (MOLGW_FLAG_GRAPH); -1 once a capture

@@ -19,6 +19,7 @@ struct Lane {
   EigWork eig;
   int eig_n = 0, eig_cols = 0;
   TcBufs tco;                 // orbital-size split operands, carved per molecule
+  FxBufs fxo;                 // the same for the fixed-point precision
   void* tco_base = nullptr;
   size_t tco_cap = 0;         // doubles
   size_t pk_fail = 0;         // packed-residue request that did not fit (not retried)
@@ -116,7 +117,8 @@ int read_status(molgw_ctx c) {
 }
 
 bool use_tc(molgw_ctx c) { return c->opts.precision != MOLGW_PREC_FP64; }
-bool use_tc_ab(molgw_ctx c) { return use_tc(c) && (c->opts.flags & MOLGW_FLAG_TC_AB); }
+bool use_fx(molgw_ctx c) { return c->opts.precision == MOLGW_PREC_BF16X10; }
+bool use_tc_ab(molgw_ctx c) { return use_tc(c) && !use_fx(c) && (c->opts.flags & MOLGW_FLAG_TC_AB); }
 int tc_prec(molgw_ctx c) {
   if (c->opts.precision == MOLGW_PREC_TF32X3) return TC_TF32X3;
   if (c->opts.precision == MOLGW_PREC_BF16X6) return TC_BF16X6;
@@ -240,7 +242,8 @@ int ensure_scratch(molgw_ctx c, Lane& l, int nb, int na, long long nov) {
 int ensure_tco(molgw_ctx c, Lane& l, int nb, int na, long long nov) {
   if (!use_tc(c)) return MOLGW_OK;
   const int prec = tc_prec(c);
-  const size_t want = tc_orb_doubles(prec, nb, na, nov, tc_mblock(prec, nb, nov));
+  const size_t want = use_fx(c) ? (fx_sigma_bytes(nb, na, nov, fx_mblock(nb, na, nov)) + 7) / 8
+                                : tc_orb_doubles(prec, nb, na, nov, tc_mblock(prec, nb, nov));
   if (want <= l.tco_cap) return MOLGW_OK;
   if (l.ex.capturing) return MOLGW_E_STATE;
   cudaStreamSynchronize(l.st);
@@ -279,7 +282,9 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
   const bool tc = use_tc(c);
   const bool tc_ab = use_tc_ab(c);
   TcBufs& tb = l.tco;
-  if (tc) {
+  if (use_fx(c)) {
+    fx_bufs_carve(l.fxo, m.nb, m.na, m.nov, fx_mblock(m.nb, m.na, m.nov), l.tco_base);
+  } else if (tc) {
     const int prec = tc_prec(c);
     tc_bufs_carve(tb, prec, m.nb, m.na, m.nov, tc_mblock(prec, m.nb, m.nov), (double*)l.tco_base);
     tb.L = c->tcb[mol].L;
@@ -324,7 +329,10 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
       stage_j_sigx(ex, m, l.scr);
       m.jx_valid = m.have_jx = true;
     }
-    if (tc) {
+    if (use_fx(c)) {
+      r = stage_sigma_fx(ex, m, l.fxo, l.scr, c->opts.eta);
+      if (r) return r;
+    } else if (tc) {
       r = stage_sigma_tc(ex, m, tb, l.scr, c->opts.eta);
       if (r) return r;
     } else {
@@ -531,7 +539,8 @@ int molgw_b200_create(const molgw_opts* o, molgw_ctx* out) {
   if (!out) return MOLGW_E_ARG;
   *out = nullptr;
   if (!o || o->struct_size != (int32_t)sizeof(molgw_opts)) return MOLGW_E_ARG;
-  if (o->precision < MOLGW_PREC_FP64 || o->precision > MOLGW_PREC_BF16X6) return MOLGW_E_ARG;
+  if (o->precision < MOLGW_PREC_FP64 || o->precision > MOLGW_PREC_BF16X10) return MOLGW_E_ARG;
+  if (o->precision == MOLGW_PREC_BF16X10 && (o->flags & MOLGW_FLAG_TC_AB)) return MOLGW_E_ARG;
   if (o->max_mols < 1 || !(o->eta > 0.0) || o->lanes < 0) return MOLGW_E_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) { cudaGetLastError(); return MOLGW_E_CUDA; }
@@ -813,6 +822,73 @@ int molgw_b200_kernel_stats(molgw_ctx c, int64_t* launches, double* ms, int rese
 }
 
 int64_t molgw_b200_launch_count(molgw_ctx c) { return c ? c->timer.total_launches : 0; }
+
+int molgw_b200_tc_gemm(molgw_ctx c, int M, int N, int K, const double* A, const double* B, double* C) {
+  if (!c || M < 1 || N < 1 || K < 1 || !A || !B || !C || !use_tc(c)) return MOLGW_E_ARG;
+  DeviceGuard g(c->device);
+  Exec& ex = c->lanes[0].ex;
+  std::vector<void*> tmp;
+  int err = 0;
+  double* dA = dalloc(tmp, (size_t)M * K, &err);
+  double* dB = dalloc(tmp, (size_t)N * K, &err);
+  double* dC = dalloc(tmp, (size_t)M * N, &err);
+  if (err) { free_all(tmp); return err; }
+  int r = copy_in(c, dA, A, (size_t)M * K);
+  if (!r) r = copy_in(c, dB, B, (size_t)N * K);
+  if (!r && use_fx(c)) {
+    const long long kp = fx_pad(K);
+    const int ns = fx_nsplit((int)kp);
+    double* ma = dalloc(tmp, (fx_mat_bytes(M, kp) + 7) / 8, &err);
+    double* mb = dalloc(tmp, (fx_mat_bytes(N, kp) + 7) / 8, &err);
+    double* part = dalloc(tmp, (size_t)ns * M * N, &err);
+    if (err) { free_all(tmp); return err; }
+    const FxMat fa = fx_mat_carve(ma, M, kp), fb = fx_mat_carve(mb, N, kp);
+    fx_split(ex, dA, M, K, K, 1, nullptr, fa);
+    fx_split(ex, dB, N, K, K, 1, nullptr, fb);
+    FxGemm gm;
+    gm.M = M; gm.N = N; gm.K = (int)kp;
+    gm.A = fa; gm.B = fb;
+    gm.out = part; gm.out_ld = M; gm.split_stride = (long long)M * N; gm.col_major = true;
+    r = fx_gemm(ex, gm);
+    if (!r) fx_reduce_cm(ex, part, ns, (long long)M * N, M, N, dC, N, 0.0);
+  } else if (!r) {
+    const int prec = tc_prec(c);
+    const long long kp = tc_pad(K, prec);
+    double* ta = dalloc(tmp, (size_t)tc_slices(prec) * (((size_t)M * kp * tc_elem_bytes(prec) + 255) / 256 * 32), &err);
+    double* tb = dalloc(tmp, (size_t)tc_slices(prec) * (((size_t)N * kp * tc_elem_bytes(prec) + 255) / 256 * 32), &err);
+    const int nkb = (int)(kp / tc_kblock(prec));
+    const int ks = tc_ksplit_of(nkb, ceil_div(nkb, std::max(1, 1024 / tc_kblock(prec))));
+    float* part = (float*)dalloc(tmp, ((size_t)ks * M * N + 1) / 2, &err);
+    if (err) { free_all(tmp); return err; }
+    TcMat a, b;
+    for (int side = 0; side < 2; ++side) {
+      TcMat& t = side ? b : a;
+      const long long rows = side ? N : M;
+      char* base = (char*)(side ? tb : ta);
+      const size_t words = ((size_t)rows * kp * tc_elem_bytes(prec) + 255) / 256 * 256;
+      t.rows = rows; t.ld = kp;
+      t.hi = base; t.lo = base + words;
+      if (tc_slices(prec) == 3) t.lo2 = base + 2 * words;
+    }
+    tc_split(ex, prec, dA, M, K, K, 1, nullptr, a);
+    tc_split(ex, prec, dB, N, K, K, 1, nullptr, b);
+    TcGemm gm;
+    gm.prec = prec;
+    gm.M = M; gm.N = N; gm.K = (int)kp;
+    gm.A = a; gm.B = b;
+    gm.ksplit = ks;
+    gm.epi.mode = TC_EPI_F32_PARTIAL;
+    gm.epi.out_f32 = part;
+    r = tc_gemm(ex, gm);
+    if (!r) tc_reduce_partials(ex, part, ks, M, N, dC, N, 0.0);
+  }
+  bool sync = false;
+  if (!r) r = launch_status();
+  if (!r) r = copy_out(c, C, dC, (size_t)M * N, &sync);
+  const int st = read_status(c);   // the temporaries are freed below: always synchronise
+  free_all(tmp);
+  return r ? r : st;
+}
 
 int64_t molgw_b200_graph_replays(molgw_ctx c) {
   if (!c) return 0;

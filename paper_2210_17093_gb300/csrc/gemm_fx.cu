@@ -1,0 +1,400 @@
+// Fixed-point split GEMM (fx.cuh) on tcgen05 for sm_103a.
+//
+// One 128 x 64 output tile and one K group (<= 1024 elements) per CTA; 12 warps:
+//   warp 0   TMA producer: the four BF16 slices of a 128-row A box and a 64-row B
+//            box per 64-element K block (128-byte swizzle) into a 2-stage ring of
+//            96 KB stages;
+//   warp 1   one thread issues tcgen05.mma (kind::f16, M=128, N=64, K=16): per
+//            K step the ten slice products (a, b) with a + b = l accumulate into
+//            level accumulator l (four per buffer); after each 256-element chunk the
+//            buffer is committed to the epilogue and the other buffer is used;
+//   warp 2   allocates / frees the 512 TMEM columns (2 buffers x 4 levels x 64);
+//   warps 4-11 the epilogue: for each chunk, tcgen05.ld of the four levels of its
+//            32 lanes x 32 columns, conversion to integers (exact) and accumulation
+//            of sum_l 2^(24-8l) L_l in 64-bit integers; after the last chunk one
+//            rounding to float64 and the scales u_a u_b 2^-24.
+// Every wait is bounded; a timeout latches MOLGW_E_TIMEOUT, raises a shared abort
+// flag that ends the other roles' waits, and the CTA still frees its TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "fx.cuh"
+
+namespace molgw {
+
+namespace {
+
+constexpr int BM = 128, BN = 64;
+constexpr int TA = BM * 128;                       // 16 KB: one A slice box
+constexpr int TB = BN * 128;                       // 8 KB: one B slice box
+constexpr int STAGE = kFxSlices * (TA + TB);       // 96 KB
+constexpr int STAGES = 2;
+constexpr int SMEM = STAGES * STAGE + 1024;
+constexpr int KB_CHUNK = kFxChunk / kFxKBlock;     // 4 K blocks per exact chunk
+constexpr int KB_GROUP = kFxGroup / kFxKBlock;     // 16 K blocks per group
+constexpr int TMEM_COLS = 512;
+constexpr int NT = 384;
+constexpr int EPI_THREADS = 256;
+constexpr long long SPIN_LIMIT = 1LL << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t cnt) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(cnt) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// bounded wait on a phase parity; gives up early when another role raised *abort
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
+  const uint32_t a = smem_u32(b);
+  for (long long it = 0; it < SPIN_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255) == 255 && *abort) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void fail(int* status, volatile int* abort) {
+  set_status(status, MOLGW_E_TIMEOUT);
+  *abort = 1;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// K-major operand, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc_sw128(const void* p) {
+  const uint32_t a = smem_u32(p);
+  uint64_t d = (uint64_t)((a & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dt),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
+struct FxParams {
+  int M, N, nkb, kb0;
+  const double* ua;
+  int a_ngroups;
+  const double* ub;
+  int b_ngroups;
+  double* out;
+  long long out_ld, split_stride;
+  int col_major;
+  int* status;
+};
+
+__global__ void __launch_bounds__(NT, 1)
+    fx_gemm_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+                   const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mA3,
+                   const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+                   const __grid_constant__ CUtensorMap mB2, const __grid_constant__ CUtensorMap mB3, FxParams p) {
+  const CUtensorMap* mapA[4] = {&mA0, &mA1, &mA2, &mA3};
+  const CUtensorMap* mapB[4] = {&mB0, &mB1, &mB2, &mB3};
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, gz = blockIdx.z;
+  const int kbl0 = gz * KB_GROUP;                           // first K block of this CTA (range-relative)
+  const int nk = min(p.nkb - kbl0, KB_GROUP);
+  const int nchunk = (nk + KB_CHUNK - 1) / KB_CHUNK;
+  const int group = (p.kb0 + kbl0) / KB_GROUP;              // scale group index of the operands
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t full[STAGES], empty[STAGES], accf[2], acce[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], EPI_THREADS);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = tmem_base;
+  volatile int* abort = &abort_flag;
+
+  if (warp == 0 && lane == 0) {
+    int issued = 0;
+    for (int i = 0; i < nk; ++i) {
+      const int s = i % STAGES;
+      if (i >= STAGES && !mbar_wait(&empty[s], ((i / STAGES) + 1) & 1, abort)) {
+        fail(p.status, abort);
+        break;
+      }
+      uint8_t* st = smem + s * STAGE;
+      mbar_expect_tx(&full[s], STAGE);
+      const int x = (p.kb0 + kbl0 + i) * kFxKBlock;
+#pragma unroll
+      for (int sl = 0; sl < kFxSlices; ++sl) {
+        tma_load_2d(st + sl * TA, mapA[sl], &full[s], x, m0);
+        tma_load_2d(st + kFxSlices * TA + sl * TB, mapB[sl], &full[s], x, n0);
+      }
+      issued = i + 1;
+    }
+    // copies in flight (on an error path) land before the CTA leaves
+    for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; ++i) {
+      const uint32_t a = smem_u32(&full[i % STAGES]);
+      for (long long it = 0; it < SPIN_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}"
+            : "=r"(done)
+            : "r"(a), "r"((uint32_t)((i / STAGES) & 1))
+            : "memory");
+        if (done) break;
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // D F32 (bit 4); A, B BF16 (1 at bits 7 and 10); K-major; N>>3 at bit 17; M>>4 at bit 24
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    int i = 0;
+    bool ok = true;
+    for (int c = 0; c < nchunk && ok; ++c) {
+      const int buf = c & 1;
+      if (c >= 2 && !mbar_wait(&acce[buf], ((c >> 1) + 1) & 1, abort)) {
+        fail(p.status, abort);
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int kbn = min(KB_CHUNK, nk - c * KB_CHUNK);
+      for (int kb = 0; kb < kbn; ++kb, ++i) {
+        const int s = i % STAGES;
+        if (!mbar_wait(&full[s], (i / STAGES) & 1, abort)) {
+          fail(p.status, abort);
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint8_t* st = smem + s * STAGE;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {          // 4 x 32 bytes of K per 128-byte row
+          const uint64_t o = 2 * kk;              // +32 B in the 16-byte-encoded address field
+#pragma unroll
+          for (int l = 0; l < kFxSlices; ++l)
+#pragma unroll
+            for (int a = 0; a <= l; ++a) {
+              const int b = l - a;
+              const uint64_t ad = sdesc_sw128(st + a * TA) + o;
+              const uint64_t bd = sdesc_sw128(st + kFxSlices * TA + b * TB) + o;
+              const uint32_t dt = tbase + (uint32_t)(buf * (kFxSlices * BN) + l * BN);
+              mma_bf16(dt, ad, bd, idesc, (kb > 0 || kk > 0 || a > 0) ? 1u : 0u);
+            }
+        }
+        mma_commit(&empty[s]);
+      }
+      if (ok) mma_commit(&accf[buf]);
+    }
+  } else if (warp >= 4) {
+    const int q = warp & 3, h = (warp - 4) >> 2;            // TMEM lane quarter, column half
+    const int lrow = 32 * q + lane, row = m0 + lrow;
+    long long V[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) V[j] = 0;
+    bool ok = true;
+    for (int c = 0; c < nchunk; ++c) {
+      const int buf = c & 1;
+      const bool got = mbar_wait(&accf[buf], (c >> 1) & 1, abort);
+      if (!got) fail(p.status, abort);
+      ok = __all_sync(0xffffffffu, got);       // the TMEM loads below are warp-collective
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int cb = 0; cb < 4; ++cb) {
+        uint32_t r[kFxSlices][8];
+#pragma unroll
+        for (int l = 0; l < kFxSlices; ++l)
+          tmem_ld8(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * (kFxSlices * BN) + l * BN + h * 32 + cb * 8),
+                   r[l]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          // every level sum is an integer below 2^24: the conversions are exact
+          const long long l0 = __float2int_rn(__uint_as_float(r[0][jj]));
+          const long long l1 = __float2int_rn(__uint_as_float(r[1][jj]));
+          const long long l2 = __float2int_rn(__uint_as_float(r[2][jj]));
+          const long long l3 = __float2int_rn(__uint_as_float(r[3][jj]));
+          V[cb * 8 + jj] += (l0 << 24) + (l1 << 16) + (l2 << 8) + l3;
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&acce[buf]);
+    }
+    if (ok && row < p.M) {
+      const double ua = p.ua[(long long)row * p.a_ngroups + group] * 0x1p-24;
+      double* out = p.out + (long long)gz * p.split_stride;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int col = n0 + h * 32 + j;
+        if (col < p.N) {
+          const double v = (double)V[j] * ua * p.ub[(long long)col * p.b_ngroups + group];
+          if (p.col_major)
+            out[(long long)col * p.out_ld + row] = v;
+          else
+            out[(long long)row * p.out_ld + col] = v;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+__global__ void k_fx_reduce_cm(const double* __restrict__ part, int ns, long long ss, int M, int N, double* out,
+                               long long ldo, double beta) {
+  const long long total = (long long)M * N;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx % M), c = (int)(idx / M);
+    double s = 0.0;
+    for (int k = 0; k < ns; ++k) s += part[k * ss + idx];
+    double* o = out + (long long)r * ldo + c;
+    *o = (beta == 0.0) ? s : s + beta * (*o);
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode_fx = nullptr;
+
+bool get_encode_fx() {
+  if (g_encode_fx) return true;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return false;
+  }
+  g_encode_fx = (EncodeTiledFn)fn;
+  return true;
+}
+
+// BF16 slice map: boxes of box_rows rows x 64 elements (128 B), 128-byte swizzle
+bool make_map_fx(CUtensorMap* m, void* base, long long rows, long long ld, int box_rows) {
+  cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)kFxKBlock, (cuuint32_t)box_rows};
+  cuuint32_t el[2] = {1, 1};
+  return g_encode_fx(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+
+size_t fx_mat_bytes(long long rows, long long ld) {
+  return kFxSlices * align256((size_t)rows * ld * 2) + align256((size_t)rows * fx_groups(ld) * sizeof(double));
+}
+
+FxMat fx_mat_carve(void* base, long long rows, long long ld) {
+  FxMat m;
+  m.rows = rows;
+  m.ld = ld;
+  m.ngroups = fx_groups(ld);
+  char* p = (char*)base;
+  for (int i = 0; i < kFxSlices; ++i) {
+    m.s[i] = p;
+    p += align256((size_t)rows * ld * 2);
+  }
+  m.u = (double*)p;
+  return m;
+}
+
+FxMat fx_rows(const FxMat& m, long long r0, long long rows) {
+  FxMat v = m;
+  for (int i = 0; i < kFxSlices; ++i) v.s[i] = (char*)m.s[i] + r0 * m.ld * 2;
+  v.u = m.u + r0 * m.ngroups;
+  v.rows = rows;
+  return v;
+}
+
+int fx_gemm(Exec& ex, const FxGemm& g) {
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0) return MOLGW_OK;
+  if (g.K % kFxKBlock || g.k0 % kFxGroup || g.A.ld % kFxKBlock || g.B.ld % kFxKBlock || g.k0 + g.K > g.A.ld ||
+      g.k0 + g.K > g.B.ld || g.M > g.A.rows || g.N > g.B.rows)
+    return MOLGW_E_ARG;
+  if (!get_encode_fx()) return MOLGW_E_CUDA;
+  CUtensorMap ma[kFxSlices], mb[kFxSlices];
+  for (int i = 0; i < kFxSlices; ++i)
+    if (!make_map_fx(&ma[i], g.A.s[i], g.A.rows, g.A.ld, BM) || !make_map_fx(&mb[i], g.B.s[i], g.B.rows, g.B.ld, BN))
+      return MOLGW_E_ARG;
+  FxParams p;
+  p.M = g.M; p.N = g.N;
+  p.nkb = g.K / kFxKBlock;
+  p.kb0 = g.k0 / kFxKBlock;
+  p.ua = g.A.u; p.a_ngroups = g.A.ngroups;
+  p.ub = g.B.u; p.b_ngroups = g.B.ngroups;
+  p.out = g.out; p.out_ld = g.out_ld; p.split_stride = g.split_stride;
+  p.col_major = g.col_major ? 1 : 0;
+  p.status = ex.status;
+  dim3 grid(ceil_div(g.N, BN), ceil_div(g.M, BM), fx_nsplit(g.K));
+  KScope ks(ex, MOLGW_K_GEMM_TC, 1);
+  cudaFuncSetAttribute(fx_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+  fx_gemm_kernel<<<grid, NT, SMEM, ex.st>>>(ma[0], ma[1], ma[2], ma[3], mb[0], mb[1], mb[2], mb[3], p);
+  return MOLGW_OK;
+}
+
+void fx_split(Exec& ex, const double* src, long long rows, long long cols, long long sr, long long sk,
+              const double* row_scale, FxMat dst) {
+  FxStrided f{src, sr, sk, rows, cols, row_scale};
+  fx_slice(ex, f, rows, dst);
+}
+
+void fx_reduce_cm(Exec& ex, const double* part, int ns, long long split_stride, int M, int N, double* out,
+                  long long ldo, double beta) {
+  const long long total = (long long)M * N;
+  KScope ks(ex, MOLGW_K_MISC);
+  k_fx_reduce_cm<<<(int)std::min<long long>(ceil_div(total, 256), 152LL * 8), 256, 0, ex.st>>>(
+      part, ns, split_stride, M, N, out, ldo, beta);
+}
+
+}  // namespace molgw

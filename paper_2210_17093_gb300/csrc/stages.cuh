@@ -1,6 +1,7 @@
 // Per-molecule device buffers and the stage drivers of one RI-qsGW pass.
 #pragma once
 #include "common.cuh"
+#include "fx.cuh"
 #include "tc.cuh"
 
 namespace molgw {
@@ -47,6 +48,18 @@ size_t tc_orb_doubles(int prec, int nb, int na, long long nov, int mb);
 void tc_ri_carve(TcBufs& t, int prec, int nb, int na, double* base);
 void tc_bufs_carve(TcBufs& t, int prec, int nb, int na, long long nov, int mb, double* base);
 
+// Operands of the fixed-point path (d)+(e): B^T and R^T sliced once per pass,
+// w (float64, per block of m) and the sliced w and g*w of the block.
+struct FxBufs {
+  int mb = 0;                  // m values per block
+  FxMat Bt, Rt;                // rows (m, p) and s, K = P
+  double* wbuf = nullptr;      // w of a block: [K group][s][(m, p)]
+  void* wp_base = nullptr;     // arena of the sliced w and g*w of a block
+};
+int fx_mblock(int nb, int na, long long nov);
+size_t fx_sigma_bytes(int nb, int na, long long nov, int mb);
+void fx_bufs_carve(FxBufs& f, int nb, int na, long long nov, int mb, void* base);
+
 struct Scratch {
   double* rho = nullptr;        // n_aux
   double* splitk = nullptr;     // split-K partials
@@ -82,5 +95,6 @@ void tc_split_ri(Exec& ex, MolBuf& m, TcBufs& t);
 int stage_ri_mo_transform_tc(Exec& ex, MolBuf& m, TcBufs& t);
 int stage_rpa_build_tc(Exec& ex, MolBuf& m, TcBufs& t);
 int stage_sigma_tc(Exec& ex, MolBuf& m, TcBufs& t, Scratch& s, double eta);
+int stage_sigma_fx(Exec& ex, MolBuf& m, FxBufs& f, Scratch& s, double eta);
 
 }  // namespace molgw

@@ -247,3 +247,181 @@ int stage_sigma_tc(Exec& ex, MolBuf& m, TcBufs& t, Scratch& s, double eta) {
 }
 
 }  // namespace molgw
+
+// ---------------------------------------------------------------------------
+// (d)+(e) on the fixed-point engine (fx.cuh): w = B_m^T R with exact chunk sums
+// rounded once to float64; the float64 differences eps_p - eps_m -/+ Omega_s and
+// g = x / (x^2 + eta^2) are formed while w and g*w are sliced; S += (g w) w^T over
+// K = (m, s), one float64 partial per 1024-wide K group, summed in a fixed order.
+// ---------------------------------------------------------------------------
+namespace molgw {
+
+namespace {
+
+constexpr long long kFxBlockBytes = 1LL << 30;   // w and its slices per block of m
+
+// 1/d by Newton-Raphson iteration from a float32 seed (two steps: each squares
+// the relative error, 2^-23 -> 2^-46 -> below float64 rounding); d > 0.
+__device__ __forceinline__ double recip_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
+  double r = (double)__frcp_rn((float)d);
+  r = r * (2.0 - d * r);
+  r = r * (2.0 - d * r);
+  return r;
+}
+
+constexpr int kSigRows = 4;   // rows p per block of k_fx_sigma_slices
+
+// Slices of w and g*w for rows p0 .. p0+3 and one K group (K = mm*sp + s): w is
+// the float64 sum of the group partials of the residue GEMM, x = (eps_p - eps_m)
+// -/+ Omega_s in float64 and g = x / (x^2 + eta^2); each value is formed once,
+// kept in shared memory for the (row, group) maxima, then sliced.
+__global__ void __launch_bounds__(256) k_fx_sigma_slices(const double* __restrict__ wbuf, int nsplit,
+                                                         long long split_stride, long long ldw, int sp, int nov,
+                                                         int nb, int no, int m0, int cnt,
+                                                         const double* __restrict__ eps,
+                                                         const double* __restrict__ om, double eta2, FxMat W,
+                                                         FxMat P) {
+  extern __shared__ double sh[];
+  double* tw = sh;                              // [kSigRows][kFxGroup]
+  double* tp = sh + kSigRows * kFxGroup;
+  const int p0 = blockIdx.x * kSigRows, g = blockIdx.y;
+  const long long K = W.ld;
+  const long long k0 = (long long)g * kFxGroup;
+  const int t = threadIdx.x;
+  const int r = t % kSigRows;
+  const int p = p0 + r;
+  for (int kk = t / kSigRows; kk < kFxGroup; kk += 256 / kSigRows) {
+    const long long k = k0 + kk;
+    double w = 0.0, gw = 0.0;
+    if (p < nb && k < K) {
+      const int mm = (int)(k / sp), s = (int)(k - (long long)mm * sp);
+      if (mm < cnt && s < nov) {
+        const long long o = (long long)s * ldw + (long long)mm * nb + p;
+        for (int j = 0; j < nsplit; ++j) w += wbuf[j * split_stride + o];
+        const int m = m0 + mm;
+        const double x = (eps[p] - eps[m]) + ((m < no) ? om[s] : -om[s]);   // float64 difference
+        gw = w * (x * recip_newton(x * x + eta2));
+      }
+    }
+    tw[r * kFxGroup + kk] = w;
+    tp[r * kFxGroup + kk] = gw;
+  }
+  __syncthreads();
+  const int warp = t >> 5, lane = t & 31;
+  const int row = warp % kSigRows;
+  const bool isP = warp >= kSigRows;
+  const double* tile = (isP ? tp : tw) + row * kFxGroup;
+  const FxMat& D = isP ? P : W;
+  const int pr = p0 + row;
+  if (pr >= nb) return;
+  // max |x| on the bit patterns: for non-negative doubles the integer order is the value order
+  long long mb = 0;
+  for (int kk = lane; kk < kFxGroup; kk += 32) {
+    const long long b = __double_as_longlong(tile[kk]) & 0x7fffffffffffffffLL;
+    mb = b > mb ? b : mb;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long b = __shfl_xor_sync(0xffffffffu, mb, o);
+    mb = b > mb ? b : mb;
+  }
+  const double u = fx_unit(__longlong_as_double(mb));
+  if (lane == 0) D.u[(long long)pr * D.ngroups + g] = u;
+  const double scale24 = 0x1p24 / u;            // a power of two: exact
+  for (int kk = lane; kk < kFxGroup && k0 + kk < K; kk += 32) {
+    __nv_bfloat16 d[kFxSlices];
+    fx_digits(tile[kk], scale24, d);
+    const long long o = (long long)pr * D.ld + k0 + kk;
+#pragma unroll
+    for (int i = 0; i < kFxSlices; ++i) ((__nv_bfloat16*)D.s[i])[o] = d[i];
+  }
+}
+}  // namespace
+
+int fx_mblock(int nb, int na, long long nov) {
+  const long long sp = fx_pad(nov);
+  const long long per_m = (long long)fx_nsplit((int)fx_pad(na)) * nb * nov * 8 + 2 * (long long)fx_mat_bytes(nb, sp);
+  return (int)std::max<long long>(1, std::min<long long>(nb, kFxBlockBytes / std::max<long long>(per_m, 1)));
+}
+
+size_t fx_sigma_bytes(int nb, int na, long long nov, int mb) {
+  const long long nap = fx_pad(na), sp = fx_pad(nov);
+  size_t t = 0;
+  t += fx_mat_bytes((long long)nb * nb, nap);                            // B^T
+  t += fx_mat_bytes(nov, nap);                                           // R^T
+  t += (size_t)fx_nsplit((int)nap) * mb * nb * nov * sizeof(double);     // w of a block
+  t += 2 * fx_mat_bytes(nb, (long long)mb * sp) + 1024;                  // sliced w, g*w
+  return t;
+}
+
+void fx_bufs_carve(FxBufs& f, int nb, int na, long long nov, int mb, void* base) {
+  const long long nap = fx_pad(na);
+  char* p = (char*)base;
+  f.mb = mb;
+  f.Bt = fx_mat_carve(p, (long long)nb * nb, nap);
+  p += fx_mat_bytes((long long)nb * nb, nap);
+  f.Rt = fx_mat_carve(p, nov, nap);
+  p += fx_mat_bytes(nov, nap);
+  f.wbuf = (double*)p;
+  p += (size_t)fx_nsplit((int)nap) * mb * nb * nov * sizeof(double);
+  f.wp_base = (void*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
+}
+
+int stage_sigma_fx(Exec& ex, MolBuf& m, FxBufs& f, Scratch& s, double eta) {
+  const int nb = m.nb, na = m.na, no = m.no;
+  const long long nov = m.nov, nn = (long long)nb * nb;
+  const long long nap = fx_pad(na), sp = fx_pad(nov);
+  // R^T: element (s, P) = R[P][s];  B^T: element ((m, p), P) = B[P][m][p]
+  fx_split(ex, m.R, nov, na, 1, nov, nullptr, f.Rt);
+  fx_split(ex, m.B, nn, na, 1, nn, nullptr, f.Bt);
+  const int nsw = fx_nsplit((int)nap);
+  const int max_splits = (int)std::max<long long>(1, (long long)s.splitk_cap / std::max<long long>(nn, 1));
+  bool first = true;
+  for (int m0 = 0; m0 < nb; m0 += f.mb) {
+    const int cnt = std::min(f.mb, nb - m0);
+    const long long rows = (long long)cnt * nb;
+    FxGemm gw;
+    gw.M = (int)rows; gw.N = (int)nov; gw.K = (int)nap;
+    gw.A = fx_rows(f.Bt, (long long)m0 * nb, rows);
+    gw.B = f.Rt;
+    gw.out = f.wbuf;
+    gw.out_ld = rows;
+    gw.split_stride = rows * nov;
+    gw.col_major = true;
+    int r = fx_gemm(ex, gw);
+    if (r) return r;
+    // slices of w and g*w over K = (mm, s), rows p
+    const long long K = (long long)cnt * sp;
+    FxMat W = fx_mat_carve(f.wp_base, nb, K);
+    FxMat P = fx_mat_carve((char*)f.wp_base + ((fx_mat_bytes(nb, K) + 255) / 256 * 256), nb, K);
+    {
+      KScope ks(ex, MOLGW_K_SIGMA);
+      const size_t shm = 2 * kSigRows * kFxGroup * sizeof(double);
+      cudaFuncSetAttribute(k_fx_sigma_slices, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      dim3 grid(ceil_div(nb, kSigRows), W.ngroups);
+      k_fx_sigma_slices<<<grid, 256, shm, ex.st>>>(f.wbuf, nsw, rows * nov, rows, (int)sp, (int)nov, nb, no, m0, cnt,
+                                                   m.eps, m.Om, eta * eta, W, P);
+    }
+    // S += P W^T over K, at most max_splits K groups per launch
+    const long long kmax = (long long)max_splits * kFxGroup;
+    for (long long k0 = 0; k0 < K; k0 += kmax) {
+      FxGemm gs;
+      gs.M = nb; gs.N = nb;
+      gs.K = (int)std::min(kmax, K - k0);
+      gs.k0 = (int)k0;
+      gs.A = P; gs.B = W;
+      gs.out = s.splitk;
+      gs.out_ld = nb;
+      gs.split_stride = nn;
+      gs.col_major = true;
+      r = fx_gemm(ex, gs);
+      if (r) return r;
+      fx_reduce_cm(ex, s.splitk, fx_nsplit(gs.K), nn, nb, nb, s.S, nb, first ? 0.0 : 1.0);
+      first = false;
+    }
+  }
+  symmetrize(ex, s.S, nb, m.sigc);
+  return MOLGW_OK;
+}
+
+}  // namespace molgw

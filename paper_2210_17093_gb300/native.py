@@ -15,7 +15,7 @@ import numpy as np
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libmolgw_gb300.so")
 
-PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2, "bf16x6": 3}
+PREC = {"fp64": 0, "bf16x3": 1, "tf32x3": 2, "bf16x6": 3, "bf16x10": 4}
 FLAG_FULL_XPY = 1
 FLAG_KTIMING = 2
 FLAG_GRAPH = 4
@@ -34,7 +34,8 @@ EXPORTS = ["molgw_b200_create", "molgw_b200_set_ri", "molgw_b200_set_orbitals", 
            "molgw_b200_sigma", "molgw_b200_qs_step", "molgw_b200_sync", "molgw_b200_fetch",
            "molgw_b200_rpa_matrix", "molgw_b200_eigh", "molgw_b200_kernel_stats",
            "molgw_b200_launch_count", "molgw_b200_set_timing", "molgw_b200_destroy",
-           "molgw_b200_status_string", "molgw_b200_eigh_noalloc", "molgw_b200_graph_replays"]
+           "molgw_b200_status_string", "molgw_b200_eigh_noalloc", "molgw_b200_graph_replays",
+           "molgw_b200_tc_gemm"]
 NOALLOC_NMAX = 256
 
 
@@ -78,6 +79,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "molgw_b200_kernel_stats": ([vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double), ip], ip),
         "molgw_b200_launch_count": ([vp], ctypes.c_int64),
         "molgw_b200_graph_replays": ([vp], ctypes.c_int64),
+        "molgw_b200_tc_gemm": ([vp, ip, ip, ip, vp, vp, vp], ip),
         "molgw_b200_set_timing": ([vp, ctypes.c_uint32], ip),
         "molgw_b200_destroy": ([vp], ip),
         "molgw_b200_status_string": ([ip], ctypes.c_char_p),
@@ -216,6 +218,13 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self._lib.molgw_b200_launch_count(self._hh()))
+
+    def tc_gemm(self, A, B, C):
+        """C[M][N] = sum_k A[m][k] B[n][k] on the context's split-precision engine."""
+        M, K = A.shape
+        N = B.shape[0]
+        _check(self._lib.molgw_b200_tc_gemm(self._hh(), M, N, K, _ptr(A, M * K), _ptr(B, N * K), _ptr(C, M * N)),
+               "tc_gemm")
 
     def graph_replays(self) -> int:
         """qs_step calls served from a captured graph (-1: capture failed, graphs off)."""

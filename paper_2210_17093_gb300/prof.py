@@ -4,7 +4,10 @@
         float64 symmetric eigensolve of a random N x N matrix (tridiagonalisation,
         bisection, twisted vectors, full back-transformation) through molgw_b200_eigh;
     python -m paper_2210_17093_gb300.prof qsgw NB NO NA PRECISION [REPS]
-        qsGW iterations of one synthetic molecule (seed 1) at the given precision.
+        qsGW iterations of one synthetic molecule (seed 1) at the given precision;
+    python -m paper_2210_17093_gb300.prof batch PRECISION LANES [REPS]
+        qsGW iterations of the 64-molecule ragged batch (n_basis ~ U{40..160},
+        seeds 100-163) as one mol = -1 call on LANES concurrent streams.
 
 Each prints the per-kernel-class event times of every repetition.
 """
@@ -61,10 +64,34 @@ def qsgw(nb: int, no: int, na: int, precision: str, reps: int = 2) -> None:
                   flush=True)
 
 
+def batch(precision: str, lanes: int, reps: int = 2) -> None:
+    import numpy as np
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import synthetic as sy
+
+    from . import Context, FLAG_KTIMING
+    mols = sy.config_molecules("D")
+    with Context(precision=precision, max_mols=len(mols), flags=FLAG_KTIMING, eta=sy.ETA, lanes=lanes) as ctx:
+        for k, m in enumerate(mols):
+            ctx.set_ri(k, m["n_basis"], m["n_aux"], np.ascontiguousarray(m["L"]))
+            ctx.set_orbitals(k, m["n_occ"], np.ascontiguousarray(m["eps"]), np.ascontiguousarray(m["C"]))
+        ctx.sync()
+        for r in range(reps):
+            ctx.kernel_stats(reset=True)
+            t = time.perf_counter()
+            ctx.qs_step(-1)
+            ctx.sync()
+            print(f"batch {precision} lanes={lanes} rep {r}: {(time.perf_counter() - t) * 1e3:.1f} ms", _stats(ctx),
+                  flush=True)
+
+
 if __name__ == "__main__":
     a = sys.argv[1:]
     if a and a[0] == "eigh":
         eigh(int(a[1]), int(a[2]) if len(a) > 2 else 1)
+    elif a and a[0] == "batch":
+        batch(a[1], int(a[2]), int(a[3]) if len(a) > 3 else 2)
     elif a and a[0] == "qsgw":
         qsgw(int(a[1]), int(a[2]), int(a[3]), a[4], int(a[5]) if len(a) > 5 else 2)
     else:

@@ -1,0 +1,145 @@
+"""Fixed-point split precision (MOLGW_PREC_BF16X10) on the BF16 tensor cores.
+
+The engine writes each value of a (row, 1024-element K group) as four integer
+BF16 slices times one power of two, sums the slice products of each level in
+float32 over 256-element chunks (every partial sum an integer below 2^24, so
+exact), combines the levels in 64-bit integers and rounds once per group to
+float64.  `fx_model` restates that arithmetic on the CPU; the GPU must agree
+with it bit for bit, which checks that the tensor cores' float32 accumulation
+is exact on such integers.  The qsGW pass with (d)+(e) on this engine must meet
+the mixed-path tolerances of the method: QP energies within 1 meV of the float64
+oracle and Sigma within 1e-6 relative.
+"""
+import numpy as np
+import pytest
+
+import synthetic as sy
+from helpers import lib_context, load_mol, rel_max
+from oracle import qsgw
+
+pytestmark = pytest.mark.gpu
+ETA = sy.ETA
+MEV = 1e-3 / 27.211386245988       # Ha
+
+
+def fx_split_model(X, group=1024, kblock=64):
+    """Scales u[row, group] and the four integer slices of X (rows x K)."""
+    rows, K = X.shape
+    kp = -(-K // kblock) * kblock
+    Xp = np.zeros((rows, kp))
+    Xp[:, :K] = X
+    ng = -(-kp // group)
+    u = np.empty((rows, ng))
+    sl = np.zeros((4, rows, kp))
+    for g in range(ng):
+        blk = Xp[:, g * group:(g + 1) * group]
+        mx = np.abs(blk).max(axis=1)
+        _, e = np.frexp(mx)
+        e = np.where(mx > 0, e, 0)
+        u[:, g] = np.ldexp(1.0, e - 7)
+        T = np.rint(blk * (2.0 ** 24 / u[:, g])[:, None]).astype(np.int64)
+        for i in (3, 2, 1):                          # balanced base-256 digits
+            d = ((T + 128) & 255) - 128
+            sl[i, :, g * group:(g + 1) * group] = d
+            T = (T - d) >> 8
+        sl[0, :, g * group:(g + 1) * group] = T
+    assert np.abs(sl).max() <= 128
+    return sl, u, kp
+
+
+def fx_model(A, B, chunk=256, group=1024):
+    """The engine's arithmetic: exact level sums per chunk, one rounding per group,
+    groups summed in order."""
+    sa, ua, kp = fx_split_model(A)
+    sb, ub, _ = fx_split_model(B)
+    C = np.zeros((A.shape[0], B.shape[0]))
+    for g in range(-(-kp // group)):
+        V = np.zeros_like(C)                                   # exact: |V| < 2^53
+        for c0 in range(g * group, min(kp, (g + 1) * group), chunk):
+            c1 = min(kp, c0 + chunk)
+            for lev in range(4):
+                L = sum(sa[a][:, c0:c1] @ sb[lev - a][:, c0:c1].T for a in range(lev + 1))
+                assert np.abs(L).max() <= 2.0 ** 24
+                V += L * 2.0 ** (24 - 8 * lev)
+        C = C + V * 2.0 ** -24 * ua[:, g][:, None] * ub[:, g][None, :]
+    return C
+
+
+@pytest.mark.parametrize("M,N,K", [(64, 48, 100), (200, 130, 2500), (300, 70, 1024)])
+def test_fx_gemm_bitwise_model(M, N, K):
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K)) * np.exp(-np.arange(K) / 300.0)[None, :]   # decaying along K
+    B = rng.standard_normal((N, K)) * 10.0 ** rng.uniform(-3, 3, size=(N, 1))  # rows of mixed scale
+    C = np.empty((M, N))
+    with lib_context(precision="bf16x10") as ctx:
+        ctx.tc_gemm(A, B, C)
+    assert np.array_equal(C, fx_model(A, B))
+    ref = A @ B.T
+    bound = 2.0 ** -30 * K * np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=1)[None, :]
+    assert np.all(np.abs(C - ref) <= bound)
+
+
+def test_fx_gemm_largest_level_sums():
+    """Values at the slice limits (y = 127.5 -> digits 127, 128 ... or -128 in the
+    lower places): level sums of 256-element chunks reach 2^22 .. 2^23 and must
+    stay exact."""
+    K = 1024
+    A = np.full((128, K), 127.5 / 128.0)
+    A[1::2] *= -1.0
+    B = np.full((64, K), 127.5 / 128.0)
+    C = np.empty((128, 64))
+    with lib_context(precision="bf16x10") as ctx:
+        ctx.tc_gemm(A, B, C)
+    assert np.array_equal(C, fx_model(A, B))
+    assert np.array_equal(C, A @ B.T)
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 3e-5), ("tf32x3", 1.5e-5), ("bf16x6", 1.5e-5)])
+def test_float_split_gemm_accuracy(prec, tol):
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((150, 700))
+    B = rng.standard_normal((90, 700))
+    C = np.empty((150, 90))
+    with lib_context(precision=prec) as ctx:
+        ctx.tc_gemm(A, B, C)
+    assert rel_max(C, A @ B.T) < tol
+
+
+@pytest.mark.parametrize("nb,no,na,seed", [(24, 5, 72, 0), (71, 13, 150, 2), (100, 20, 300, 1)])
+def test_bf16x10_pass_within_1meV(nb, no, na, seed):
+    m = sy.molecule(nb, no, na, seed)
+    r = qsgw.qsgw_pass(m["L"], m["eps"], m["C"], no, ETA)
+    nov = no * (nb - no)
+    with lib_context(precision="bf16x10", eta=ETA) as ctx:
+        load_mol(ctx, 0, m)
+        om = np.empty(nov)
+        ctx.rpa(0, om)
+        sx = np.empty((nb, nb))
+        sc = np.empty((nb, nb))
+        ctx.sigma(0, sx, sc)
+        eps = np.empty(nb)
+        ctx.qs_step(0, eps)
+    assert np.max(np.abs(om - r["Omega"])) < 1e-8
+    assert rel_max(sx, r["sigma_x"]) < 1e-12
+    assert rel_max(sc, r["sigma_c"]) < 1e-6
+    assert np.max(np.abs(eps - r["eps_new"])) < 1.0 * MEV
+
+
+def test_bf16x10_bench_size_within_1meV():
+    m = sy.molecule(200, 40, 600, 1)
+    r = qsgw.qsgw_pass(m["L"], m["eps"], m["C"], 40, ETA)
+    with lib_context(precision="bf16x10", eta=ETA) as ctx:
+        load_mol(ctx, 0, m)
+        sc = np.empty((200, 200))
+        ctx.sigma(0, None, sc)
+        eps = np.empty(200)
+        ctx.qs_step(0, eps)
+    assert rel_max(sc, r["sigma_c"]) < 1e-6
+    assert np.max(np.abs(eps - r["eps_new"])) < 1.0 * MEV
+
+
+def test_bf16x10_rejects_tc_ab():
+    from paper_2210_17093_gb300 import MolgwError, FLAG_TC_AB
+    with pytest.raises(MolgwError) as e:
+        lib_context(precision="bf16x10", flags=FLAG_TC_AB)
+    assert e.value.code == -1
