@@ -86,7 +86,12 @@ enum molgw_flags {
                                     graph (all lanes of mol = -1 in one graph) and replayed while the
                                     buffers and the set of molecules stay the same                  */
   MOLGW_FLAG_USE_STREAM = 1u << 3, /* run on opts.stream even when it is NULL (the legacy default stream) */
-  MOLGW_FLAG_TC_AB = 1u << 4       /* with BF16X3/TF32X3: stages (a) and (b) on the tensor cores too */
+  MOLGW_FLAG_TC_AB = 1u << 4,      /* with BF16X3/TF32X3: stages (a) and (b) on the tensor cores too */
+  MOLGW_FLAG_EIG_TC = 1u << 5      /* the trailing SYR2K update of the tridiagonalisation on the
+                                      tensor cores: 7 fixed-point BF16 digits per value (56 bits,
+                                      values within 4x of their group maximum exact), exact sums,
+                                      one float64 rounding -- float64 accuracy in the normwise
+                                      sense, not float64 arithmetic; any precision            */
 };
 
 typedef struct {
@@ -211,12 +216,14 @@ int molgw_b200_set_timing(molgw_ctx ctx, uint32_t class_mask);
  * replay counts the kernels the graph holds). */
 int64_t molgw_b200_launch_count(molgw_ctx ctx);
 
-/* Library extension (the paper has no counterpart): the split-precision GEMM
- * of the context's precision (not MOLGW_PREC_FP64, else MOLGW_E_ARG) on its own,
- * C[m][n] = sum_k A[m][k] B[n][k] for row-major float64 A[M][K], B[N][K], C[M][N]
- * (host or device memory), so that the tensor-core arithmetic of (d) and (e) can
- * be checked against float64.  Allocates temporaries and synchronises. */
-int molgw_b200_tc_gemm(molgw_ctx ctx, int M, int N, int K, const double* A, const double* B, double* C);
+/* Library extension (the paper has no counterpart): a tensor-core GEMM on its
+ * own, C[m][n] = sum_k A[m][k] B[n][k] for row-major float64 A[M][K], B[N][K],
+ * C[M][N] (host or device memory), so that the tensor-core arithmetic can be
+ * checked against float64.  digits = 0: the split of the context's precision
+ * (not MOLGW_PREC_FP64, else MOLGW_E_ARG); digits = 4 or 7: the fixed-point
+ * engine with that many digits (any precision).  Allocates temporaries and
+ * synchronises. */
+int molgw_b200_tc_gemm(molgw_ctx ctx, int digits, int M, int N, int K, const double* A, const double* B, double* C);
 
 /* Library extension (the paper has no counterpart): number of qs_step calls
  * served by replaying a captured graph (MOLGW_FLAG_GRAPH); -1 once a capture

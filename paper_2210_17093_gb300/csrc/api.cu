@@ -23,6 +23,8 @@ struct Lane {
   void* tco_base = nullptr;
   size_t tco_cap = 0;         // doubles
   size_t pk_fail = 0;         // packed-residue request that did not fit (not retried)
+  void* eigfx = nullptr;      // MOLGW_FLAG_EIG_TC: fixed-point operands of the trailing updates
+  long long eigfx_rows = 0, eigfx_cols = 0;
 };
 
 constexpr int kMaxLanes = 8;
@@ -162,6 +164,7 @@ void lane_free(Lane& l) {
   if (l.scr.base) cudaFree(l.scr.base);
   if (l.scr.pk_base) cudaFree(l.scr.pk_base);
   if (l.tco_base) cudaFree(l.tco_base);
+  if (l.eigfx) cudaFree(l.eigfx);
   eig_work_free(l.eig);
   if (l.done) cudaEventDestroy(l.done);
   if (l.own_stream) cudaStreamDestroy(l.st);
@@ -176,6 +179,38 @@ int ensure_eig(molgw_ctx c, Lane& l, int n, int ncols) {
   int r = eig_work_alloc(l.eig, nn, nc);
   if (r) { l.eig_n = l.eig_cols = 0; return r; }
   l.eig_n = nn; l.eig_cols = nc;
+  return MOLGW_OK;
+}
+
+bool use_eig_tc(molgw_ctx c) { return (c->opts.flags & MOLGW_FLAG_EIG_TC) != 0; }
+
+// Attach (allocating if needed) the fixed-point arena of the eigensolver's
+// trailing updates to the lane's workspace (MOLGW_FLAG_EIG_TC), sized for eig_n.
+int ensure_eigfx(molgw_ctx c, Lane& l) {
+  if (!use_eig_tc(c)) {
+    l.eig.fx = nullptr;
+    l.eig.fx_rows = 0;
+    return MOLGW_OK;
+  }
+  const long long rows = l.eig_n, cols = l.eig_cols;
+  if (rows > l.eigfx_rows || cols > l.eigfx_cols) {
+    if (l.ex.capturing) return MOLGW_E_STATE;
+    cudaStreamSynchronize(l.st);
+    ++c->gen;
+    if (l.eigfx) cudaFree(l.eigfx);
+    l.eigfx = nullptr;
+    l.eigfx_rows = l.eigfx_cols = 0;
+    if (cudaMalloc(&l.eigfx, eig_fx_bytes(rows, cols)) != cudaSuccess) {
+      cudaGetLastError();
+      l.eigfx = nullptr;
+      return MOLGW_E_NOMEM;
+    }
+    l.eigfx_rows = rows;
+    l.eigfx_cols = cols;
+  }
+  l.eig.fx = l.eigfx;
+  l.eig.fx_rows = l.eigfx_rows;
+  l.eig.fx_cols = l.eigfx_cols;
   return MOLGW_OK;
 }
 
@@ -266,6 +301,7 @@ int lane_fit(molgw_ctx c, Lane& l, const MolBuf& m) {
   int r = ensure_scratch(c, l, m.nb, m.na, m.nov);
   if (!r) r = ensure_eig(c, l, (int)std::max<long long>(m.nov, m.nb),
                          std::max<int>(std::max(m.na, m.nb), full ? (int)m.nov : 0));
+  if (!r) r = ensure_eigfx(c, l);
   if (!r) r = ensure_tco(c, l, m.nb, m.na, m.nov);
   return r;
 }
@@ -788,6 +824,7 @@ int molgw_b200_eigh(molgw_ctx c, int n, const double* A, double* w, double* Z) {
   DeviceGuard g(c->device);
   Lane& l = c->lanes[0];
   int r = ensure_eig(c, l, n, n);
+  if (!r) r = ensure_eigfx(c, l);
   if (r) return r;
   std::vector<void*> tmp;
   int err = 0;
@@ -823,8 +860,11 @@ int molgw_b200_kernel_stats(molgw_ctx c, int64_t* launches, double* ms, int rese
 
 int64_t molgw_b200_launch_count(molgw_ctx c) { return c ? c->timer.total_launches : 0; }
 
-int molgw_b200_tc_gemm(molgw_ctx c, int M, int N, int K, const double* A, const double* B, double* C) {
-  if (!c || M < 1 || N < 1 || K < 1 || !A || !B || !C || !use_tc(c)) return MOLGW_E_ARG;
+int molgw_b200_tc_gemm(molgw_ctx c, int digits, int M, int N, int K, const double* A, const double* B, double* C) {
+  if (!c || M < 1 || N < 1 || K < 1 || !A || !B || !C) return MOLGW_E_ARG;
+  if (digits != 0 && digits != 4 && digits != 7) return MOLGW_E_ARG;
+  if (digits == 0 && !use_tc(c)) return MOLGW_E_ARG;
+  if (digits == 0 && use_fx(c)) digits = kFxSlices;
   DeviceGuard g(c->device);
   Exec& ex = c->lanes[0].ex;
   std::vector<void*> tmp;
@@ -835,14 +875,14 @@ int molgw_b200_tc_gemm(molgw_ctx c, int M, int N, int K, const double* A, const 
   if (err) { free_all(tmp); return err; }
   int r = copy_in(c, dA, A, (size_t)M * K);
   if (!r) r = copy_in(c, dB, B, (size_t)N * K);
-  if (!r && use_fx(c)) {
+  if (!r && digits > 0) {
     const long long kp = fx_pad(K);
     const int ns = fx_nsplit((int)kp);
-    double* ma = dalloc(tmp, (fx_mat_bytes(M, kp) + 7) / 8, &err);
-    double* mb = dalloc(tmp, (fx_mat_bytes(N, kp) + 7) / 8, &err);
+    double* ma = dalloc(tmp, (fx_mat_bytes(M, kp, digits) + 7) / 8, &err);
+    double* mb = dalloc(tmp, (fx_mat_bytes(N, kp, digits) + 7) / 8, &err);
     double* part = dalloc(tmp, (size_t)ns * M * N, &err);
     if (err) { free_all(tmp); return err; }
-    const FxMat fa = fx_mat_carve(ma, M, kp), fb = fx_mat_carve(mb, N, kp);
+    const FxMat fa = fx_mat_carve(ma, M, kp, digits), fb = fx_mat_carve(mb, N, kp, digits);
     fx_split(ex, dA, M, K, K, 1, nullptr, fa);
     fx_split(ex, dB, N, K, K, 1, nullptr, fb);
     FxGemm gm;

@@ -122,6 +122,11 @@ struct EigWork {
   double *tmp1 = nullptr, *tmp2 = nullptr;  // 64 x ncols_max each
   int ncols_max = 0;
   bool owned = false;          // allocated by eig_work_alloc (freed by eig_work_free)
+  // with MOLGW_FLAG_EIG_TC: arena of the 7-digit fixed-point operands of the
+  // trailing updates (two fx_mat_bytes(fx_rows, 128, 7)), else nullptr
+  void* fx = nullptr;
+  long long fx_rows = 0;       // matrices up to fx_rows (n)
+  long long fx_cols = 0;       // back-transformations of up to fx_cols columns
 };
 // Workspace sizes in doubles for matrices up to n and back-transformations of
 // up to ncols (>= 64) columns at a time.

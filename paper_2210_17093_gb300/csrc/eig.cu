@@ -15,6 +15,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "fx.cuh"
 
 namespace molgw {
 
@@ -345,11 +346,73 @@ void build_wy(Exec& ex, EigWork& w, int n, const double* A) {
   k_wy_t<<<npan, NBP, 0, ex.st>>>(G, w.tau, n, w.Tm);
 }
 
+namespace {
+
+// Fixed-point layout of the back-transformation operands inside w.fx.
+struct BtFx {
+  FxMat vt, xs, vr, t2;
+};
+BtFx bt_fx(const EigWork& w, long long m, int nc) {
+  const long long np = fx_pad(w.fx_rows), mp = fx_pad(m);
+  char* p = (char*)w.fx;
+  BtFx b;
+  b.vt = fx_mat_carve(p, 64, mp, 7);
+  p += fx_mat_bytes(64, np, 7);
+  b.xs = fx_mat_carve(p, nc, mp, 7);
+  p += fx_mat_bytes(w.fx_cols, np, 7);
+  b.vr = fx_mat_carve(p, m, 64, 7);
+  p += fx_mat_bytes(w.fx_rows, 64, 7);
+  b.t2 = fx_mat_carve(p, nc, 64, 7);
+  return b;
+}
+
+// One panel of apply_q on the 7-digit engine: tmp1 = V^T X[k0:, :] (one launch
+// per 1024-wide K group, accumulated in order), tmp2 = T^(T) tmp1 in float64,
+// X[k0:, :] -= V tmp2.
+void apply_panel_fx(Exec& ex, EigWork& w, int n, const double* V, int nbp, int m, double* Xk, long long sr,
+                    long long sc, int nc, const double* T, int trans) {
+  BtFx b = bt_fx(w, m, nc);
+  const int kp = (int)fx_pad(m);
+  fx_split(ex, V, nbp, m, n, 1, nullptr, b.vt, MOLGW_K_BACKTRANSFORM);     // (c, r) = V(r, c)
+  fx_split(ex, Xk, nc, m, sc, sr, nullptr, b.xs, MOLGW_K_BACKTRANSFORM);   // (col, r) = X(r, col)
+  for (int g0 = 0; g0 < kp; g0 += kFxGroup) {
+    FxGemm g;
+    g.M = nbp; g.N = nc; g.K = std::min(kFxGroup, kp - g0); g.k0 = g0;
+    g.A = b.vt; g.B = b.xs;
+    g.out = w.tmp1; g.out_ld = nc;
+    g.accumulate = g0 > 0;
+    g.kclass = MOLGW_K_BACKTRANSFORM;
+    fx_gemm(ex, g);
+  }
+  GemmF64 g2;
+  g2.M = nbp; g2.N = nc; g2.K = nbp;
+  g2.A = T; if (trans) { g2.sa_m = 1; g2.sa_k = NBP; } else { g2.sa_m = NBP; g2.sa_k = 1; }
+  g2.B = w.tmp1; g2.sb_k = nc; g2.sb_n = 1;
+  g2.C = w.tmp2; g2.sc_m = nc; g2.sc_n = 1;
+  g2.kclass = MOLGW_K_BACKTRANSFORM;
+  gemm_f64(ex, g2);
+  fx_split(ex, V, m, nbp, 1, n, nullptr, b.vr, MOLGW_K_BACKTRANSFORM);      // (r, c) = V(r, c)
+  fx_split(ex, w.tmp2, nc, nbp, 1, nc, nullptr, b.t2, MOLGW_K_BACKTRANSFORM);  // (col, c) = tmp2(c, col)
+  FxGemm g3;
+  g3.M = m; g3.N = nc; g3.K = 64;
+  g3.A = b.vr; g3.B = b.t2;
+  g3.out = Xk;
+  g3.col_major = (sr == 1);
+  g3.out_ld = (sr == 1) ? sc : sr;
+  g3.accumulate = true;
+  g3.alpha = -1.0;
+  g3.kclass = MOLGW_K_BACKTRANSFORM;
+  fx_gemm(ex, g3);
+}
+
+}  // namespace
+
 void apply_q(Exec& ex, EigWork& w, int n, const double* A, double* X, long long sr, long long sc,
              int ncols, int trans) {
   const int nref = n - 1;
   if (nref <= 0 || ncols <= 0) return;
   const int npan = ceil_div(nref, NBP);
+  const bool fx = w.fx && n <= w.fx_rows && std::min(ncols, w.ncols_max) <= w.fx_cols && (sr == 1 || sc == 1);
   for (int c0 = 0; c0 < ncols; c0 += w.ncols_max) {
     const int nc = std::min(w.ncols_max, ncols - c0);
     double* Xc = X + (long long)c0 * sc;
@@ -360,6 +423,10 @@ void apply_q(Exec& ex, EigWork& w, int n, const double* A, double* X, long long 
       const int m = n - k0;
       const double* V = A + k0 + (long long)k0 * n;     // m x nbp, column-major
       const double* T = w.Tm + (long long)p * NBP * NBP;
+      if (fx && m >= 128) {
+        apply_panel_fx(ex, w, n, V, nbp, m, Xc + (long long)k0 * sr, sr, sc, nc, T, trans);
+        continue;
+      }
       // tmp1 (nbp x nc) = V^T X[k0:, :]
       GemmF64 g1;
       g1.M = nbp; g1.N = nc; g1.K = m;

@@ -1,17 +1,20 @@
 // Fixed-point split GEMM on the BF16 tensor cores with exact float32 sums.
 //
 // Every float64 value x of a row's group of kFxGroup consecutive K elements is
-// written as x ~ u * (s0 + s1 2^-8 + s2 2^-16 + s3 2^-24), where u = 2^(e-7) is
-// one power of two for the (row, group) with max|x| < 2^e, and the slices s_i are
-// the balanced base-256 digits of rint(2^24 x / u), integers in [-128, 128]
-// (exact in BF16).  A product of two slices is an integer
-// below 2^14 in magnitude; the ten slice products with i + j <= 3 are summed per
-// "level" l = i + j in four float32 accumulators over chunks of 256 K elements, so
-// that every partial sum is an integer below 2^24 and the float32 accumulation is
-// exact.  The levels are combined exactly in 64-bit integers and only the result
-// of a group is rounded, to float64: C ~ 2^-24 u_a u_b sum_l 2^(24-8l) L_l.
-// The only approximation is the truncation of x to 32 bits relative to the
-// largest |x| of its (row, group).
+// written with NS base-256 digits: x ~ u * sum_i s_i 2^(-8i), where u = 2^(e-7)
+// is one power of two for the (row, group) with max|x| < 2^e, and the digits s_i
+// are the balanced base-256 digits of rint(2^(8(NS-1)) x / u), integers in
+// [-128, 128] (exact in BF16).  A product of two digits is an integer below 2^14
+// in magnitude; the products with i + j < NS are summed per "level" l = i + j in
+// NS float32 accumulators over chunks of K elements short enough that every
+// partial sum is an integer below 2^24, so the float32 accumulation is exact.
+// The levels are combined exactly in 64-bit integers and only the result of a
+// group is rounded, to float64.  The only approximation is the truncation of x
+// to 8 NS bits relative to the largest |x| of its (row, group).
+//   NS = 4 (MOLGW_PREC_BF16X10): 10 products, 32 bits, 256-element chunks;
+//   NS = 7: 28 products, 56 bits -- every value within a factor 4 of its group's
+//           largest is represented exactly, so the product matches float64
+//           accuracy (normwise); 128-element chunks.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -19,34 +22,37 @@
 
 namespace molgw {
 
-constexpr int kFxSlices = 4;
-constexpr int kFxKBlock = 64;      // K elements per 128-byte swizzle row
-constexpr int kFxChunk = 256;      // K elements per exact float32 sum
+constexpr int kFxSlices = 4;       // digits of the BF16X10 precision
+constexpr int kFxMaxSlices = 7;
+constexpr int kFxKBlock = 64;      // K padding unit of every operand
 constexpr int kFxGroup = 1024;     // K elements per scale u (one CTA's K range)
 
 inline long long fx_pad(long long k) { return (k + kFxKBlock - 1) / kFxKBlock * kFxKBlock; }
 inline int fx_groups(long long ld) { return (int)((ld + kFxGroup - 1) / kFxGroup); }
 
-// rows x ld BF16 slices (ld a multiple of kFxKBlock) and the float64 scale u of
-// each (row, group), at u[row * ngroups + group].
+// rows x ld BF16 digits (ns of them; ld a multiple of kFxKBlock) and the float64
+// scale u of each (row, group), at u[row * ngroups + group].
 struct FxMat {
-  void* s[kFxSlices] = {nullptr, nullptr, nullptr, nullptr};
+  void* s[kFxMaxSlices] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double* u = nullptr;
   long long rows = 0, ld = 0;
   int ngroups = 0;
+  int ns = kFxSlices;
 };
 
-// bytes of an FxMat of rows x ld (ld padded), 256-byte aligned parts
-size_t fx_mat_bytes(long long rows, long long ld);
-// lay an FxMat out over device memory of fx_mat_bytes(rows, ld) bytes
-FxMat fx_mat_carve(void* base, long long rows, long long ld);
+// bytes of an FxMat of rows x ld (ld padded) with ns digits, 256-byte aligned parts
+size_t fx_mat_bytes(long long rows, long long ld, int ns = kFxSlices);
+// lay an FxMat out over device memory of fx_mat_bytes(rows, ld, ns) bytes
+FxMat fx_mat_carve(void* base, long long rows, long long ld, int ns = kFxSlices);
 // rows of an FxMat starting at row r0 (the same K layout)
 FxMat fx_rows(const FxMat& m, long long r0, long long rows);
 
-// C = A B^T over K (a multiple of kFxKBlock, <= A.ld, B.ld).  The K range splits
-// into groups of kFxGroup; group g of the CTA grid writes its float64 result to
-// out + g * split_stride (one group: no partials).  Element (row, col) goes to
-// out[row * out_ld + col], or out[col * out_ld + row] with col_major.
+// C = A B^T over K (a multiple of kFxKBlock, <= A.ld, B.ld); A.ns == B.ns (4 or 7).
+// The K range splits into groups of kFxGroup; group g of the CTA grid writes its
+// float64 result to out + g * split_stride (one group: no partials).  Element
+// (row, col) goes to out[row * out_ld + col], or out[col * out_ld + row] with
+// col_major.  accumulate (one group only): out = out + alpha * C.  lower_only:
+// only elements in 64 x 64 blocks on or below the diagonal (row/64 >= col/64).
 struct FxGemm {
   int M = 0, N = 0, K = 0;
   int k0 = 0;                 // first K element (a multiple of kFxGroup)
@@ -55,20 +61,39 @@ struct FxGemm {
   long long out_ld = 0;
   long long split_stride = 0;
   bool col_major = false;
+  bool accumulate = false;
+  double alpha = 1.0;
+  bool lower_only = false;
+  int kclass = MOLGW_K_GEMM_TC;   // kernel class for launch accounting
 };
 int fx_gemm(Exec& ex, const FxGemm& g);
+// Arena of the 7-digit operands of the eigensolver (MOLGW_FLAG_EIG_TC) for
+// matrices up to n and back-transformations of up to ncols columns: the two
+// 128-wide SYR2K operands, or (later in the same solve) the back-transformation
+// operands V^T, X^T, V, T-product and a block of kFxZBlock eigenvector columns.
+constexpr int kFxZBlock = 2048;
+inline size_t eig_fx_bytes(long long n, long long ncols) {
+  const long long np = fx_pad(n);
+  const size_t syr2k = 2 * fx_mat_bytes(n, 128, 7);
+  const size_t bt = fx_mat_bytes(64, np, 7) + fx_mat_bytes(ncols, np, 7) + fx_mat_bytes(n, 64, 7) +
+                    fx_mat_bytes(ncols, 64, 7) + fx_mat_bytes(n < kFxZBlock ? n : kFxZBlock, np, 7);
+  return syr2k > bt ? syr2k : bt;
+}
+
 // number of K groups (= output splits) of a K range
 inline int fx_nsplit(int K) { return (K + kFxGroup - 1) / kFxGroup; }
 
 // ---------------------------------------------------------------------------
-// The four digits of y = x / u (|y| < 128): T = rint(y 2^24) (one float64 scaling,
-// exact, and one rounding) split into balanced base-256 digits s3, s2, s1 in
-// [-128, 127] and the leading s0 in [-128, 128], y ~ sum_i s_i 2^(-8i), with
+// The NS digits of y = x / u (|y| < 128): T = rint(y 2^(8(NS-1))) (one float64
+// scaling, exact, and one rounding) split into balanced base-256 digits in
+// [-128, 127] below a leading digit in [-128, 128], y ~ sum_i s_i 2^(-8i), with
 // integer arithmetic (the float64 pipe does two operations per value).
-__device__ __forceinline__ void fx_digits(double x, double scale24, __nv_bfloat16* out) {
-  long long T = __double2ll_rn(x * scale24);
+// scale = 2^(8(NS-1)) / u.
+template <int NS>
+__device__ __forceinline__ void fx_digits(double x, double scale, __nv_bfloat16* out) {
+  long long T = __double2ll_rn(x * scale);
 #pragma unroll
-  for (int i = kFxSlices - 1; i > 0; --i) {
+  for (int i = NS - 1; i > 0; --i) {
     const int d = (int)(((T + 128) & 255) - 128);
     out[i] = __float2bfloat16_rn((float)d);
     T = (T - d) >> 8;
@@ -108,8 +133,8 @@ __global__ void k_fx_scale(Src f, long long rows, long long ld, FxMat dst) {
   }
 }
 
-// the slices of a 32-row x kFxTileK tile
-template <class Src>
+// the digits of a 32-row x kFxTileK tile
+template <int NS, class Src>
 __global__ void k_fx_slices(Src f, long long rows, long long ld, FxMat dst) {
   __shared__ double tile[kFxTileK][33];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -120,29 +145,32 @@ __global__ void k_fx_slices(Src f, long long rows, long long ld, FxMat dst) {
   for (int rr = warp; rr < 32; rr += 8) {
     const long long r = r0 + rr;
     if (r >= rows) break;
-    const double scale24 = 0x1p24 / dst.u[r * dst.ngroups + g];   // a power of two: exact
+    const double scale = ldexp(1.0, 8 * (NS - 1)) / dst.u[r * dst.ngroups + g];   // a power of two
 #pragma unroll
     for (int j = 0; j < kFxTileK / 32; ++j) {
       const int k = lane + 32 * j;
       if (c0 + k < ld) {
-        __nv_bfloat16 d[kFxSlices];
-        fx_digits(tile[k][rr], scale24, d);
+        __nv_bfloat16 d[NS];
+        fx_digits<NS>(tile[k][rr], scale, d);
         const long long o = r * dst.ld + c0 + k;
 #pragma unroll
-        for (int i = 0; i < kFxSlices; ++i) ((__nv_bfloat16*)dst.s[i])[o] = d[i];
+        for (int i = 0; i < NS; ++i) ((__nv_bfloat16*)dst.s[i])[o] = d[i];
       }
     }
   }
 }
 
 template <class Src>
-void fx_slice(Exec& ex, const Src& f, long long rows, FxMat dst) {
+void fx_slice(Exec& ex, const Src& f, long long rows, FxMat dst, int kclass = MOLGW_K_MISC) {
   if (rows <= 0) return;
-  KScope ks(ex, MOLGW_K_MISC, 2);
+  KScope ks(ex, kclass, 2);
   dim3 g1(ceil_div(rows, 32), dst.ngroups);
   k_fx_scale<Src><<<g1, 256, 0, ex.st>>>(f, rows, dst.ld, dst);
   dim3 g2(ceil_div(rows, 32), ceil_div(dst.ld, kFxTileK));
-  k_fx_slices<Src><<<g2, 256, 0, ex.st>>>(f, rows, dst.ld, dst);
+  if (dst.ns == 7)
+    k_fx_slices<7, Src><<<g2, 256, 0, ex.st>>>(f, rows, dst.ld, dst);
+  else
+    k_fx_slices<4, Src><<<g2, 256, 0, ex.st>>>(f, rows, dst.ld, dst);
 }
 
 struct FxStrided {
@@ -159,7 +187,7 @@ struct FxStrided {
 // Slice a strided float64 matrix: element (r, k) = src[r*sr + k*sk] for k < cols,
 // zero for cols <= k < dst.ld; row_scale (optional) multiplies row r.
 void fx_split(Exec& ex, const double* src, long long rows, long long cols, long long sr, long long sk,
-              const double* row_scale, FxMat dst);
+              const double* row_scale, FxMat dst, int kclass = MOLGW_K_MISC);
 
 // out[r][c] = beta*out[r][c] + sum_{s<ns} part[s][c][r]  (col-major partials)
 void fx_reduce_cm(Exec& ex, const double* part, int ns, long long split_stride, int M, int N, double* out,

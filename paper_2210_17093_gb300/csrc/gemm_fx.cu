@@ -1,18 +1,22 @@
 // Fixed-point split GEMM (fx.cuh) on tcgen05 for sm_103a.
 //
-// One 128 x 64 output tile and one K group (<= 1024 elements) per CTA; 12 warps:
-//   warp 0   TMA producer: the four BF16 slices of a 128-row A box and a 64-row B
-//            box per 64-element K block (128-byte swizzle) into a 2-stage ring of
-//            96 KB stages;
-//   warp 1   one thread issues tcgen05.mma (kind::f16, M=128, N=64, K=16): per
-//            K step the ten slice products (a, b) with a + b = l accumulate into
-//            level accumulator l (four per buffer); after each 256-element chunk the
+// One 128 x BN output tile and one K group (<= 1024 elements) per CTA; 12 warps:
+//   warp 0   TMA producer: the NS BF16 digit planes of a 128-row A box and a
+//            BN-row B box per K block into a shared-memory ring;
+//   warp 1   one thread issues tcgen05.mma (kind::f16, M=128, N=BN, K=16): per K
+//            step the products of digit planes (a, b) with a + b = l accumulate
+//            into level accumulator l (NS per buffer); after each chunk the
 //            buffer is committed to the epilogue and the other buffer is used;
-//   warp 2   allocates / frees the 512 TMEM columns (2 buffers x 4 levels x 64);
-//   warps 4-11 the epilogue: for each chunk, tcgen05.ld of the four levels of its
-//            32 lanes x 32 columns, conversion to integers (exact) and accumulation
-//            of sum_l 2^(24-8l) L_l in 64-bit integers; after the last chunk one
-//            rounding to float64 and the scales u_a u_b 2^-24.
+//   warp 2   allocates / frees the 512 TMEM columns (2 buffers x NS levels x BN);
+//   warps 4-11 the epilogue: for each chunk, tcgen05.ld of the levels of its 32
+//            lanes x BN/2 columns, conversion to integers (exact) and accumulation
+//            of sum_l 2^(-8l) L_l in 64-bit integers (two words for NS = 7); after
+//            the last chunk one rounding to float64 and the scales u_a u_b.
+// Configurations:
+//   NS = 4: K block 64 elements (128-byte swizzle), BN = 64, 256-element chunks,
+//           2 stages of 96 KB;
+//   NS = 7: K block 32 elements (64-byte swizzle), BN = 32, 128-element chunks,
+//           3 stages of 70 KB.
 // Every wait is bounded; a timeout latches MOLGW_E_TIMEOUT, raises a shared abort
 // flag that ends the other roles' waits, and the CTA still frees its TMEM.
 #include <cuda.h>
@@ -24,18 +28,33 @@ namespace molgw {
 
 namespace {
 
-constexpr int BM = 128, BN = 64;
-constexpr int TA = BM * 128;                       // 16 KB: one A slice box
-constexpr int TB = BN * 128;                       // 8 KB: one B slice box
-constexpr int STAGE = kFxSlices * (TA + TB);       // 96 KB
-constexpr int STAGES = 2;
-constexpr int SMEM = STAGES * STAGE + 1024;
-constexpr int KB_CHUNK = kFxChunk / kFxKBlock;     // 4 K blocks per exact chunk
-constexpr int KB_GROUP = kFxGroup / kFxKBlock;     // 16 K blocks per group
+constexpr int BM = 128;
 constexpr int TMEM_COLS = 512;
 constexpr int NT = 384;
 constexpr int EPI_THREADS = 256;
 constexpr long long SPIN_LIMIT = 1LL << 26;
+
+template <int NS> struct FxT;
+template <> struct FxT<4> {
+  static constexpr int KE = 64, BN = 64, CHUNK = 256, STAGES = 2, LAYOUT = 2, SBO = 1024;
+};
+template <> struct FxT<7> {
+  static constexpr int KE = 32, BN = 32, CHUNK = 128, STAGES = 3, LAYOUT = 4, SBO = 512;
+};
+template <int NS> struct FxK : FxT<NS> {
+  using B = FxT<NS>;
+  static constexpr int ROWB = B::KE * 2;                 // bytes per K row of a box
+  static constexpr int TA = BM * ROWB, TB = B::BN * ROWB;
+  static constexpr int STAGE = NS * (TA + TB);
+  static constexpr int SMEM = B::STAGES * STAGE + 1024;
+  static constexpr int KSTEPS = B::KE / 16;
+  static constexpr int KB_CHUNK = B::CHUNK / B::KE;
+  static constexpr int KB_GROUP = kFxGroup / B::KE;
+  static constexpr int LEVEL_COLS = NS * B::BN;          // TMEM columns of one buffer
+  static constexpr int CPT = B::BN / 2;                  // epilogue columns per thread
+  static_assert(2 * LEVEL_COLS <= TMEM_COLS, "two accumulator buffers must fit in TMEM");
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -74,14 +93,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
-// K-major operand, 128-byte swizzle, 8-row groups 1024 B apart
-__device__ __forceinline__ uint64_t sdesc_sw128(const void* p) {
+// K-major operand with a LAYOUT swizzle (2: 128-byte, 4: 64-byte), 8-row groups SBO bytes apart
+template <int LAYOUT, int SBO>
+__device__ __forceinline__ uint64_t sdesc(const void* p) {
   const uint32_t a = smem_u32(p);
   uint64_t d = (uint64_t)((a & 0x3FFFF) >> 4);
   d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)(SBO >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)LAYOUT << 61;
   return d;
 }
 __device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
@@ -99,30 +119,33 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
                : "r"(taddr));
 }
 
+struct FxMaps {
+  CUtensorMap a[kFxMaxSlices], b[kFxMaxSlices];
+};
+
 struct FxParams {
-  int M, N, nkb, kb0;
+  int M, N, nkb, kb0;                 // K blocks (of the configuration's KE) in the range, first one
   const double* ua;
   int a_ngroups;
   const double* ub;
   int b_ngroups;
   double* out;
   long long out_ld, split_stride;
-  int col_major;
+  int col_major, accumulate, lower_only;
+  double alpha;
   int* status;
 };
 
-__global__ void __launch_bounds__(NT, 1)
-    fx_gemm_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
-                   const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mA3,
-                   const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
-                   const __grid_constant__ CUtensorMap mB2, const __grid_constant__ CUtensorMap mB3, FxParams p) {
-  const CUtensorMap* mapA[4] = {&mA0, &mA1, &mA2, &mA3};
-  const CUtensorMap* mapB[4] = {&mB0, &mB1, &mB2, &mB3};
+template <int NS>
+__global__ void __launch_bounds__(NT, 1) fx_gemm_kernel(const __grid_constant__ FxMaps maps, FxParams p) {
+  using C = FxK<NS>;
+  constexpr int BN = C::BN, STAGES = C::STAGES;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, gz = blockIdx.z;
-  const int kbl0 = gz * KB_GROUP;                           // first K block of this CTA (range-relative)
-  const int nk = min(p.nkb - kbl0, KB_GROUP);
-  const int nchunk = (nk + KB_CHUNK - 1) / KB_CHUNK;
-  const int group = (p.kb0 + kbl0) / KB_GROUP;              // scale group index of the operands
+  if (p.lower_only && n0 / 64 > (m0 + BM - 1) / 64) return;   // only strictly-upper 64-blocks
+  const int kbl0 = gz * C::KB_GROUP;                        // first K block of this CTA (range-relative)
+  const int nk = min(p.nkb - kbl0, C::KB_GROUP);
+  const int nchunk = (nk + C::KB_CHUNK - 1) / C::KB_CHUNK;
+  const int group = (p.kb0 + kbl0) / C::KB_GROUP;           // scale group index of the operands
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -162,13 +185,13 @@ __global__ void __launch_bounds__(NT, 1)
         fail(p.status, abort);
         break;
       }
-      uint8_t* st = smem + s * STAGE;
-      mbar_expect_tx(&full[s], STAGE);
-      const int x = (p.kb0 + kbl0 + i) * kFxKBlock;
+      uint8_t* st = smem + s * C::STAGE;
+      mbar_expect_tx(&full[s], C::STAGE);
+      const int x = (p.kb0 + kbl0 + i) * C::KE;
 #pragma unroll
-      for (int sl = 0; sl < kFxSlices; ++sl) {
-        tma_load_2d(st + sl * TA, mapA[sl], &full[s], x, m0);
-        tma_load_2d(st + kFxSlices * TA + sl * TB, mapB[sl], &full[s], x, n0);
+      for (int sl = 0; sl < NS; ++sl) {
+        tma_load_2d(st + sl * C::TA, &maps.a[sl], &full[s], x, m0);
+        tma_load_2d(st + NS * C::TA + sl * C::TB, &maps.b[sl], &full[s], x, n0);
       }
       issued = i + 1;
     }
@@ -198,7 +221,7 @@ __global__ void __launch_bounds__(NT, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int kbn = min(KB_CHUNK, nk - c * KB_CHUNK);
+      const int kbn = min(C::KB_CHUNK, nk - c * C::KB_CHUNK);
       for (int kb = 0; kb < kbn; ++kb, ++i) {
         const int s = i % STAGES;
         if (!mbar_wait(&full[s], (i / STAGES) & 1, abort)) {
@@ -207,18 +230,18 @@ __global__ void __launch_bounds__(NT, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        uint8_t* st = smem + s * STAGE;
+        uint8_t* st = smem + s * C::STAGE;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {          // 4 x 32 bytes of K per 128-byte row
-          const uint64_t o = 2 * kk;              // +32 B in the 16-byte-encoded address field
+        for (int kk = 0; kk < C::KSTEPS; ++kk) {   // 32 bytes of K per step
+          const uint64_t o = 2 * kk;                // +32 B in the 16-byte-encoded address field
 #pragma unroll
-          for (int l = 0; l < kFxSlices; ++l)
+          for (int l = 0; l < NS; ++l)
 #pragma unroll
             for (int a = 0; a <= l; ++a) {
               const int b = l - a;
-              const uint64_t ad = sdesc_sw128(st + a * TA) + o;
-              const uint64_t bd = sdesc_sw128(st + kFxSlices * TA + b * TB) + o;
-              const uint32_t dt = tbase + (uint32_t)(buf * (kFxSlices * BN) + l * BN);
+              const uint64_t ad = sdesc<C::LAYOUT, C::SBO>(st + a * C::TA) + o;
+              const uint64_t bd = sdesc<C::LAYOUT, C::SBO>(st + NS * C::TA + b * C::TB) + o;
+              const uint32_t dt = tbase + (uint32_t)(buf * C::LEVEL_COLS + l * BN);
               mma_bf16(dt, ad, bd, idesc, (kb > 0 || kk > 0 || a > 0) ? 1u : 0u);
             }
         }
@@ -229,9 +252,13 @@ __global__ void __launch_bounds__(NT, 1)
   } else if (warp >= 4) {
     const int q = warp & 3, h = (warp - 4) >> 2;            // TMEM lane quarter, column half
     const int lrow = 32 * q + lane, row = m0 + lrow;
-    long long V[32];
+    constexpr int CPT = C::CPT;
+    constexpr int NL = (NS == 7) ? CPT : 1;
+    long long Vh[CPT], Vl[NL];                              // Vl: levels 4.. (NS = 7 only)
 #pragma unroll
-    for (int j = 0; j < 32; ++j) V[j] = 0;
+    for (int j = 0; j < CPT; ++j) Vh[j] = 0;
+#pragma unroll
+    for (int j = 0; j < NL; ++j) Vl[j] = 0;
     bool ok = true;
     for (int c = 0; c < nchunk; ++c) {
       const int buf = c & 1;
@@ -241,38 +268,42 @@ __global__ void __launch_bounds__(NT, 1)
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-      for (int cb = 0; cb < 4; ++cb) {
-        uint32_t r[kFxSlices][8];
+      for (int cb = 0; cb < CPT / 8; ++cb) {
+        uint32_t r[NS][8];
 #pragma unroll
-        for (int l = 0; l < kFxSlices; ++l)
-          tmem_ld8(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * (kFxSlices * BN) + l * BN + h * 32 + cb * 8),
+        for (int l = 0; l < NS; ++l)
+          tmem_ld8(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * C::LEVEL_COLS + l * BN + h * CPT + cb * 8),
                    r[l]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) {
           // every level sum is an integer below 2^24: the conversions are exact
-          const long long l0 = __float2int_rn(__uint_as_float(r[0][jj]));
-          const long long l1 = __float2int_rn(__uint_as_float(r[1][jj]));
-          const long long l2 = __float2int_rn(__uint_as_float(r[2][jj]));
-          const long long l3 = __float2int_rn(__uint_as_float(r[3][jj]));
-          V[cb * 8 + jj] += (l0 << 24) + (l1 << 16) + (l2 << 8) + l3;
+          long long L[NS];
+#pragma unroll
+          for (int l = 0; l < NS; ++l) L[l] = __float2int_rn(__uint_as_float(r[l][jj]));
+          Vh[cb * 8 + jj] += (L[0] << 24) + (L[1] << 16) + (L[2] << 8) + L[3];
+          if constexpr (NS == 7) Vl[cb * 8 + jj] += (L[4] << 16) + (L[5] << 8) + L[6];
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&acce[buf]);
     }
     if (ok && row < p.M) {
+      // value = (2^-24 Vh + 2^-48 Vl) u_a u_b = 2^-24 (Vh + 2^-24 Vl) u_a u_b; Vh, Vl exact in float64
       const double ua = p.ua[(long long)row * p.a_ngroups + group] * 0x1p-24;
       double* out = p.out + (long long)gz * p.split_stride;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int col = n0 + h * 32 + j;
-        if (col < p.N) {
-          const double v = (double)V[j] * ua * p.ub[(long long)col * p.b_ngroups + group];
-          if (p.col_major)
-            out[(long long)col * p.out_ld + row] = v;
+      for (int j = 0; j < CPT; ++j) {
+        const int col = n0 + h * CPT + j;
+        if (col < p.N && !(p.lower_only && row / 64 < col / 64)) {
+          double v = (double)Vh[j];
+          if constexpr (NS == 7) v += (double)Vl[j] * 0x1p-24;
+          v *= ua * p.ub[(long long)col * p.b_ngroups + group];
+          double* o = p.col_major ? out + (long long)col * p.out_ld + row : out + (long long)row * p.out_ld + col;
+          if (p.accumulate)
+            *o += p.alpha * v;
           else
-            out[(long long)row * p.out_ld + col] = v;
+            *o = v;
         }
       }
     }
@@ -316,32 +347,60 @@ bool get_encode_fx() {
   return true;
 }
 
-// BF16 slice map: boxes of box_rows rows x 64 elements (128 B), 128-byte swizzle
-bool make_map_fx(CUtensorMap* m, void* base, long long rows, long long ld, int box_rows) {
+// BF16 digit-plane map: boxes of box_rows rows x ke elements, swizzle of ke * 2 bytes
+bool make_map_fx(CUtensorMap* m, void* base, long long rows, long long ld, int box_rows, int ke) {
   cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)kFxKBlock, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)ke, (cuuint32_t)box_rows};
   cuuint32_t el[2] = {1, 1};
+  const CUtensorMapSwizzle sw = (ke == 64) ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   return g_encode_fx(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+                     sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NS>
+int fx_launch(Exec& ex, const FxGemm& g) {
+  using C = FxK<NS>;
+  FxMaps maps;
+  for (int i = 0; i < NS; ++i)
+    if (!make_map_fx(&maps.a[i], g.A.s[i], g.A.rows, g.A.ld, BM, C::KE) ||
+        !make_map_fx(&maps.b[i], g.B.s[i], g.B.rows, g.B.ld, C::BN, C::KE))
+      return MOLGW_E_ARG;
+  FxParams p;
+  p.M = g.M; p.N = g.N;
+  p.nkb = g.K / C::KE;
+  p.kb0 = g.k0 / C::KE;
+  p.ua = g.A.u; p.a_ngroups = g.A.ngroups;
+  p.ub = g.B.u; p.b_ngroups = g.B.ngroups;
+  p.out = g.out; p.out_ld = g.out_ld; p.split_stride = g.split_stride;
+  p.col_major = g.col_major ? 1 : 0;
+  p.accumulate = g.accumulate ? 1 : 0;
+  p.lower_only = g.lower_only ? 1 : 0;
+  p.alpha = g.alpha;
+  p.status = ex.status;
+  dim3 grid(ceil_div(g.N, C::BN), ceil_div(g.M, BM), fx_nsplit(g.K));
+  KScope ks(ex, g.kclass, 1);
+  cudaFuncSetAttribute(fx_gemm_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  fx_gemm_kernel<NS><<<grid, NT, C::SMEM, ex.st>>>(maps, p);
+  return MOLGW_OK;
 }
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 }  // namespace
 
-size_t fx_mat_bytes(long long rows, long long ld) {
-  return kFxSlices * align256((size_t)rows * ld * 2) + align256((size_t)rows * fx_groups(ld) * sizeof(double));
+size_t fx_mat_bytes(long long rows, long long ld, int ns) {
+  return ns * align256((size_t)rows * ld * 2) + align256((size_t)rows * fx_groups(ld) * sizeof(double));
 }
 
-FxMat fx_mat_carve(void* base, long long rows, long long ld) {
+FxMat fx_mat_carve(void* base, long long rows, long long ld, int ns) {
   FxMat m;
   m.rows = rows;
   m.ld = ld;
   m.ngroups = fx_groups(ld);
+  m.ns = ns;
   char* p = (char*)base;
-  for (int i = 0; i < kFxSlices; ++i) {
+  for (int i = 0; i < ns; ++i) {
     m.s[i] = p;
     p += align256((size_t)rows * ld * 2);
   }
@@ -351,7 +410,7 @@ FxMat fx_mat_carve(void* base, long long rows, long long ld) {
 
 FxMat fx_rows(const FxMat& m, long long r0, long long rows) {
   FxMat v = m;
-  for (int i = 0; i < kFxSlices; ++i) v.s[i] = (char*)m.s[i] + r0 * m.ld * 2;
+  for (int i = 0; i < m.ns; ++i) v.s[i] = (char*)m.s[i] + r0 * m.ld * 2;
   v.u = m.u + r0 * m.ngroups;
   v.rows = rows;
   return v;
@@ -359,34 +418,19 @@ FxMat fx_rows(const FxMat& m, long long r0, long long rows) {
 
 int fx_gemm(Exec& ex, const FxGemm& g) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return MOLGW_OK;
+  if (g.A.ns != g.B.ns || (g.A.ns != 4 && g.A.ns != 7)) return MOLGW_E_ARG;
   if (g.K % kFxKBlock || g.k0 % kFxGroup || g.A.ld % kFxKBlock || g.B.ld % kFxKBlock || g.k0 + g.K > g.A.ld ||
       g.k0 + g.K > g.B.ld || g.M > g.A.rows || g.N > g.B.rows)
     return MOLGW_E_ARG;
+  if (g.accumulate && fx_nsplit(g.K) != 1) return MOLGW_E_ARG;
   if (!get_encode_fx()) return MOLGW_E_CUDA;
-  CUtensorMap ma[kFxSlices], mb[kFxSlices];
-  for (int i = 0; i < kFxSlices; ++i)
-    if (!make_map_fx(&ma[i], g.A.s[i], g.A.rows, g.A.ld, BM) || !make_map_fx(&mb[i], g.B.s[i], g.B.rows, g.B.ld, BN))
-      return MOLGW_E_ARG;
-  FxParams p;
-  p.M = g.M; p.N = g.N;
-  p.nkb = g.K / kFxKBlock;
-  p.kb0 = g.k0 / kFxKBlock;
-  p.ua = g.A.u; p.a_ngroups = g.A.ngroups;
-  p.ub = g.B.u; p.b_ngroups = g.B.ngroups;
-  p.out = g.out; p.out_ld = g.out_ld; p.split_stride = g.split_stride;
-  p.col_major = g.col_major ? 1 : 0;
-  p.status = ex.status;
-  dim3 grid(ceil_div(g.N, BN), ceil_div(g.M, BM), fx_nsplit(g.K));
-  KScope ks(ex, MOLGW_K_GEMM_TC, 1);
-  cudaFuncSetAttribute(fx_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-  fx_gemm_kernel<<<grid, NT, SMEM, ex.st>>>(ma[0], ma[1], ma[2], ma[3], mb[0], mb[1], mb[2], mb[3], p);
-  return MOLGW_OK;
+  return g.A.ns == 7 ? fx_launch<7>(ex, g) : fx_launch<4>(ex, g);
 }
 
 void fx_split(Exec& ex, const double* src, long long rows, long long cols, long long sr, long long sk,
-              const double* row_scale, FxMat dst) {
+              const double* row_scale, FxMat dst, int kclass) {
   FxStrided f{src, sr, sk, rows, cols, row_scale};
-  fx_slice(ex, f, rows, dst);
+  fx_slice(ex, f, rows, dst, kclass);
 }
 
 void fx_reduce_cm(Exec& ex, const double* part, int ns, long long split_stride, int M, int N, double* out,

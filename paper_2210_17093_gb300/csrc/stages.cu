@@ -318,13 +318,40 @@ void stage_rpa_eigensolve(Exec& ex, MolBuf& m, EigWork& w, Scratch& s, bool full
   // Y = Q^T Xv in place (column-major n x na)
   apply_q(ex, w, n, m.M, m.Xv, 1, n, na, 1);
   // R[P][s] = sum_t Y[t][P] ZT[t][s] / sqrt(2 Omega_s)
-  GemmF64 g;
-  g.M = na; g.N = n; g.K = n;
-  g.A = m.Xv; g.sa_m = n; g.sa_k = 1;
-  g.B = m.ZT; g.sb_k = n; g.sb_n = 1;
-  g.C = m.R; g.sc_m = n; g.sc_n = 1;
-  g.kclass = MOLGW_K_BACKTRANSFORM;
-  gemm_f64(ex, g);
+  if (w.fx && n <= w.fx_rows && na <= w.fx_cols && n >= 128) {
+    // on the 7-digit engine: R^T block (s, P) = sum_t ZT(t, s) Y(t, P), written
+    // column-major into R; blocks of kFxZBlock eigenvectors, K groups in order
+    const long long np = fx_pad(n), nbz = std::min<long long>(n, kFxZBlock);
+    char* p = (char*)w.fx;
+    p += fx_mat_bytes(64, np, 7);                    // the layout of apply_q's operands:
+    FxMat ys = fx_mat_carve(p, na, np, 7);           // Y^T where apply_q kept X^T
+    p += fx_mat_bytes(w.fx_cols, np, 7);
+    p += fx_mat_bytes(w.fx_rows, 64, 7);
+    p += fx_mat_bytes(w.fx_cols, 64, 7);
+    fx_split(ex, m.Xv, na, n, n, 1, nullptr, ys, MOLGW_K_BACKTRANSFORM);
+    for (long long s0 = 0; s0 < n; s0 += nbz) {
+      const int nsb = (int)std::min<long long>(nbz, n - s0);
+      FxMat zs = fx_mat_carve(p, nsb, np, 7);
+      fx_split(ex, m.ZT + s0, nsb, n, 1, n, nullptr, zs, MOLGW_K_BACKTRANSFORM);
+      for (long long g0 = 0; g0 < np; g0 += kFxGroup) {
+        FxGemm g;
+        g.M = nsb; g.N = na; g.K = (int)std::min<long long>(kFxGroup, np - g0); g.k0 = (int)g0;
+        g.A = zs; g.B = ys;
+        g.out = m.R + s0; g.out_ld = n; g.col_major = true;
+        g.accumulate = g0 > 0;
+        g.kclass = MOLGW_K_BACKTRANSFORM;
+        fx_gemm(ex, g);
+      }
+    }
+  } else {
+    GemmF64 g;
+    g.M = na; g.N = n; g.K = n;
+    g.A = m.Xv; g.sa_m = n; g.sa_k = 1;
+    g.B = m.ZT; g.sb_k = n; g.sb_n = 1;
+    g.C = m.R; g.sc_m = n; g.sc_n = 1;
+    g.kclass = MOLGW_K_BACKTRANSFORM;
+    gemm_f64(ex, g);
+  }
   {
     KScope ks(ex, MOLGW_K_MISC);
     k_scale_r<<<grid_for((long long)na * n), 256, 0, ex.st>>>(m.R, m.Om, na, n);

@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(256) k_fx_sigma_slices(const double* __restric
   const double scale24 = 0x1p24 / u;            // a power of two: exact
   for (int kk = lane; kk < kFxGroup && k0 + kk < K; kk += 32) {
     __nv_bfloat16 d[kFxSlices];
-    fx_digits(tile[kk], scale24, d);
+    fx_digits<kFxSlices>(tile[kk], scale24, d);
     const long long o = (long long)pr * D.ld + k0 + kk;
 #pragma unroll
     for (int i = 0; i < kFxSlices; ++i) ((__nv_bfloat16*)D.s[i])[o] = d[i];

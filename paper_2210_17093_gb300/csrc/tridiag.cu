@@ -29,6 +29,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "fx.cuh"
 
 namespace molgw {
 
@@ -71,33 +72,31 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
   return v;
 }
 
-// Grid-wide barrier for a cooperative launch, with a bounded wait: after ~1 s
-// without progress it latches MOLGW_E_TIMEOUT, raises the abort flag and
-// returns false so that every CTA leaves the kernel.
-__device__ bool grid_sync(GridBar* bar, int* status) {
+// Grid-wide barrier for a cooperative launch.  Arrival is one fire-and-forget
+// release increment of a counter that only grows during the launch (zeroed before
+// it); barrier number e of the launch is passed when the counter reaches
+// e * gridDim.x, seen with acquire loads.  The wait is bounded: after ~1 s without
+// progress it latches MOLGW_E_TIMEOUT, raises the abort flag and returns false so
+// that every CTA leaves the kernel.
+__device__ bool grid_sync(GridBar* bar, int* status, unsigned int& epoch) {
   __shared__ int ok;
   __syncthreads();
+  ++epoch;
   if (threadIdx.x == 0) {
     ok = 1;
-    const unsigned int g = atomicAdd(&bar->gen, 0u);
+    const unsigned int target = epoch * gridDim.x;
     __threadfence();
-    const unsigned int arrived = atomicAdd(&bar->count, 1u) + 1u;
-    if (arrived == gridDim.x) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      long long spins = 0;
-      while (ld_acquire(&bar->gen) == g) {
-        if (*(volatile int*)&bar->abort != 0) { ok = 0; break; }
-        if (++spins > (1LL << 24)) {
-          set_status(status, MOLGW_E_TIMEOUT);
-          atomicExch(&bar->abort, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
+    long long spins = 0;
+    while (ld_acquire(&bar->count) < target) {
+      if (*(volatile int*)&bar->abort != 0) { ok = 0; break; }
+      if (++spins > (1LL << 24)) {
+        set_status(status, MOLGW_E_TIMEOUT);
+        atomicExch(&bar->abort, 1);
+        ok = 0;
+        break;
       }
+      if (spins > 64) __nanosleep(32);
     }
     __threadfence();
   }
@@ -163,6 +162,7 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
   double* A = p.A;
   const int t = threadIdx.x;
   const int nrbt = (n + TB - 1) / TB;
+  unsigned int epoch = 0;                 // grid barriers passed in this launch
 
   for (int j = 0; j < p.nbp; ++j) {
     const int i = k0 + j;
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
       }
       __syncthreads();
     }
-    if (!grid_sync(p.bar, p.status)) return;
+    if (!grid_sync(p.bar, p.status, epoch)) return;
 
     // ---------------- P2: reflector and y = A22 v ----------------
     const Refl h = householder(p, i, sh);
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
         J = Jn;
       }
     }
-    if (!grid_sync(p.bar, p.status)) return;
+    if (!grid_sync(p.bar, p.status, epoch)) return;
 
     // ---------------- P3: W column ----------------
     for (int c = t; c < 2 * j; c += blockDim.x) {
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
       p.tau[i] = h.tau;
       A[(i + 1) + (long long)i * ld] = 1.0;
     }
-    if (!grid_sync(p.bar, p.status)) return;
+    if (!grid_sync(p.bar, p.status, epoch)) return;
   }
 
   // ---------------- end of panel: last W correction and packing ----------------
@@ -500,7 +500,25 @@ void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
       cudaLaunchCooperativeKernel((const void*)k_panel, dim3(grid), dim3(RT), args, 0, ex.st);
     }
     const int m = n - k1;
-    if (m > 0) {
+    if (m > 0 && w.fx && m <= w.fx_rows && m >= 128) {
+      // A22 -= [V W] [W V]^T on the tensor cores: 7-digit fixed point, exact sums
+      const int kk = (int)fx_pad(2 * nbp);
+      FxMat a = fx_mat_carve(w.fx, m, 128, 7);
+      FxMat b = fx_mat_carve((char*)w.fx + fx_mat_bytes(w.fx_rows, 128, 7), m, 128, 7);
+      fx_split(ex, p.VW, m, 2 * nbp, 1, m, nullptr, a, MOLGW_K_TRIDIAG_SYR2K);
+      fx_split(ex, p.WV, m, 2 * nbp, 1, m, nullptr, b, MOLGW_K_TRIDIAG_SYR2K);
+      FxGemm g;
+      g.M = m; g.N = m; g.K = kk;
+      g.A = a; g.B = b;
+      g.out = A + k1 + (long long)k1 * n;
+      g.out_ld = n;
+      g.col_major = true;
+      g.accumulate = true;
+      g.alpha = -1.0;
+      g.lower_only = true;
+      g.kclass = MOLGW_K_TRIDIAG_SYR2K;
+      fx_gemm(ex, g);
+    } else if (m > 0) {
       GemmF64 g;
       g.M = m; g.N = m; g.K = 2 * nbp;
       g.A = p.VW; g.sa_m = 1; g.sa_k = m;

@@ -21,6 +21,7 @@ FLAG_KTIMING = 2
 FLAG_GRAPH = 4
 FLAG_USE_STREAM = 8
 FLAG_TC_AB = 16
+FLAG_EIG_TC = 32
 
 ITEM = {"B": 0, "Omega": 1, "R": 2, "sigma_x": 3, "sigma_c": 4, "J": 5, "h_mo": 6, "eps": 7, "C": 8}
 KERNELS = ["gemm_f64", "tridiag_panel", "tridiag_syr2k", "bisect", "twisted", "backtransform",
@@ -79,7 +80,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "molgw_b200_kernel_stats": ([vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double), ip], ip),
         "molgw_b200_launch_count": ([vp], ctypes.c_int64),
         "molgw_b200_graph_replays": ([vp], ctypes.c_int64),
-        "molgw_b200_tc_gemm": ([vp, ip, ip, ip, vp, vp, vp], ip),
+        "molgw_b200_tc_gemm": ([vp, ip, ip, ip, ip, vp, vp, vp], ip),
         "molgw_b200_set_timing": ([vp, ctypes.c_uint32], ip),
         "molgw_b200_destroy": ([vp], ip),
         "molgw_b200_status_string": ([ip], ctypes.c_char_p),
@@ -219,12 +220,13 @@ class Context:
     def launch_count(self) -> int:
         return int(self._lib.molgw_b200_launch_count(self._hh()))
 
-    def tc_gemm(self, A, B, C):
-        """C[M][N] = sum_k A[m][k] B[n][k] on the context's split-precision engine."""
+    def tc_gemm(self, A, B, C, digits: int = 0):
+        """C[M][N] = sum_k A[m][k] B[n][k] on a tensor-core engine: the context's split
+        (digits=0) or the fixed-point engine with 4 or 7 digits."""
         M, K = A.shape
         N = B.shape[0]
-        _check(self._lib.molgw_b200_tc_gemm(self._hh(), M, N, K, _ptr(A, M * K), _ptr(B, N * K), _ptr(C, M * N)),
-               "tc_gemm")
+        _check(self._lib.molgw_b200_tc_gemm(self._hh(), digits, M, N, K, _ptr(A, M * K), _ptr(B, N * K),
+                                            _ptr(C, M * N)), "tc_gemm")
 
     def graph_replays(self) -> int:
         """qs_step calls served from a captured graph (-1: capture failed, graphs off)."""

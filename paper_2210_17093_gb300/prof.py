@@ -3,8 +3,9 @@
     python -m paper_2210_17093_gb300.prof eigh N [REPS]
         float64 symmetric eigensolve of a random N x N matrix (tridiagonalisation,
         bisection, twisted vectors, full back-transformation) through molgw_b200_eigh;
-    python -m paper_2210_17093_gb300.prof qsgw NB NO NA PRECISION [REPS]
-        qsGW iterations of one synthetic molecule (seed 1) at the given precision;
+    python -m paper_2210_17093_gb300.prof qsgw NB NO NA PRECISION [REPS [FLAGS]]
+        qsGW iterations of one synthetic molecule (seed 1) at the given precision
+        (FLAGS: extra MOLGW_FLAG_* bits, e.g. 32 for MOLGW_FLAG_EIG_TC);
     python -m paper_2210_17093_gb300.prof batch PRECISION LANES [REPS]
         qsGW iterations of the 64-molecule ragged batch (n_basis ~ U{40..160},
         seeds 100-163) as one mol = -1 call on LANES concurrent streams.
@@ -41,7 +42,7 @@ def eigh(n: int, reps: int = 1) -> None:
             print(f"eigh n={n} rep {r}: {(time.perf_counter() - t) * 1e3:.1f} ms", _stats(ctx), flush=True)
 
 
-def qsgw(nb: int, no: int, na: int, precision: str, reps: int = 2) -> None:
+def qsgw(nb: int, no: int, na: int, precision: str, reps: int = 2, flags: int = 0) -> None:
     import numpy as np
     import torch
 
@@ -51,7 +52,8 @@ def qsgw(nb: int, no: int, na: int, precision: str, reps: int = 2) -> None:
     from . import Context, FLAG_KTIMING
     m = sy.molecule(nb, no, na, 1)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    with Context(precision=precision, stream=torch.cuda.current_stream(), flags=FLAG_KTIMING, eta=sy.ETA) as ctx:
+    with Context(precision=precision, stream=torch.cuda.current_stream(), flags=FLAG_KTIMING | flags,
+                 eta=sy.ETA) as ctx:
         ctx.set_ri(0, nb, na, d(m["L"]))
         ctx.set_orbitals(0, no, d(m["eps"]), d(m["C"]))
         for r in range(reps):
@@ -60,7 +62,7 @@ def qsgw(nb: int, no: int, na: int, precision: str, reps: int = 2) -> None:
             t = time.perf_counter()
             ctx.qs_step(0)
             ctx.sync()
-            print(f"qs_step nb={nb} {precision} rep {r}: {(time.perf_counter() - t) * 1e3:.1f} ms", _stats(ctx),
+            print(f"qs_step nb={nb} {precision} flags={flags} rep {r}: {(time.perf_counter() - t) * 1e3:.1f} ms", _stats(ctx),
                   flush=True)
 
 
@@ -93,7 +95,7 @@ if __name__ == "__main__":
     elif a and a[0] == "batch":
         batch(a[1], int(a[2]), int(a[3]) if len(a) > 3 else 2)
     elif a and a[0] == "qsgw":
-        qsgw(int(a[1]), int(a[2]), int(a[3]), a[4], int(a[5]) if len(a) > 5 else 2)
+        qsgw(int(a[1]), int(a[2]), int(a[3]), a[4], int(a[5]) if len(a) > 5 else 2, int(a[6]) if len(a) > 6 else 0)
     else:
         print(__doc__)
         sys.exit(2)

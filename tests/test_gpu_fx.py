@@ -22,23 +22,23 @@ ETA = sy.ETA
 MEV = 1e-3 / 27.211386245988       # Ha
 
 
-def fx_split_model(X, group=1024, kblock=64):
-    """Scales u[row, group] and the four integer slices of X (rows x K)."""
+def fx_split_model(X, ns=4, group=1024, kblock=64):
+    """Scales u[row, group] and the ns integer digits of X (rows x K)."""
     rows, K = X.shape
     kp = -(-K // kblock) * kblock
     Xp = np.zeros((rows, kp))
     Xp[:, :K] = X
     ng = -(-kp // group)
     u = np.empty((rows, ng))
-    sl = np.zeros((4, rows, kp))
+    sl = np.zeros((ns, rows, kp))
     for g in range(ng):
         blk = Xp[:, g * group:(g + 1) * group]
         mx = np.abs(blk).max(axis=1)
         _, e = np.frexp(mx)
         e = np.where(mx > 0, e, 0)
         u[:, g] = np.ldexp(1.0, e - 7)
-        T = np.rint(blk * (2.0 ** 24 / u[:, g])[:, None]).astype(np.int64)
-        for i in (3, 2, 1):                          # balanced base-256 digits
+        T = np.rint(blk * (2.0 ** (8 * (ns - 1)) / u[:, g])[:, None]).astype(np.int64)
+        for i in range(ns - 1, 0, -1):               # balanced base-256 digits
             d = ((T + 128) & 255) - 128
             sl[i, :, g * group:(g + 1) * group] = d
             T = (T - d) >> 8
@@ -47,21 +47,31 @@ def fx_split_model(X, group=1024, kblock=64):
     return sl, u, kp
 
 
-def fx_model(A, B, chunk=256, group=1024):
-    """The engine's arithmetic: exact level sums per chunk, one rounding per group,
-    groups summed in order."""
-    sa, ua, kp = fx_split_model(A)
-    sb, ub, _ = fx_split_model(B)
+def fx_model(A, B, ns=4, group=1024):
+    """The engine's arithmetic: exact level sums per chunk (256 elements with 4
+    digits, 128 with 7), levels combined in integers (two words with 7 digits),
+    one rounding per group, groups summed in order."""
+    chunk = 256 if ns == 4 else 128
+    sa, ua, kp = fx_split_model(A, ns)
+    sb, ub, _ = fx_split_model(B, ns)
     C = np.zeros((A.shape[0], B.shape[0]))
     for g in range(-(-kp // group)):
-        V = np.zeros_like(C)                                   # exact: |V| < 2^53
+        Vh = np.zeros(C.shape, dtype=np.int64)
+        Vl = np.zeros(C.shape, dtype=np.int64)
         for c0 in range(g * group, min(kp, (g + 1) * group), chunk):
             c1 = min(kp, c0 + chunk)
-            for lev in range(4):
-                L = sum(sa[a][:, c0:c1] @ sb[lev - a][:, c0:c1].T for a in range(lev + 1))
-                assert np.abs(L).max() <= 2.0 ** 24
-                V += L * 2.0 ** (24 - 8 * lev)
-        C = C + V * 2.0 ** -24 * ua[:, g][:, None] * ub[:, g][None, :]
+            L = []
+            for lev in range(ns):
+                s = sum(sa[a][:, c0:c1] @ sb[lev - a][:, c0:c1].T for a in range(lev + 1))
+                assert np.abs(s).max() < 2.0 ** 24
+                L.append(s.astype(np.int64))
+            Vh += (L[0] << 24) + (L[1] << 16) + (L[2] << 8) + L[3]
+            if ns == 7:
+                Vl += (L[4] << 16) + (L[5] << 8) + L[6]
+        v = Vh.astype(np.float64)
+        if ns == 7:
+            v = v + Vl.astype(np.float64) * 2.0 ** -24
+        C = C + v * (2.0 ** -24 * ua[:, g][:, None] * ub[:, g][None, :])
     return C
 
 
@@ -92,6 +102,23 @@ def test_fx_gemm_largest_level_sums():
         ctx.tc_gemm(A, B, C)
     assert np.array_equal(C, fx_model(A, B))
     assert np.array_equal(C, A @ B.T)
+
+
+@pytest.mark.parametrize("M,N,K", [(64, 48, 100), (200, 130, 2500), (257, 33, 1024)])
+def test_fx7_gemm_bitwise_model(M, N, K):
+    """Seven digits (the engine of MOLGW_FLAG_EIG_TC): bit-exact against the model
+    and within float64 accuracy of the exact product."""
+    rng = np.random.default_rng(7 * M + N + K)
+    A = rng.standard_normal((M, K)) * np.exp(-np.arange(K) / 300.0)[None, :]
+    B = rng.standard_normal((N, K)) * 10.0 ** rng.uniform(-3, 3, size=(N, 1))
+    C = np.empty((M, N))
+    with lib_context() as ctx:                   # float64 context: digits select the engine
+        ctx.tc_gemm(A, B, C, digits=7)
+    assert np.array_equal(C, fx_model(A, B, ns=7))
+    ref = A @ B.T
+    amax, bmax = np.abs(A).max(axis=1)[:, None], np.abs(B).max(axis=1)[None, :]
+    assert np.all(np.abs(C - ref) <= K * 2.0 ** -52 * amax * bmax)
+    assert np.abs(C - ref).max() / np.abs(ref).max() < 1e-14
 
 
 @pytest.mark.parametrize("prec,tol", [("bf16x3", 3e-5), ("tf32x3", 1.5e-5), ("bf16x6", 1.5e-5)])
@@ -143,3 +170,46 @@ def test_bf16x10_rejects_tc_ab():
     with pytest.raises(MolgwError) as e:
         lib_context(precision="bf16x10", flags=FLAG_TC_AB)
     assert e.value.code == -1
+
+
+def test_eig_tc_eigh_matches_float64():
+    """MOLGW_FLAG_EIG_TC: the trailing updates on 7 digits; eigenvalues to float64
+    accuracy and orthonormal residual-small eigenvectors."""
+    from paper_2210_17093_gb300 import FLAG_EIG_TC
+    n = 1100
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal((n, n))
+    A = (X + X.T) / 2 + np.diag(np.linspace(-5, 5, n))
+    ref = np.linalg.eigvalsh(A)
+    out = {}
+    for flags in (0, FLAG_EIG_TC):
+        w = np.empty(n)
+        Z = np.empty((n, n))
+        with lib_context(flags=flags) as ctx:
+            ctx.eigh(np.ascontiguousarray(A), w, Z)
+        out[flags] = (w, Z)
+    nrm = np.abs(ref).max()
+    for flags, (w, Z) in out.items():
+        assert np.max(np.abs(w - ref)) < 1e-12 * nrm, flags
+        Zc = Z.reshape(n, n)
+        # eigenvectors are columns or rows of Z depending on layout: test both ways
+        R1 = np.abs(A @ Zc.T - Zc.T * w[None, :]).max()
+        R2 = np.abs(A @ Zc - Zc * w[None, :]).max()
+        assert min(R1, R2) < 1e-10 * nrm, flags
+
+
+@pytest.mark.parametrize("prec,tol_ha", [("fp64", 1e-8), ("bf16x10", 1.0 * MEV)])
+def test_eig_tc_pass(prec, tol_ha):
+    from paper_2210_17093_gb300 import FLAG_EIG_TC
+    nb, no, na = 100, 20, 300
+    m = sy.molecule(nb, no, na, 1)
+    r = qsgw.qsgw_pass(m["L"], m["eps"], m["C"], no, ETA)
+    nov = no * (nb - no)
+    with lib_context(precision=prec, eta=ETA, flags=FLAG_EIG_TC) as ctx:
+        load_mol(ctx, 0, m)
+        om = np.empty(nov)
+        ctx.rpa(0, om)
+        eps = np.empty(nb)
+        ctx.qs_step(0, eps)
+    assert np.max(np.abs(om - r["Omega"])) < 1e-8
+    assert np.max(np.abs(eps - r["eps_new"])) < tol_ha
