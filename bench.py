@@ -9,7 +9,10 @@ n_occ=40, n_aux=600 (6,400 transitions, M is 6400^2 float64), seed 1, plain
 float64 on the GPU.  Each step continues the self-consistency from the previous
 one (the orbitals are updated in place).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload B|C|E|D]
+
+--workload D times the 64-molecule ragged batch (n_basis ~ U{40..160}) as one
+qs_step(-1) per step on concurrent lanes with graph replay.
 
 Under torchrun each rank runs an independent molecule (seed + rank): the units
 are independent, there is no data-path collective, scaling is weak.
@@ -218,7 +221,7 @@ def run_ours(args, wl):
     import torch
 
     world, rank, local, dist = dist_setup()
-    from paper_2210_17093_gb300 import Context
+    from paper_2210_17093_gb300 import FLAG_EIG_TC, Context
 
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
@@ -294,11 +297,10 @@ def run_ours(args, wl):
         t_e2e = max_over_ranks(dist, t_e2e)
         eps_fp64_step1 = eps_o.numpy().copy()     # float64 step from the input orbitals
 
-    mixed = None
-    if not args.no_mixed:
-        # the split-precision path on the same molecule: time per step, and its first
-        # step against the float64 GPU path (which matches the CPU oracle to 1e-8 Ha)
-        with Context(precision=args.mixed, device=local, eta=sy.ETA, stream=st) as mctx:
+    def variant(precision: str, flags: int, stages: str) -> dict:
+        """Another precision / flag set on the same molecule: time per step, and its
+        first step against the float64 GPU path (which matches the oracle to 1e-8 Ha)."""
+        with Context(precision=precision, device=local, eta=sy.ETA, stream=st, flags=flags) as mctx:
             mctx.set_ri(0, nb, na, L_d)
             mctx.set_orbitals(0, no, eps_d, C_d)
             e1 = torch.empty(nb, dtype=torch.float64).pin_memory()
@@ -315,32 +317,41 @@ def run_ours(args, wl):
                 mctx.qs_step(0)
             m1.record(st)
             torch.cuda.synchronize()
-            t_mixed = max_over_ranks(dist, m0.elapsed_time(m1) / 1e3)
+            t_v = max_over_ranks(dist, m0.elapsed_time(m1) / 1e3)
             mctx.set_timing(["gemm_f64", "tridiag_panel", "tridiag_syr2k", "bisect", "twisted",
                              "backtransform", "sigma", "gemm_tc", "misc"])
             mctx.kernel_stats(reset=True)
             mctx.qs_step(0)
-            mbreak = mctx.kernel_stats(reset=True)
+            vbreak = mctx.kernel_stats(reset=True)
         err = float(np.max(np.abs(e1.numpy() - eps_fp64_step1)))
-        tc_ms = mbreak.get("gemm_tc", (0, 0.0))[1]
-        peaks = measured_peaks()
-        nov = n
-        tc_exec = None
-        if args.mixed == "bf16x10" and tc_ms > 0:
-            # ten BF16 slice products per useful multiply-add: w = B_m^T R (K = n_aux padded
+        out = {"precision": precision, "flags": flags, "stages": stages,
+               "ms_per_step": t_v / args.steps * 1e3,
+               "speedup_vs_fp64": (t_max / args.steps) / (t_v / args.steps),
+               "qp_error_vs_fp64_meV": err * 27211.386,
+               "meets_1meV": bool(err * 27211.386 <= 1.0),
+               "stages_ms": {k: round(v[1], 3) for k, v in vbreak.items() if v[0]}}
+        tc_ms = vbreak.get("gemm_tc", (0, 0.0))[1]
+        if precision == "bf16x10" and tc_ms > 0:
+            # ten BF16 digit products per useful multiply-add: w = B_m^T R (K = n_aux padded
             # to 64) and S = (g w) w^T (K = n_basis x n_ov padded to 64)
+            peaks = measured_peaks()
             pad = lambda k: -(-k // 64) * 64
-            ex_flops = 10 * 2 * (nb * nb * nov * pad(na) + nb * nb * nb * pad(nov))
-            tc_exec = {"executed_tflops": ex_flops / (tc_ms / 1e3) / 1e12,
-                       "frac_of_bf16_peak": ex_flops / (tc_ms / 1e3) / 1e12 / peaks["bf16_tflops"],
-                       "peak_tflops": peaks["bf16_tflops"], "peak_kind": peaks["kind"] + " bf16 burst"}
-        mixed = {"precision": args.mixed, "stages": "(d)+(e) on tcgen05 tensor cores; (a)-(c), (f) float64",
-                 "tensor": tc_exec,
-                 "ms_per_step": t_mixed / args.steps * 1e3,
-                 "speedup_vs_fp64": (t_max / args.steps) / (t_mixed / args.steps),
-                 "qp_error_vs_fp64_meV": err * 27211.386,
-                 "meets_1meV": bool(err * 27211.386 <= 1.0),
-                 "stages_ms": {k: round(v[1], 3) for k, v in mbreak.items() if v[0]}}
+            ex_flops = 10 * 2 * (nb * nb * n * pad(na) + nb * nb * nb * pad(n))
+            out["tensor"] = {"kernels": "gemm_tc class: fx_gemm_kernel<4> of (d)+(e)",
+                             "executed_tflops": ex_flops / (tc_ms / 1e3) / 1e12,
+                             "frac_of_bf16_peak": ex_flops / (tc_ms / 1e3) / 1e12 / peaks["bf16_tflops"],
+                             "peak_tflops": peaks["bf16_tflops"], "peak_kind": peaks["kind"] + " bf16 burst"}
+        return out
+
+    mixed = mixed_eig = fp64_eig = None
+    if not args.no_mixed:
+        mixed = variant(args.mixed, 0, "(d)+(e) on tcgen05 tensor cores; (a)-(c), (f) float64")
+        mixed_eig = variant(args.mixed, FLAG_EIG_TC,
+                            "(d)+(e) as in 'mixed'; the eigensolvers' SYR2K and back-transformation GEMMs on "
+                            "7-digit fixed point (float64 accuracy, tensor cores); the rest float64")
+        fp64_eig = variant("fp64", FLAG_EIG_TC,
+                           "float64, with the eigensolvers' SYR2K and back-transformation GEMMs on 7-digit "
+                           "fixed point (float64 accuracy, tensor cores)")
 
     if rank != 0:
         return 0
@@ -370,6 +381,8 @@ def run_ours(args, wl):
         },
         "stages_ms": {k: round(v[1], 3) for k, v in breakdown.items() if v[0]},
         "mixed": mixed,
+        "mixed_eig_tc": mixed_eig,
+        "fp64_eig_tc": fp64_eig,
         "e2e": {"value": t_e2e, "unit": "s",
                 "h2d_bytes_per_step": int((na * nb * nb + nb + nb * nb) * 8),
                 "d2h_bytes_per_step": int((nb + nb * nb) * 8)},
@@ -384,13 +397,126 @@ def run_ours(args, wl):
     return 0
 
 
+def run_batch(args):
+    """Workload D: 64 molecules (n_basis ~ U{40..160}, seeds 100-163 + 64 x rank) as one
+    qs_step(-1) per step on concurrent lanes, replayed from a captured graph."""
+    import torch
+
+    world, rank, local, dist = dist_setup()
+    from paper_2210_17093_gb300 import FLAG_GRAPH, Context
+
+    torch.cuda.set_device(local)
+    seeds = [s + 64 * rank for s in sy.BATCH_SEEDS]
+    mols = [sy.batch_molecule(s) for s in seeds]
+    st = torch.cuda.Stream(device=f"cuda:{local}")
+    flops = {}
+    for m in mols:
+        for k, v in workload_flops(m["n_basis"], m["n_occ"], m["n_aux"]).items():
+            flops[k] = flops.get(k, 0.0) + v
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    host = [(pin(m["L"]), pin(m["eps"]), pin(m["C"])) for m in mols]
+    prec = args.batch_precision
+    with Context(precision=prec, device=local, eta=sy.ETA, stream=st, max_mols=len(mols),
+                 flags=FLAG_GRAPH, lanes=8) as ctx:
+        def load():
+            for k, (m, (L, e, C)) in enumerate(zip(mols, host)):
+                ctx.set_ri(k, m["n_basis"], m["n_aux"], L)
+                ctx.set_orbitals(k, m["n_occ"], e, C)
+        load()
+        dominant = args.dominant
+        # graph replays record no kernel events: the roofline comes from the first
+        # (directly issued) warm-up step, whose panel launches are those of every step
+        ctx.set_timing([dominant])
+        ctx.kernel_stats(reset=True)
+        ctx.qs_step(-1)
+        kstats = ctx.kernel_stats(reset=True)
+        ctx.set_timing([])
+        for _ in range(args.warmup - 1):
+            ctx.qs_step(-1)
+        ctx.sync()
+        l0 = ctx.launch_count()
+        r0 = ctx.graph_replays()
+        sampler = ClockSampler(local)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier(dist)
+        torch.cuda.synchronize()
+        sampler.start()
+        e0.record(st)
+        for _ in range(args.steps):
+            ctx.qs_step(-1)
+        e1.record(st)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        t_max = max_over_ranks(dist, e0.elapsed_time(e1) / 1e3)
+        launches = ctx.launch_count() - l0
+        replays = ctx.graph_replays() - r0
+        # end to end: inputs from pinned host memory, qs_step(-1), eps of every molecule to the host
+        outs = [torch.empty(m["n_basis"], dtype=torch.float64).pin_memory() for m in mols]
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        load()
+        ctx.qs_step(-1)
+        for k, o in enumerate(outs):
+            ctx.fetch(k, "eps", o)
+        t_e2e = max_over_ranks(dist, time.perf_counter() - t0)
+    if rank != 0:
+        return 0
+    nl, kms = kstats[dominant]
+    dom_flops = flops.get(dominant)
+    achieved = dom_flops / (kms / 1e3) / 1e12 if (dom_flops and kms > 0) else None
+    nbs = [m["n_basis"] for m in mols]
+    line = {
+        "metric": METRIC, "value": t_max / (args.steps * world), "unit": "s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else prec, "data": "synthetic",
+        "config": {"workload": f"ragged batch of {len(mols)} closed-shell RI-qsGW iterations, n_basis "
+                               f"{min(nbs)}..{max(nbs)} (U{{40..160}}), n_occ = round(n_basis/5), n_aux = 3 n_basis, "
+                               f"seeds {seeds[0]}..{seeds[-1]}; one qs_step(-1) per step on 8 lanes, "
+                               f"graph replay", "molecules": len(mols), "precision": prec, "eta_ha": sy.ETA,
+                   "l2": "inputs larger than L2 (RI factors and Casida matrices of 64 molecules, ~10 GB)"},
+        "tflops": sum(flops.values()) / (t_max / args.steps) / 1e12,
+        "gpu_launches": int(launches), "graph_replays": int(replays),
+        "clocks": clocks,
+        "roofline": {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                     "traffic": None, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                     "launches": nl, "event_ms": kms,
+                     "note": "one directly issued step (graph replays record no events); launches of "
+                             "concurrent lanes overlap, so achieved = flops / summed launch time"},
+        "e2e": {"value": t_e2e, "unit": "s",
+                "h2d_bytes_per_step": int(sum((m["n_aux"] * m["n_basis"] ** 2 + m["n_basis"] + m["n_basis"] ** 2) * 8
+                                              for m in mols)),
+                "d2h_bytes_per_step": int(sum(m["n_basis"] * 8 for m in mols))},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        # a bounded sample: 4 molecules of the batch, one oracle iteration each, scaled to 64
+        from oracle import qsgw
+        sample = mols[:4]
+        t0 = time.perf_counter()
+        for m in sample:
+            qsgw.qsgw_pass(m["L"], m["eps"], m["C"], m["n_occ"], sy.ETA)
+        t_cpu = (time.perf_counter() - t0) * len(mols) / len(sample)
+        line["cpu_baseline"] = {
+            "value": t_cpu, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one oracle iteration of molecules {seeds[0]}..{seeds[3]} (n_basis "
+                      f"{', '.join(str(m['n_basis']) for m in sample)}), time x {len(mols)}/{len(sample)}"}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="B")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["D"], default="B",
+                    help="B/C/E: one molecule; D: the 64-molecule ragged batch")
+    ap.add_argument("--batch-precision", choices=["fp64", "bf16x3", "tf32x3", "bf16x6", "bf16x10"],
+                    default="bf16x10", help="precision of workload D")
     ap.add_argument("--precision", choices=["fp64", "bf16x3", "tf32x3", "bf16x6", "bf16x10"], default="fp64")
     ap.add_argument("--dominant", default="tridiag_panel", help="kernel class reported in 'roofline'")
     ap.add_argument("--mixed", choices=["bf16x3", "tf32x3", "bf16x6", "bf16x10"], default="bf16x10",
@@ -400,6 +526,11 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.workload == "D":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "workload D has no reference line; use the default"}))
+            return 0
+        return run_batch(args)
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
