@@ -62,7 +62,7 @@ def measured_peaks() -> dict:
 # DRAM bytes the tridiagonalisation panel kernel moves per algorithmic byte (the lower
 # triangle of the trailing matrix once per column), from one ncu capture of the panel of
 # columns 192..255 at n = 6400: 10.13 GB measured for 9.77 GB algorithmic.
-PANEL_TRAFFIC_RATIO = 10.13 / 9.77
+PANEL_TRAFFIC_RATIO = 4.581 / 6.629   # ncu, one panel launch (n=6400, columns 1280-1343)
 
 
 def panel_bytes(n):
@@ -375,8 +375,9 @@ def run_ours(args, wl):
             "kernel": dominant, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
             "traffic": traffic, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-            "traffic_source": "ncu dram__bytes_read+write of one panel launch (n=6400, columns 192-255), "
-                              "scaled by the algorithmic bytes per launch",
+            "traffic_source": "ncu dram__bytes_read+write of one panel launch (n=6400, columns 1280-1343: "
+                              "4.58 GB for 6.63 GB algorithmic, part of the trailing matrix served by L2), "
+                              "that ratio times the algorithmic bytes per launch",
             "launches": nl, "event_ms": kms,
         },
         "stages_ms": {k: round(v[1], 3) for k, v in breakdown.items() if v[0]},
