@@ -1,8 +1,12 @@
 // Float64 tridiagonal eigensolver and back-transformation.
 //
-//  * Eigenvalues: bisection on Sturm counts (one thread per eigenvalue index),
-//    the count taken from the LDL^T pivots q_j = d_j - x - e_{j-1}^2 / q_{j-1}
-//    with tiny pivots replaced by -pivmin (Kahan/Demmel; LAPACK dstebz style).
+//  * Eigenvalues: 4 threads per eigenvalue index.  A float32 bisection on the
+//    LDL^T pivots q_j = d_j - x - e_{j-1}^2 / q_{j-1} (tiny pivots replaced by
+//    -pivmin) brackets it to a few float32 ulps; the float64 phase counts sign
+//    changes of the leading principal minors (three-term recurrence with power-
+//    of-two rescaling, no division; Barth, Martin and Wilkinson) and takes
+//    safeguarded Newton steps on det(T - x I) with the derivative of the same
+//    recurrence, each step checked against the Sturm counts of the bracket.
 //  * Eigenvectors: for each eigenvalue a twisted factorisation of T - lambda I
 //    (Fernando; Parlett and Dhillon): the stationary factor L+ D+ from the top,
 //    the progressive factor U- D- from the bottom, the twist index r minimising
@@ -54,31 +58,46 @@ __global__ void k_gersh(const double* d, const double* e, int n, double* out) {
   }
 }
 
-// 1/q by Newton-Raphson (r <- r (2 - q r), quadratic convergence) from the
-// float32 reciprocal as seed: two steps take the ~24-bit seed past float64
-// precision.  Outside the float32 range the plain division is used.
-__device__ __forceinline__ double recip_nr(double q) {
-  const double aq = fabs(q);
-  if (aq > 1e-30 && aq < 1e30) {
-    double r = (double)__frcp_rn((float)q);
-    r = r * fma(-q, r, 2.0);
-    r = r * fma(-q, r, 2.0);
-    return r;
-  }
-  return 1.0 / q;
-}
-
-// Number of eigenvalues of T below x (float64 LDL^T pivots).
-__device__ __forceinline__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e2,
-                                           int n, double x, double pivmin) {
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  int cnt = (q < 0.0);
+// Number of eigenvalues of T below x from the three-term recurrence of the leading
+// principal minors, p_j = (d_j - x) p_{j-1} - e_{j-1}^2 p_{j-2} (p_{-1} = 1): the
+// count of sign changes along p_{-1}, p_0, ..., p_{n-1} (Sturm sequence property),
+// with no division.  A zero minor takes the sign opposite to its predecessor (the
+// limit of a tiny negative pivot).  The derivatives p_j' follow from the same
+// recurrence, and S = p_{n-1}' / p_{n-1} = det'(T - x I) / det(T - x I) gives a
+// Newton step x - 1/S.  Every 4 steps the state is rescaled by a power of two, which
+// changes neither the signs nor the ratio.  Sign tests and rescaling run on the
+// integer pipe; the float64 work is 5 operations per step.
+__device__ __forceinline__ int sturm_count_minors(const double* __restrict__ d, const double* __restrict__ e2,
+                                                  int n, double x, double* S) {
+  double p0 = 1.0, p0d = 0.0;               // p_{j-2}, p_{j-2}'
+  double p1 = d[0] - x, p1d = -1.0;         // p_{j-1}, p_{j-1}'
+  if (p1 == 0.0) p1 = -1e-300;
+  int cnt = (p1 < 0.0);
   for (int j = 1; j < n; ++j) {
-    q = (d[j] - x) - e2[j - 1] * recip_nr(q);
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += (q < 0.0);
+    const double dx = d[j] - x;
+    const double ee = e2[j - 1];
+    double p2 = fma(dx, p1, -ee * p0);
+    const double p2d = fma(-ee, p0d, fma(dx, p1d, -p1));
+    const long long b1 = __double_as_longlong(p1);
+    long long b2 = __double_as_longlong(p2);
+    if ((b2 & 0x7fffffffffffffffLL) == 0) {   // zero minor: opposite sign to p_{j-1}
+      p2 = (b1 < 0) ? 1e-300 : -1e-300;
+      b2 = __double_as_longlong(p2);
+    }
+    cnt += (int)((unsigned long long)(b1 ^ b2) >> 63);
+    p0 = p1; p0d = p1d;
+    p1 = p2; p1d = p2d;
+    if ((j & 3) == 0) {
+      // keep max(|p_{j-2}|, |p_{j-1}|) near 1: multiply the state by 2^-(its exponent)
+      const int e1 = (int)((b1 >> 52) & 0x7ff), e2x = (int)((b2 >> 52) & 0x7ff);
+      const int ex = (e1 > e2x ? e1 : e2x) - 1023;
+      if (ex > 256 || ex < -256) {
+        const double f = __longlong_as_double((long long)(1023 - ex) << 52);
+        p0 *= f; p0d *= f; p1 *= f; p1d *= f;
+      }
+    }
   }
+  *S = p1d / p1;
   return cnt;
 }
 
@@ -128,7 +147,7 @@ __device__ __forceinline__ void multisect(T& lo, T& hi, int cnt_l, T x_l, int k,
 // is widened by a safety margin and accepted only if float64 Sturm counts
 // confirm that it still encloses eigenvalue k (else the Gershgorin interval is
 // used).  The float64 phase then multisects to 2 eps |lambda| + 4 eps ||T||.
-__global__ void __launch_bounds__(128) k_bisect(const double* d, const double* e2, const float* d32,
+__global__ void __launch_bounds__(32) k_bisect(const double* d, const double* e2, const float* d32,
                                                 const float* e232, const double* g, int n, double* lam,
                                                 int* status) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
@@ -154,19 +173,46 @@ __global__ void __launch_bounds__(128) k_bisect(const double* d, const double* e
   const double margin = 64.0 * 5.9604645e-8 * nrm + atol;
   double lo = fmax(glo, (double)lo32 - margin), hi = fmin(ghi, (double)hi32 + margin);
   int cl = 0;
-  if (lo < hi && l < 2) cl = sturm_count(d, e2, n, l == 0 ? lo : hi, pivmin);
+  double S = 0.0;
+  if (lo < hi && l < 2) cl = sturm_count_minors(d, e2, n, l == 0 ? lo : hi, &S);
   const int c_lo = __shfl_sync(mask, cl, 0, 4), c_hi = __shfl_sync(mask, cl, 1, 4);
   if (!(lo < hi) || c_lo > k || c_hi <= k) {
     lo = glo;
     hi = ghi;
   }
+  // float64 phase: safeguarded Newton on det(T - x I).  While the Newton iterate xn
+  // lies inside the bracket, the 4 lanes evaluate xn, xn -/+ e (e = half the last
+  // Newton step: the root is there once the iteration converges quadratically) and
+  // the bracket midpoint (halving it whatever Newton does); otherwise they
+  // multisect.  Every count updates the bracket, which always holds eigenvalue k;
+  // the result is the bracket's midpoint once it is 2 eps |lambda| + atol wide.
   bool ok = false;
+  double xn = 0.5 * (lo + hi), dn = hi - lo;
   for (int it = 0; it < 128; ++it) {
-    if (hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + atol) { ok = true; break; }
-    const double x = lo + (double)(l + 1) * (hi - lo) * 0.2;
-    const int c = (x > lo && x < hi) ? sturm_count(d, e2, n, x, pivmin) : ((x <= lo) ? 0 : n);
+    const double tol = 2.0 * eps * fmax(fabs(lo), fabs(hi)) + atol;
+    if (hi - lo <= tol) { ok = true; break; }
+    const bool newton = xn > lo && xn < hi;
+    double x;
+    if (newton) {
+      const double e = fmax(0.5 * fabs(dn), 0.25 * tol);
+      x = (l == 0) ? xn : (l == 1) ? xn - e : (l == 2) ? xn + e : 0.5 * (lo + hi);
+    } else {
+      x = lo + (double)(l + 1) * (hi - lo) * 0.2;
+    }
+    S = 0.0;
+    int c;
+    if (x > lo && x < hi)
+      c = sturm_count_minors(d, e2, n, x, &S);   // one code path for the whole warp
+    else
+      c = (x <= lo) ? 0 : n;
     const double plo = lo, phi = hi;
     multisect<double>(lo, hi, c, x, k, l, mask);
+    // lane 0's Newton step from its point (ignored when not finite)
+    const double S0 = __shfl_sync(mask, S, 0, 4), x0 = __shfl_sync(mask, x, 0, 4);
+    const double step = (S0 != 0.0 && isfinite(S0)) ? -1.0 / S0 : 0.0;
+    xn = x0 + step;
+    dn = step;
+    if (!(step != 0.0 && isfinite(xn))) { xn = 0.5 * (lo + hi); dn = hi - lo; }
     if (lo == plo && hi == phi) { ok = true; break; }   // no representable progress
   }
   if (!ok && l == 0) set_status(status, MOLGW_E_NOCONV);
@@ -175,7 +221,7 @@ __global__ void __launch_bounds__(128) k_bisect(const double* d, const double* e
 
 // Twisted factorisation eigenvector of T - lambda_s I; S1/S2 are strided scratch
 // columns (element j at [j*ld + s]); the normalised vector is left in S1.
-__global__ void __launch_bounds__(128) k_twisted(const double* __restrict__ d, const double* __restrict__ e,
+__global__ void __launch_bounds__(32) k_twisted(const double* __restrict__ d, const double* __restrict__ e,
                                                  const double* __restrict__ lam, const double* g, int n,
                                                  double* S1, double* S2, long long ld) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -304,12 +350,12 @@ void tridiag_eigvals(Exec& ex, EigWork& w, int n) {
   KScope ks(ex, MOLGW_K_BISECT, 3);
   k_gersh<<<1, 256, 0, ex.st>>>(w.d, w.e, n, g);
   k_e2<<<ceil_div(n, 256), 256, 0, ex.st>>>(w.d, w.e, e2, d32, e232, n);
-  k_bisect<<<ceil_div(4LL * n, 128), 128, 0, ex.st>>>(w.d, e2, d32, e232, g, n, w.lam, ex.status);
+  k_bisect<<<ceil_div(4LL * n, 32), 32, 0, ex.st>>>(w.d, e2, d32, e232, g, n, w.lam, ex.status);
 }
 
 void tridiag_eigvecs(Exec& ex, EigWork& w, int n, double* ZT, long long ldz) {
   KScope ks(ex, MOLGW_K_TWISTED, 1);
-  k_twisted<<<ceil_div(n, 128), 128, 0, ex.st>>>(w.d, w.e, w.lam, w.scal + 8, n, ZT, w.S2, ldz);
+  k_twisted<<<ceil_div(n, 32), 32, 0, ex.st>>>(w.d, w.e, w.lam, w.scal + 8, n, ZT, w.S2, ldz);
 }
 
 void build_wy(Exec& ex, EigWork& w, int n, const double* A) {
