@@ -221,7 +221,7 @@ def run_ours(args, wl):
     import torch
 
     world, rank, local, dist = dist_setup()
-    from paper_2210_17093_gb300 import FLAG_EIG_TC, Context
+    from paper_2210_17093_gb300 import FLAG_EIG_TC, FLAG_TC_AB, Context
 
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
@@ -337,7 +337,12 @@ def run_ours(args, wl):
             peaks = measured_peaks()
             pad = lambda k: -(-k // 64) * 64
             ex_flops = 10 * 2 * (nb * nb * n * pad(na) + nb * nb * nb * pad(n))
-            out["tensor"] = {"kernels": "gemm_tc class: fx_gemm_kernel<4> of (d)+(e)",
+            if flags & FLAG_TC_AB:
+                # (a): two GEMMs M = n_aux n_basis, N = n_basis, K = n_basis padded; (b): lower
+                # 64-blocks of Xv Xv^T (about half of n_ov^2 n_aux padded)
+                ex_flops += 10 * 2 * (2 * na * nb * nb * pad(nb) + 0.5 * n * n * pad(na))
+            out["tensor"] = {"kernels": "gemm_tc class: fx_gemm_kernel<4> of (d)+(e)"
+                                        + (" and (a), (b)" if flags & FLAG_TC_AB else ""),
                              "executed_tflops": ex_flops / (tc_ms / 1e3) / 1e12,
                              "frac_of_bf16_peak": ex_flops / (tc_ms / 1e3) / 1e12 / peaks["bf16_tflops"],
                              "peak_tflops": peaks["bf16_tflops"], "peak_kind": peaks["kind"] + " bf16 burst"}
@@ -345,10 +350,13 @@ def run_ours(args, wl):
 
     mixed = mixed_eig = fp64_eig = None
     if not args.no_mixed:
-        mixed = variant(args.mixed, 0, "(d)+(e) on tcgen05 tensor cores; (a)-(c), (f) float64")
-        mixed_eig = variant(args.mixed, FLAG_EIG_TC,
-                            "(d)+(e) as in 'mixed'; the eigensolvers' SYR2K and back-transformation GEMMs on "
-                            "7-digit fixed point (float64 accuracy, tensor cores); the rest float64")
+        ab = FLAG_TC_AB if args.mixed == "bf16x10" else 0
+        mixed = variant(args.mixed, ab, "(a), (b), (d) and the Sigma contraction of (e) on tcgen05 tensor cores; "
+                                        "eigensolvers (c), (f) and the denominators float64")
+        mixed_eig = variant(args.mixed, ab | FLAG_EIG_TC,
+                            "as 'mixed', and the eigensolvers' SYR2K and back-transformation GEMMs on 7-digit "
+                            "fixed point (float64 accuracy, tensor cores); the panel mat-vecs, bisection and "
+                            "twisted vectors float64")
         fp64_eig = variant("fp64", FLAG_EIG_TC,
                            "float64, with the eigensolvers' SYR2K and back-transformation GEMMs on 7-digit "
                            "fixed point (float64 accuracy, tensor cores)")
@@ -404,7 +412,7 @@ def run_batch(args):
     import torch
 
     world, rank, local, dist = dist_setup()
-    from paper_2210_17093_gb300 import FLAG_GRAPH, Context
+    from paper_2210_17093_gb300 import FLAG_GRAPH, FLAG_TC_AB, Context
 
     torch.cuda.set_device(local)
     seeds = [s + 64 * rank for s in sy.BATCH_SEEDS]
@@ -417,8 +425,9 @@ def run_batch(args):
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     host = [(pin(m["L"]), pin(m["eps"]), pin(m["C"])) for m in mols]
     prec = args.batch_precision
+    flags = FLAG_GRAPH | (FLAG_TC_AB if prec != "fp64" else 0)
     with Context(precision=prec, device=local, eta=sy.ETA, stream=st, max_mols=len(mols),
-                 flags=FLAG_GRAPH, lanes=8) as ctx:
+                 flags=flags, lanes=8) as ctx:
         def load():
             for k, (m, (L, e, C)) in enumerate(zip(mols, host)):
                 ctx.set_ri(k, m["n_basis"], m["n_aux"], L)
@@ -476,7 +485,8 @@ def run_batch(args):
         "config": {"workload": f"ragged batch of {len(mols)} closed-shell RI-qsGW iterations, n_basis "
                                f"{min(nbs)}..{max(nbs)} (U{{40..160}}), n_occ = round(n_basis/5), n_aux = 3 n_basis, "
                                f"seeds {seeds[0]}..{seeds[-1]}; one qs_step(-1) per step on 8 lanes, "
-                               f"graph replay", "molecules": len(mols), "precision": prec, "eta_ha": sy.ETA,
+                               f"graph replay", "molecules": len(mols), "precision": prec,
+                   "stages_on_tensor_cores": "(a), (b), (d), (e)" if prec != "fp64" else "none", "eta_ha": sy.ETA,
                    "l2": "inputs larger than L2 (RI factors and Casida matrices of 64 molecules, ~10 GB)"},
         "tflops": sum(flops.values()) / (t_max / args.steps) / 1e12,
         "gpu_launches": int(launches), "graph_replays": int(replays),

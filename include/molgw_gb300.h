@@ -70,7 +70,8 @@ enum molgw_precision {
   MOLGW_PREC_BF16X6 = 3,  /* tcgen05 BF16 products, 3 slices hi+mid+lo, 6 products, FP32 */
   MOLGW_PREC_BF16X10 = 4  /* tcgen05 BF16 products of 4 fixed-point slices (10 products),
                              exact FP32 sums per 256-element chunk, one FP64 rounding per
-                             1024-element group; (d) and (e) only (no MOLGW_FLAG_TC_AB)  */
+                             1024-element group; (d) and (e), and (a), (b) with
+                             MOLGW_FLAG_TC_AB                                         */
 };
 /* With BF16X3, TF32X3 or BF16X6 the residue and self-energy contractions (d),
  * (e) run on the tensor cores (the residues in float32 chunks of 64 auxiliary
@@ -86,7 +87,7 @@ enum molgw_flags {
                                     graph (all lanes of mol = -1 in one graph) and replayed while the
                                     buffers and the set of molecules stay the same                  */
   MOLGW_FLAG_USE_STREAM = 1u << 3, /* run on opts.stream even when it is NULL (the legacy default stream) */
-  MOLGW_FLAG_TC_AB = 1u << 4,      /* with BF16X3/TF32X3: stages (a) and (b) on the tensor cores too */
+  MOLGW_FLAG_TC_AB = 1u << 4,      /* with a split precision: stages (a) and (b) on the tensor cores too */
   MOLGW_FLAG_EIG_TC = 1u << 5      /* the trailing SYR2K update of the tridiagonalisation on the
                                       tensor cores: 7 fixed-point BF16 digits per value (56 bits,
                                       values within 4x of their group maximum exact), exact sums,

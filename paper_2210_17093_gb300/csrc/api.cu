@@ -120,7 +120,7 @@ int read_status(molgw_ctx c) {
 
 bool use_tc(molgw_ctx c) { return c->opts.precision != MOLGW_PREC_FP64; }
 bool use_fx(molgw_ctx c) { return c->opts.precision == MOLGW_PREC_BF16X10; }
-bool use_tc_ab(molgw_ctx c) { return use_tc(c) && !use_fx(c) && (c->opts.flags & MOLGW_FLAG_TC_AB); }
+bool use_tc_ab(molgw_ctx c) { return use_tc(c) && (c->opts.flags & MOLGW_FLAG_TC_AB); }
 int tc_prec(molgw_ctx c) {
   if (c->opts.precision == MOLGW_PREC_TF32X3) return TC_TF32X3;
   if (c->opts.precision == MOLGW_PREC_BF16X6) return TC_BF16X6;
@@ -277,7 +277,8 @@ int ensure_scratch(molgw_ctx c, Lane& l, int nb, int na, long long nov) {
 int ensure_tco(molgw_ctx c, Lane& l, int nb, int na, long long nov) {
   if (!use_tc(c)) return MOLGW_OK;
   const int prec = tc_prec(c);
-  const size_t want = use_fx(c) ? (fx_sigma_bytes(nb, na, nov, fx_mblock(nb, na, nov)) + 7) / 8
+  const size_t want = use_fx(c) ? (std::max(fx_sigma_bytes(nb, na, nov, fx_mblock(nb, na, nov)),
+                                            use_tc_ab(c) ? fx_ab_bytes(nb, na, nov) : (size_t)0) + 7) / 8
                                 : tc_orb_doubles(prec, nb, na, nov, tc_mblock(prec, nb, nov));
   if (want <= l.tco_cap) return MOLGW_OK;
   if (l.ex.capturing) return MOLGW_E_STATE;
@@ -326,7 +327,10 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
     tb.L = c->tcb[mol].L;
   }
   if (!m.b_valid) {
-    if (tc_ab) {
+    if (tc_ab && use_fx(c)) {
+      r = stage_ri_mo_transform_fx(ex, m, c->tcb[mol].Lfx, l.tco_base);
+      if (r) return r;
+    } else if (tc_ab) {
       r = stage_ri_mo_transform_tc(ex, m, tb);
       if (r) return r;
     } else {
@@ -341,7 +345,10 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
     m.h_ready = true;
   }
   if (upto == 'b') {
-    if (tc_ab) {
+    if (tc_ab && use_fx(c)) {
+      r = stage_rpa_build_fx(ex, m, l.tco_base);
+      if (r) return r;
+    } else if (tc_ab) {
       r = stage_rpa_build_tc(ex, m, tb);
       if (r) return r;
     } else {
@@ -351,7 +358,10 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
     return launch_status();
   }
   if (!m.rpa_valid) {
-    if (tc_ab) {
+    if (tc_ab && use_fx(c)) {
+      r = stage_rpa_build_fx(ex, m, l.tco_base);
+      if (r) return r;
+    } else if (tc_ab) {
       r = stage_rpa_build_tc(ex, m, tb);
       if (r) return r;
     } else {
@@ -576,7 +586,6 @@ int molgw_b200_create(const molgw_opts* o, molgw_ctx* out) {
   *out = nullptr;
   if (!o || o->struct_size != (int32_t)sizeof(molgw_opts)) return MOLGW_E_ARG;
   if (o->precision < MOLGW_PREC_FP64 || o->precision > MOLGW_PREC_BF16X10) return MOLGW_E_ARG;
-  if (o->precision == MOLGW_PREC_BF16X10 && (o->flags & MOLGW_FLAG_TC_AB)) return MOLGW_E_ARG;
   if (o->max_mols < 1 || !(o->eta > 0.0) || o->lanes < 0) return MOLGW_E_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) { cudaGetLastError(); return MOLGW_E_CUDA; }
@@ -639,7 +648,11 @@ int molgw_b200_set_ri(molgw_ctx c, int mol, int n_basis, int n_aux, const double
     m.T1 = dalloc(m.ri_allocs, nl, &err);
     TcBufs& tb = c->tcb[mol];
     free_all(tb.ri_allocs);
-    if (use_tc_ab(c)) {
+    if (use_tc_ab(c) && use_fx(c)) {
+      const long long rows = (long long)n_aux * n_basis, ld = fx_pad(n_basis);
+      double* base = dalloc(tb.ri_allocs, (fx_mat_bytes(rows, ld) + 7) / 8, &err);
+      if (!err) tb.Lfx = fx_mat_carve(base, rows, ld);
+    } else if (use_tc_ab(c)) {
       double* base = dalloc(tb.ri_allocs, tc_ri_doubles(tc_prec(c), n_basis, n_aux), &err);
       if (!err) tc_ri_carve(tb, tc_prec(c), n_basis, n_aux, base);
     }
@@ -649,7 +662,10 @@ int molgw_b200_set_ri(molgw_ctx c, int mol, int n_basis, int n_aux, const double
   if (r) return r;
   Exec& ex = c->lanes[0].ex;
   check_finite(ex, m.L, (long long)nl);
-  if (use_tc_ab(c)) tc_split_ri(ex, m, c->tcb[mol]);
+  if (use_tc_ab(c) && use_fx(c))
+    fx_split(ex, m.L, (long long)n_aux * n_basis, n_basis, n_basis, 1, nullptr, c->tcb[mol].Lfx);
+  else if (use_tc_ab(c))
+    tc_split_ri(ex, m, c->tcb[mol]);
   m.have_ri = true;
   return launch_status();
 }

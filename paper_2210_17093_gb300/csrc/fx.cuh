@@ -64,6 +64,7 @@ struct FxGemm {
   bool accumulate = false;
   double alpha = 1.0;
   bool lower_only = false;
+  const double* diag = nullptr;   // adds diag[row]^2 where row == col (not with accumulate)
   int kclass = MOLGW_K_GEMM_TC;   // kernel class for launch accounting
 };
 int fx_gemm(Exec& ex, const FxGemm& g);

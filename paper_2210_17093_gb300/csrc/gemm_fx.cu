@@ -133,6 +133,7 @@ struct FxParams {
   long long out_ld, split_stride;
   int col_major, accumulate, lower_only;
   double alpha;
+  const double* diag;
   int* status;
 };
 
@@ -299,6 +300,7 @@ __global__ void __launch_bounds__(NT, 1) fx_gemm_kernel(const __grid_constant__ 
           double v = (double)Vh[j];
           if constexpr (NS == 7) v += (double)Vl[j] * 0x1p-24;
           v *= ua * p.ub[(long long)col * p.b_ngroups + group];
+          if (p.diag && row == col) v += p.diag[row] * p.diag[row];
           double* o = p.col_major ? out + (long long)col * p.out_ld + row : out + (long long)row * p.out_ld + col;
           if (p.accumulate)
             *o += p.alpha * v;
@@ -377,6 +379,7 @@ int fx_launch(Exec& ex, const FxGemm& g) {
   p.accumulate = g.accumulate ? 1 : 0;
   p.lower_only = g.lower_only ? 1 : 0;
   p.alpha = g.alpha;
+  p.diag = g.accumulate ? nullptr : g.diag;
   p.status = ex.status;
   dim3 grid(ceil_div(g.N, C::BN), ceil_div(g.M, BM), fx_nsplit(g.K));
   KScope ks(ex, g.kclass, 1);

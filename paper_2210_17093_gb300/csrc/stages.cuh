@@ -37,6 +37,7 @@ struct TcBufs {
   int mb = 0;            // m values per self-energy block
   long long sp = 0;      // padded n_ov
   TcMat L;               // (n_aux*nb) x nb: L[P][nu][mu]       (per set_ri)
+  FxMat Lfx;             // the same as 4 fixed-point digits (BF16X10 with MOLGW_FLAG_TC_AB)
   TcMat Ct, X, Xv, Rt, Bt, W, P;                  // per pass (lane arena)
   float* wpart = nullptr;                         // float32 K-chunk partials of w
   long long wpart_floats = 0;
@@ -57,6 +58,8 @@ struct FxBufs {
   void* wp_base = nullptr;     // arena of the sliced w and g*w of a block
 };
 int fx_mblock(int nb, int na, long long nov);
+// lane arena of stages (a), (b) on the fixed-point engine: C, T = L C and Xv as digits
+size_t fx_ab_bytes(int nb, int na, long long nov);
 size_t fx_sigma_bytes(int nb, int na, long long nov, int mb);
 void fx_bufs_carve(FxBufs& f, int nb, int na, long long nov, int mb, void* base);
 
@@ -96,5 +99,7 @@ int stage_ri_mo_transform_tc(Exec& ex, MolBuf& m, TcBufs& t);
 int stage_rpa_build_tc(Exec& ex, MolBuf& m, TcBufs& t);
 int stage_sigma_tc(Exec& ex, MolBuf& m, TcBufs& t, Scratch& s, double eta);
 int stage_sigma_fx(Exec& ex, MolBuf& m, FxBufs& f, Scratch& s, double eta);
+int stage_ri_mo_transform_fx(Exec& ex, MolBuf& m, const FxMat& L, void* arena);
+int stage_rpa_build_fx(Exec& ex, MolBuf& m, void* arena);
 
 }  // namespace molgw

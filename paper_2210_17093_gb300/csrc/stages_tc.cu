@@ -338,6 +338,75 @@ __global__ void __launch_bounds__(256) k_fx_sigma_slices(const double* __restric
 }
 }  // namespace
 
+namespace {
+
+// element (r = P nb + p, k = mu) = T[P][mu][p] of T = L C (for B_P = C^T T_P, read
+// transposed through the symmetry of B_P)
+struct TSrc {
+  const double* T;
+  long long nb, rows;
+  __device__ double operator()(long long r, long long k) const {
+    if (r >= rows || k >= nb) return 0.0;
+    const long long P = r / nb, pp = r - P * nb;
+    return T[(P * nb + k) * nb + pp];
+  }
+};
+
+}  // namespace
+
+size_t fx_ab_bytes(int nb, int na, long long nov) {
+  const long long nbp = fx_pad(nb), nap = fx_pad(na);
+  return fx_mat_bytes(nb, nbp) + fx_mat_bytes((long long)na * nb, nbp) + fx_mat_bytes(nov, nap) + 1024;
+}
+
+// (a) on the fixed-point engine: T[P][mu][q] = sum_nu L[P][mu][nu] C[nu][q], then
+// B[P][p][q] = sum_mu T[P][mu][p] C[mu][q] (= (C^T L_P C)[q][p], B_P symmetric).
+int stage_ri_mo_transform_fx(Exec& ex, MolBuf& m, const FxMat& L, void* arena) {
+  const int nb = m.nb, na = m.na;
+  const long long nbp = fx_pad(nb), rows = (long long)na * nb;
+  char* p = (char*)arena;
+  FxMat Cb = fx_mat_carve(p, nb, nbp);                     // (q, nu) = C[nu][q]
+  p += fx_mat_bytes(nb, nbp);
+  FxMat Ta = fx_mat_carve(p, rows, nbp);                   // ((P, p), mu) = T[P][mu][p]
+  fx_split(ex, m.C, nb, nb, 1, nb, nullptr, Cb);
+  FxGemm g1;
+  g1.M = (int)rows; g1.N = nb; g1.K = (int)nbp;
+  g1.A = L; g1.B = Cb;
+  g1.out = m.T1; g1.out_ld = nb;
+  int r = fx_gemm(ex, g1);
+  if (r) return r;
+  TSrc ts{m.T1, nb, rows};
+  fx_slice(ex, ts, rows, Ta);
+  FxGemm g2;
+  g2.M = (int)rows; g2.N = nb; g2.K = (int)nbp;
+  g2.A = Ta; g2.B = Cb;
+  g2.out = m.B; g2.out_ld = nb;
+  return fx_gemm(ex, g2);
+}
+
+// (b) on the fixed-point engine: M = D^2 + Xv Xv^T, the lower 64-blocks of the
+// column-major matrix (diagonal blocks in full), one launch per 1024-wide K group.
+int stage_rpa_build_fx(Exec& ex, MolBuf& m, void* arena) {
+  const int nb = m.nb, na = m.na;
+  const long long nov = m.nov, nbp = fx_pad(nb), nap = fx_pad(na);
+  gather_xv(ex, m);                                        // float64 Xv (column-major) and D
+  char* p = (char*)arena + fx_mat_bytes(nb, nbp) + fx_mat_bytes((long long)na * nb, nbp);
+  FxMat X = fx_mat_carve(p, nov, nap);                     // (t, P) = Xv[P][t]
+  fx_split(ex, m.Xv, nov, na, 1, nov, nullptr, X);
+  for (long long g0 = 0; g0 < nap; g0 += kFxGroup) {
+    FxGemm g;
+    g.M = (int)nov; g.N = (int)nov; g.K = (int)std::min<long long>(kFxGroup, nap - g0); g.k0 = (int)g0;
+    g.A = X; g.B = X;
+    g.out = m.M; g.out_ld = nov; g.col_major = true;
+    g.lower_only = true;
+    g.accumulate = g0 > 0;
+    g.diag = m.D;
+    int r = fx_gemm(ex, g);
+    if (r) return r;
+  }
+  return MOLGW_OK;
+}
+
 int fx_mblock(int nb, int na, long long nov) {
   const long long sp = fx_pad(nov);
   const long long per_m = (long long)fx_nsplit((int)fx_pad(na)) * nb * nov * 8 + 2 * (long long)fx_mat_bytes(nb, sp);

@@ -165,11 +165,30 @@ def test_bf16x10_bench_size_within_1meV():
     assert np.max(np.abs(eps - r["eps_new"])) < 1.0 * MEV
 
 
-def test_bf16x10_rejects_tc_ab():
-    from paper_2210_17093_gb300 import MolgwError, FLAG_TC_AB
-    with pytest.raises(MolgwError) as e:
-        lib_context(precision="bf16x10", flags=FLAG_TC_AB)
-    assert e.value.code == -1
+@pytest.mark.parametrize("nb,no,na,seed", [(71, 13, 150, 2), (200, 40, 600, 1)])
+def test_bf16x10_tc_ab_within_1meV(nb, no, na, seed):
+    """(a) and (b) on the fixed-point engine too (MOLGW_FLAG_TC_AB): B and M to ~1e-9,
+    Omega to ~1e-7 Ha, QP energies still within 1 meV."""
+    from paper_2210_17093_gb300 import FLAG_TC_AB
+    m = sy.molecule(nb, no, na, seed)
+    r = qsgw.qsgw_pass(m["L"], m["eps"], m["C"], no, ETA)
+    nov = no * (nb - no)
+    with lib_context(precision="bf16x10", eta=ETA, flags=FLAG_TC_AB) as ctx:
+        load_mol(ctx, 0, m)
+        M = np.empty(nov * nov)
+        ctx.rpa_matrix(0, M)
+        B = np.empty(na * nb * nb)
+        ctx.fetch(0, "B", B)
+        om = np.empty(nov)
+        ctx.rpa(0, om)
+        eps = np.empty(nb)
+        ctx.qs_step(0, eps)
+    print(f"nb={nb}: B {rel_max(B.reshape(na, nb, nb), r['B']):.2e} M {rel_max(M.reshape(nov, nov), r['M']):.2e} "
+          f"Omega {np.max(np.abs(om - r['Omega'])):.2e} QP {np.max(np.abs(eps - r['eps_new'])) / MEV:.4f} meV")
+    assert rel_max(B.reshape(na, nb, nb), r["B"]) < 1e-8
+    assert rel_max(M.reshape(nov, nov), r["M"]) < 5e-8
+    assert np.max(np.abs(om - r["Omega"])) < 1e-5
+    assert np.max(np.abs(eps - r["eps_new"])) < 1.0 * MEV
 
 
 def test_eig_tc_eigh_matches_float64():
