@@ -40,6 +40,7 @@ import synthetic as sy  # noqa: E402
 
 METRIC = "s per qsGW iteration; TFLOP/s vs peak; mixed vs FP64 GPU speedup at ≤1 meV QP error"
 WORKLOADS = {
+    "A": dict(nb=24, no=5, na=72, seed=0),
     "B": dict(nb=200, no=40, na=600, seed=1),
     "C": dict(nb=400, no=80, na=1200, seed=4),
     "E": dict(nb=600, no=120, na=1800, seed=7),
@@ -147,6 +148,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def molecule_seed(wl, rank):
+    """Weak scaling: rank r runs its own molecule of the workload's shape, seed + r."""
+    return wl["seed"] + rank
+
+
+def batch_seeds(rank):
+    """Weak scaling of the batch: rank r runs 64 molecules of its own, seeds 100..163 + 64 r."""
+    return [s + 64 * rank for s in sy.BATCH_SEEDS]
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -217,6 +228,38 @@ def run_reference(args, wl):
     return 0
 
 
+def run_reference_batch(args):
+    """The oracle on workload D: each step one oracle iteration of a bounded sample of
+    8 of the 64 molecules, scaled to the whole batch (rank 0 only)."""
+    world, rank, local, dist = dist_setup()
+    if rank != 0:
+        return 0
+    from oracle import qsgw
+    mols = [sy.batch_molecule(s) for s in batch_seeds(0)]
+    sample = mols[:8]
+    steps, warmup = min(args.steps, 3), min(args.warmup, 1)
+    for _ in range(warmup):
+        qsgw.qsgw_pass(sample[0]["L"], sample[0]["eps"], sample[0]["C"], sample[0]["n_occ"], sy.ETA)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for m in sample:
+            qsgw.qsgw_pass(m["L"], m["eps"], m["C"], m["n_occ"], sy.ETA)
+    t = (time.perf_counter() - t0) / steps * len(mols) / len(sample)
+    desc = (f"one oracle iteration of molecules {sy.BATCH_SEEDS[0]}..{sy.BATCH_SEEDS[7]} (n_basis "
+            f"{', '.join(str(m['n_basis']) for m in sample)}) per step, time x {len(mols)}/{len(sample)}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": t, "unit": "s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": warmup, "ms_per_step": t * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "ragged batch of 64 closed-shell RI-qsGW iterations (oracle sample)",
+                   "molecules": len(mols), "eta_ha": sy.ETA},
+        "cpu_baseline": {"value": t, "unit": "s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc},
+        "e2e": {"value": t, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_ours(args, wl):
     import torch
 
@@ -227,7 +270,7 @@ def run_ours(args, wl):
     dev = f"cuda:{local}"
     nb, no, na = wl["nb"], wl["no"], wl["na"]
     n = no * (nb - no)
-    m = sy.molecule(nb, no, na, wl["seed"] + rank)
+    m = sy.molecule(nb, no, na, molecule_seed(wl, rank))
     st = torch.cuda.Stream(device=dev)
     L_d = torch.from_numpy(m["L"]).to(dev)
     eps_d = torch.from_numpy(m["eps"]).to(dev)
@@ -415,7 +458,7 @@ def run_batch(args):
     from paper_2210_17093_gb300 import FLAG_GRAPH, FLAG_TC_AB, Context
 
     torch.cuda.set_device(local)
-    seeds = [s + 64 * rank for s in sy.BATCH_SEEDS]
+    seeds = batch_seeds(rank)
     mols = [sy.batch_molecule(s) for s in seeds]
     st = torch.cuda.Stream(device=f"cuda:{local}")
     flops = {}
@@ -539,8 +582,7 @@ def main():
         args.warmup = 3
     if args.workload == "D":
         if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "workload D has no reference line; use the default"}))
-            return 0
+            return run_reference_batch(args)
         return run_batch(args)
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
