@@ -105,7 +105,8 @@ typedef struct {
                           unless MOLGW_FLAG_USE_STREAM asks for the legacy default stream */
   uint32_t flags;      /* enum molgw_flags                                          */
   int32_t lanes;       /* mol = -1: molecules run on up to this many concurrent streams
-                          (0 = 8, the maximum), assigned longest pass first          */
+                          (at most 16), assigned longest pass first; 0 = 8, or the
+                          count molgw_b200_autotune chose                             */
 } molgw_opts;
 
 /* Create a context.  Returns MOLGW_E_ARG for a bad opts, MOLGW_E_CUDA if the
@@ -225,6 +226,18 @@ int64_t molgw_b200_launch_count(molgw_ctx ctx);
  * engine with that many digits (any precision).  Allocates temporaries and
  * synchronises. */
 int molgw_b200_tc_gemm(molgw_ctx ctx, int digits, int M, int N, int K, const double* A, const double* B, double* C);
+
+/* Library extension (the paper has no counterpart): tune the batch schedule.
+ * Times one qs_step of all ready molecules (mol = -1) with 4, 8, 12 and 16
+ * concurrent lanes (fewer when there are fewer molecules), puts every molecule's
+ * energies, orbitals and h_MO back after each trial, and keeps the fastest lane
+ * count for later mol = -1 calls when opts.lanes is 0.  *lanes_out (may be NULL)
+ * receives it.  Synchronises; allocates a snapshot of the orbitals meanwhile.
+ * MOLGW_E_STATE when no molecule is ready. */
+int molgw_b200_autotune(molgw_ctx ctx, int32_t* lanes_out);
+
+/* Lane count the next mol = -1 call uses. */
+int32_t molgw_b200_lanes(molgw_ctx ctx);
 
 /* Library extension (the paper has no counterpart): number of qs_step calls
  * served by replaying a captured graph (MOLGW_FLAG_GRAPH); -1 once a capture

@@ -27,7 +27,8 @@ struct Lane {
   long long eigfx_rows = 0, eigfx_cols = 0;
 };
 
-constexpr int kMaxLanes = 8;
+constexpr int kMaxLanes = 16;
+constexpr int kDefaultLanes = 8;
 
 struct molgw_ctx_s {
   molgw_opts opts{};
@@ -50,6 +51,8 @@ struct molgw_ctx_s {
   int64_t graph_launches[MOLGW_K_COUNT] = {0};
   bool graph_off = false;        // capture failed once: run eagerly from then on
   int64_t graph_replays = 0;
+  int graph_lanes = 0;           // lane count of the captured plan
+  int tuned_lanes = 0;           // molgw_b200_autotune's choice (0: none)
 };
 
 namespace {
@@ -412,8 +415,13 @@ struct Plan {
 };
 
 // Longest-processing-time-first assignment of molecules to at most `lanes` lanes.
-Plan plan_batch(molgw_ctx c, const std::vector<int>& mols) {
-  int want = c->opts.lanes > 0 ? c->opts.lanes : kMaxLanes;
+int lanes_wanted(molgw_ctx c) {
+  if (c->opts.lanes > 0) return std::min(c->opts.lanes, kMaxLanes);
+  return c->tuned_lanes > 0 ? c->tuned_lanes : kDefaultLanes;
+}
+
+Plan plan_batch(molgw_ctx c, const std::vector<int>& mols, int lanes = 0) {
+  int want = lanes > 0 ? lanes : lanes_wanted(c);
   want = std::max(1, std::min(std::min(want, kMaxLanes), (int)mols.size()));
   std::vector<int> order(mols);
   std::stable_sort(order.begin(), order.end(),
@@ -538,6 +546,7 @@ bool graph_capture(molgw_ctx c, int mol, const std::vector<int>& mols, const Pla
   c->graph_mol = mol;
   c->graph_gen = c->gen;
   c->graph_set = mol_set(c, mols);
+  c->graph_lanes = (int)p.lane_mols.size();
   return true;
 }
 
@@ -561,7 +570,8 @@ int run_mols(molgw_ctx c, int mol, char upto) {
   bool graph = upto == 'f' && (c->opts.flags & MOLGW_FLAG_GRAPH) && !c->graph_off;
   for (int k : mols) graph = graph && steady(c->mols[k]);
   if (!graph) return issue_plan(c, p, upto);
-  const bool match = c->gexec && c->graph_mol == mol && c->graph_gen == c->gen && c->graph_set == mol_set(c, mols);
+  const bool match = c->gexec && c->graph_mol == mol && c->graph_gen == c->gen && c->graph_set == mol_set(c, mols) &&
+                     c->graph_lanes == (int)p.lane_mols.size();
   if (!match && !graph_capture(c, mol, mols, p)) return issue_plan(c, p, upto);
   if (cudaGraphLaunch(c->gexec, c->st) != cudaSuccess) return cuda_status(cudaGetLastError());
   ++c->graph_replays;
@@ -945,6 +955,77 @@ int molgw_b200_tc_gemm(molgw_ctx c, int digits, int M, int N, int K, const doubl
   free_all(tmp);
   return r ? r : st;
 }
+
+int molgw_b200_autotune(molgw_ctx c, int32_t* lanes_out) {
+  if (!c) return MOLGW_E_ARG;
+  DeviceGuard g(c->device);
+  std::vector<int> mols;
+  for (int k = 0; k < (int)c->mols.size(); ++k)
+    if (ready(c->mols[k])) mols.push_back(k);
+  if (mols.empty()) return MOLGW_E_STATE;
+  // snapshot of the state a qs_step changes: eps, C, h_MO and the host flags
+  std::vector<void*> tmp;
+  int err = 0;
+  std::vector<double*> snap;
+  std::vector<Flags> flags;
+  for (int k : mols) {
+    const MolBuf& m = c->mols[k];
+    const size_t nn = (size_t)m.nb * m.nb;
+    double* b = dalloc(tmp, m.nb + 2 * nn, &err);
+    if (err) { free_all(tmp); return err; }
+    snap.push_back(b);
+    flags.push_back(get_flags(m));
+    cudaMemcpyAsync(b, m.eps, m.nb * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    cudaMemcpyAsync(b + m.nb, m.C, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    cudaMemcpyAsync(b + m.nb + nn, m.hmo, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  }
+  auto restore = [&]() {
+    for (size_t q = 0; q < mols.size(); ++q) {
+      MolBuf& m = c->mols[mols[q]];
+      const size_t nn = (size_t)m.nb * m.nb;
+      cudaMemcpyAsync(m.eps, snap[q], m.nb * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+      cudaMemcpyAsync(m.C, snap[q] + m.nb, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+      cudaMemcpyAsync(m.hmo, snap[q] + m.nb + nn, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+      put_flags(m, flags[q]);
+    }
+  };
+  std::vector<int> cand;
+  for (int l : {4, 8, 12, 16}) {
+    const int v = std::min(l, (int)mols.size());
+    if (cand.empty() || cand.back() != v) cand.push_back(v);
+  }
+  int best = 0;
+  float best_ms = 0.0f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int r = MOLGW_OK;
+  for (int lanes : cand) {
+    Plan p = plan_batch(c, mols, lanes);
+    r = plan_fit(c, p);
+    if (r) break;
+    cudaEventRecord(e0, c->st);
+    r = issue_plan(c, p, 'f');
+    cudaEventRecord(e1, c->st);
+    restore();
+    if (r) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) { r = cuda_status(cudaGetLastError()); break; }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best == 0 || ms < best_ms) { best = (int)p.lane_mols.size(); best_ms = ms; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const int s = read_status(c);   // the snapshot is freed below: synchronise first
+  free_all(tmp);
+  if (r) return r;
+  if (s) return s;
+  c->tuned_lanes = best;
+  if (lanes_out) *lanes_out = lanes_wanted(c);
+  return MOLGW_OK;
+}
+
+int32_t molgw_b200_lanes(molgw_ctx c) { return c ? lanes_wanted(c) : 0; }
 
 int64_t molgw_b200_graph_replays(molgw_ctx c) {
   if (!c) return 0;

@@ -36,7 +36,7 @@ EXPORTS = ["molgw_b200_create", "molgw_b200_set_ri", "molgw_b200_set_orbitals", 
            "molgw_b200_rpa_matrix", "molgw_b200_eigh", "molgw_b200_kernel_stats",
            "molgw_b200_launch_count", "molgw_b200_set_timing", "molgw_b200_destroy",
            "molgw_b200_status_string", "molgw_b200_eigh_noalloc", "molgw_b200_graph_replays",
-           "molgw_b200_tc_gemm"]
+           "molgw_b200_tc_gemm", "molgw_b200_autotune", "molgw_b200_lanes"]
 NOALLOC_NMAX = 256
 
 
@@ -80,6 +80,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "molgw_b200_kernel_stats": ([vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double), ip], ip),
         "molgw_b200_launch_count": ([vp], ctypes.c_int64),
         "molgw_b200_graph_replays": ([vp], ctypes.c_int64),
+        "molgw_b200_autotune": ([vp, ctypes.POINTER(ctypes.c_int32)], ip),
+        "molgw_b200_lanes": ([vp], ctypes.c_int32),
         "molgw_b200_tc_gemm": ([vp, ip, ip, ip, ip, vp, vp, vp], ip),
         "molgw_b200_set_timing": ([vp, ctypes.c_uint32], ip),
         "molgw_b200_destroy": ([vp], ip),
@@ -227,6 +229,15 @@ class Context:
         N = B.shape[0]
         _check(self._lib.molgw_b200_tc_gemm(self._hh(), digits, M, N, K, _ptr(A, M * K), _ptr(B, N * K),
                                             _ptr(C, M * N)), "tc_gemm")
+
+    def autotune(self) -> int:
+        """Time one qs_step(-1) per lane count (state restored after each), keep the fastest."""
+        out = ctypes.c_int32(0)
+        _check(self._lib.molgw_b200_autotune(self._hh(), ctypes.byref(out)), "autotune")
+        return int(out.value)
+
+    def lanes(self) -> int:
+        return int(self._lib.molgw_b200_lanes(self._hh()))
 
     def graph_replays(self) -> int:
         """qs_step calls served from a captured graph (-1: capture failed, graphs off)."""

@@ -129,3 +129,19 @@ def test_mixed_lanes_match_solo():
         solo = run_solo(m, precision="bf16x3")
         assert np.max(np.abs(hist[0][k]["eps"] - solo["eps"])) < 1e-7, k
         assert rel_max(hist[0][k]["sigma_c"], solo["sigma_c"]) < 1e-6, k
+
+
+def test_autotune_restores_state_and_keeps_a_lane_count():
+    """molgw_b200_autotune times trial steps and puts the orbitals back: the next step
+    equals a step of a context fixed to the chosen lane count, bit for bit."""
+    mols = [sy.batch_molecule(s) for s in (100, 101, 102, 104, 107, 110)]
+    with lib_context(stream=None, eta=sy.ETA, max_mols=len(mols)) as ctx:
+        for k, m in enumerate(mols):
+            load_mol(ctx, k, m, device=False)
+        lanes = ctx.autotune()
+        assert ctx.lanes() == lanes and lanes in (4, 6)
+        ctx.qs_step(-1)
+        tuned = [fetch(ctx, k, m, "eps") for k, m in enumerate(mols)]
+    hist, _, _ = run_batch(mols, lanes=lanes)
+    for k in range(len(mols)):
+        assert np.array_equal(tuned[k], hist[0][k]["eps"]), k
