@@ -145,3 +145,20 @@ def test_autotune_restores_state_and_keeps_a_lane_count():
     hist, _, _ = run_batch(mols, lanes=lanes)
     for k in range(len(mols)):
         assert np.array_equal(tuned[k], hist[0][k]["eps"]), k
+
+
+def test_bf16x10_tc_ab_lanes_match_solo():
+    """The fixed-point path with (a) and (b) on the tensor cores too, as a batch on
+    concurrent lanes (each lane carves its own operand arena) against solo runs."""
+    from paper_2210_17093_gb300 import FLAG_TC_AB
+    mols = [sy.batch_molecule(s) for s in (100, 105, 108, 122)]
+
+    def solo(m):
+        with lib_context(stream=None, precision="bf16x10", eta=sy.ETA, flags=FLAG_TC_AB) as ctx:
+            load_mol(ctx, 0, m, device=False)
+            ctx.qs_step(0)
+            return fetch(ctx, 0, m, "eps")
+
+    hist, _, _ = run_batch(mols, precision="bf16x10", flags=FLAG_TC_AB)
+    for k, m in enumerate(mols):
+        assert np.max(np.abs(hist[0][k]["eps"] - solo(m))) < 1e-7, k
