@@ -227,13 +227,16 @@ int64_t molgw_b200_launch_count(molgw_ctx ctx);
  * synchronises. */
 int molgw_b200_tc_gemm(molgw_ctx ctx, int digits, int M, int N, int K, const double* A, const double* B, double* C);
 
-/* Library extension (the paper has no counterpart): tune the batch schedule.
- * Times one qs_step of all ready molecules (mol = -1) with 4, 8, 12 and 16
- * concurrent lanes (fewer when there are fewer molecules), puts every molecule's
- * energies, orbitals and h_MO back after each trial, and keeps the fastest lane
- * count for later mol = -1 calls when opts.lanes is 0.  *lanes_out (may be NULL)
- * receives it.  Synchronises; allocates a snapshot of the orbitals meanwhile.
- * MOLGW_E_STATE when no molecule is ready. */
+/* Library extension (the paper has no counterpart): tune the schedule.
+ * Runs trial qs_steps of all ready molecules (mol = -1) and puts every
+ * molecule's energies, orbitals and h_MO back after each: a first trial times
+ * every float64 GEMM shape of the pass with each tile side (64, 48, 40, 32;
+ * the results are bit-identical, only the time differs) and keeps the fastest
+ * per shape; then one trial each with 4, 8, 12 and 16 concurrent lanes (fewer
+ * with fewer molecules) picks the lane count used by later mol = -1 calls when
+ * opts.lanes is 0.  *lanes_out (may be NULL) receives it.  Synchronises;
+ * allocates a snapshot of the orbitals meanwhile.  MOLGW_E_STATE when no
+ * molecule is ready. */
 int molgw_b200_autotune(molgw_ctx ctx, int32_t* lanes_out);
 
 /* Lane count the next mol = -1 call uses. */

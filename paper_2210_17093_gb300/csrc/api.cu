@@ -53,6 +53,7 @@ struct molgw_ctx_s {
   int64_t graph_replays = 0;
   int graph_lanes = 0;           // lane count of the captured plan
   int tuned_lanes = 0;           // molgw_b200_autotune's choice (0: none)
+  GemmTuner tuner;               // float64 GEMM tile choices (molgw_b200_autotune)
 };
 
 namespace {
@@ -157,6 +158,7 @@ int lane_get(molgw_ctx c, int k, Lane** out) {
     l.ex.st = l.st;
     l.ex.status = c->d_status;
     l.ex.timer = &c->timer;
+    l.ex.tuner = &c->tuner;
     c->lanes.push_back(l);
   }
   *out = &c->lanes[k];
@@ -1000,7 +1002,19 @@ int molgw_b200_autotune(molgw_ctx c, int32_t* lanes_out) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   int r = MOLGW_OK;
+  {
+    // an untimed first trial on one lane measures the tile side of every float64
+    // GEMM shape of the pass (the lane trials below then run with those tiles)
+    c->tuner.active = true;
+    Plan p = plan_batch(c, mols, 1);
+    r = plan_fit(c, p);
+    if (!r) r = issue_plan(c, p, 'f');
+    c->tuner.active = false;
+    restore();
+    if (!r && cudaStreamSynchronize(c->st) != cudaSuccess) r = cuda_status(cudaGetLastError());
+  }
   for (int lanes : cand) {
+    if (r) break;
     Plan p = plan_batch(c, mols, lanes);
     r = plan_fit(c, p);
     if (r) break;

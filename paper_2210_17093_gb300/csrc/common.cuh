@@ -42,8 +42,11 @@ struct KTimer {
   }
 };
 
+struct GemmTuner;
+
 struct Exec {
   cudaStream_t st = nullptr;
+  GemmTuner* tuner = nullptr;  // tile choices of the float64 GEMM (per context), or none
   int* status = nullptr;   // device status word (0 = OK, else a molgw_status)
   KTimer* timer = nullptr;
   bool capturing = false;  // inside stream capture: no events, no allocation
@@ -101,6 +104,25 @@ struct GemmF64 {
   int kclass = MOLGW_K_GEMM_F64;  // kernel class for launch accounting
 };
 void gemm_f64(Exec& ex, const GemmF64& g);
+
+// Measured tile choices of gemm_f64.  Shapes are bucketed (four buckets per octave
+// of M, N and K, exact batch and operand layouts); while `active`, a shape not yet
+// seen is run once with every tile side (64, 48, 40, 32) into a scratch output
+// and the fastest is kept.  All sides give bit-identical results (each output is
+// one thread's sequential sum over K), so the choice changes only the time.
+struct GemmTuner {
+  bool active = false;
+  std::vector<std::pair<std::vector<long long>, int>> best;
+  double* scratch = nullptr;
+  size_t scratch_cap = 0;          // doubles
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int tuned = 0;                   // shapes measured so far
+  ~GemmTuner() {
+    if (scratch) cudaFree(scratch);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
 // Choose a K split so that the grid fills the GPU; returns 1 if not needed.
 int gemm_f64_pick_split(int M, int N, int K, int batch, size_t work_cap_doubles);
 

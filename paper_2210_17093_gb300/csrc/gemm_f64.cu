@@ -158,6 +158,73 @@ int gemm_f64_pick_split(int M, int N, int K, int batch, size_t work_cap_doubles)
   return (int)std::max<long long>(1, std::min<long long>(ks, 64));
 }
 
+namespace {
+
+long long bucket(long long x) {
+  // the smallest of {4, 5, 6, 7} x 2^k (k >= 0) that is >= x
+  if (x <= 4) return x;
+  long long b = 4;
+  while (b * 2 < x) b *= 2;
+  for (long long f = 4; f <= 8; ++f)
+    if (b / 4 * f >= x) return b / 4 * f;
+  return b * 2;
+}
+
+void launch_side(Exec& ex, const GemmParams& p, int side, int kclass, int M, int N, int batch) {
+  dim3 grid(ceil_div(N, side), ceil_div(M, side), batch * p.ksplit);
+  KScope ks(ex, kclass, p.ksplit > 1 ? 2 : 1);
+  switch (side) {
+    case 48: gemm_f64_kernel<48, 48><<<grid, 144, 0, ex.st>>>(p); break;
+    case 40: gemm_f64_kernel<40, 40><<<grid, 100, 0, ex.st>>>(p); break;
+    case 32: gemm_f64_kernel<32, 32><<<grid, 64, 0, ex.st>>>(p); break;
+    default: gemm_f64_kernel<64, 64><<<grid, 256, 0, ex.st>>>(p); break;
+  }
+  if (p.ksplit > 1) {
+    const long long total = (long long)M * N * batch;
+    const int blocks = (int)std::min<long long>(ceil_div(total, 256), 152LL * 16);
+    gemm_splitk_reduce<<<blocks, 256, 0, ex.st>>>(p);
+  }
+}
+
+// Time every tile side on the shape of p with the output redirected to the tuner's
+// scratch (beta = 0, the same majorness); returns the fastest side, or 0.
+int tune_side(Exec& ex, const GemmParams& p0, int M, int N, int batch) {
+  GemmTuner& t = *ex.tuner;
+  const size_t need = (size_t)M * N * batch;
+  if (need > ((size_t)64 << 20)) return 0;
+  if (need > t.scratch_cap) {
+    cudaStreamSynchronize(ex.st);
+    if (t.scratch) cudaFree(t.scratch);
+    t.scratch = nullptr;
+    t.scratch_cap = 0;
+    if (cudaMalloc(&t.scratch, need * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return 0; }
+    t.scratch_cap = need;
+  }
+  if (!t.e0) { cudaEventCreate(&t.e0); cudaEventCreate(&t.e1); }
+  GemmParams p = p0;
+  p.C = t.scratch;
+  p.beta = 0.0;
+  if (p0.sc_m == 1) { p.sc_m = 1; p.sc_n = M; } else { p.sc_m = N; p.sc_n = 1; }
+  p.sc_b = (long long)M * N;
+  Exec quiet = ex;
+  quiet.timer = nullptr;
+  int best = 0;
+  float best_ms = 0.0f;
+  for (int side : {64, 48, 40, 32}) {
+    cudaEventRecord(t.e0, ex.st);
+    launch_side(quiet, p, side, MOLGW_K_MISC, M, N, batch);
+    cudaEventRecord(t.e1, ex.st);
+    if (cudaEventSynchronize(t.e1) != cudaSuccess) { cudaGetLastError(); return 0; }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, t.e0, t.e1);
+    if (best == 0 || ms < best_ms) { best = side; best_ms = ms; }
+  }
+  ++t.tuned;
+  return best;
+}
+
+}  // namespace
+
 void gemm_f64(Exec& ex, const GemmF64& g) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
   GemmParams p;
@@ -176,22 +243,20 @@ void gemm_f64(Exec& ex, const GemmF64& g) {
   // else the side that pads M and N least
   const int bm = g.lower_only ? 64 : pick_tile(g.M);
   const int bnn = g.lower_only ? 64 : pick_tile(g.N);
-  const int side = std::min(bm, bnn) == 64 ? 64 : std::max(std::min(bm, bnn), 32);
-  dim3 grid(ceil_div(g.N, side), ceil_div(g.M, side), g.batch * p.ksplit);
-  {
-    KScope ks(ex, g.kclass, p.ksplit > 1 ? 2 : 1);
-    switch (side) {
-      case 48: gemm_f64_kernel<48, 48><<<grid, 144, 0, ex.st>>>(p); break;
-      case 40: gemm_f64_kernel<40, 40><<<grid, 100, 0, ex.st>>>(p); break;
-      case 32: gemm_f64_kernel<32, 32><<<grid, 64, 0, ex.st>>>(p); break;
-      default: gemm_f64_kernel<64, 64><<<grid, 256, 0, ex.st>>>(p); break;
+  int side = std::min(bm, bnn) == 64 ? 64 : std::max(std::min(bm, bnn), 32);
+  if (ex.tuner && !g.lower_only) {
+    const std::vector<long long> key = {bucket(g.M), bucket(g.N), bucket(g.K), g.batch, p.ksplit > 1,
+                                        g.sa_m == 1, g.sa_k == 1, g.sb_k == 1, g.sb_n == 1, g.sc_m == 1};
+    int found = 0;
+    for (const auto& e : ex.tuner->best)
+      if (e.first == key) { found = e.second; break; }
+    if (!found && ex.tuner->active && !ex.capturing) {
+      found = tune_side(ex, p, g.M, g.N, g.batch);
+      if (found) ex.tuner->best.push_back({key, found});
     }
-    if (p.ksplit > 1) {
-      const long long total = (long long)g.M * g.N * g.batch;
-      const int blocks = (int)std::min<long long>(ceil_div(total, 256), 152LL * 16);
-      gemm_splitk_reduce<<<blocks, 256, 0, ex.st>>>(p);
-    }
+    if (found) side = found;
   }
+  launch_side(ex, p, side, g.kclass, g.M, g.N, g.batch);
 }
 
 }  // namespace molgw

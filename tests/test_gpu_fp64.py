@@ -292,3 +292,23 @@ def test_errors_and_call_order():
         om = np.empty(21)
         ctx.rpa(0, om)                                     # the context stays usable
         assert np.all(om > 0)
+
+
+def test_autotuned_tiles_give_identical_bits():
+    """The GEMM tile autotuner changes only the time: a step after tuning equals a
+    step of an untuned context bit for bit (every tile side sums each output over K
+    in the same order)."""
+    m = sy.molecule(100, 20, 300, 3)
+    out = []
+    for tune in (False, True):
+        with lib_context(stream=None) as ctx:
+            load_mol(ctx, 0, m, device=False)
+            if tune:
+                ctx.autotune()
+            e = np.empty(100)
+            ctx.qs_step(0, e)
+            sc = np.empty((100, 100))
+            ctx.fetch(0, "sigma_c", sc)
+            out.append((e, sc))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
