@@ -241,37 +241,62 @@ __global__ void __launch_bounds__(32) k_twisted(const double* __restrict__ d, co
     if (fabs(Dp) < piv) Dp = piv;
     z[(long long)(j + 1) * ld] = Dp;
   }
-  // backward: U-_j into u[j], gamma_j, twist index
+  // backward: U-_j into u[j], gamma_j, twist index.  The stored D+_j are read 8
+  // steps ahead of their use (one warp per SM at most: no other latency hiding).
   double Dm = d[n - 1] - l;
   if (fabs(Dm) < piv) Dm = piv;
   double best = fabs(z[(long long)(n - 1) * ld] + Dm - (d[n - 1] - l));
   int r = n - 1;
-  for (int j = n - 2; j >= 0; --j) {
-    const double Um = e[j] / Dm;
-    u[(long long)j * ld] = Um;
-    Dm = d[j] - l - Um * e[j];
-    if (fabs(Dm) < piv) Dm = piv;
-    const double gam = fabs(z[(long long)j * ld] + Dm - (d[j] - l));
-    if (gam < best) { best = gam; r = j; }
+  constexpr int PF = 8;
+  for (int j0 = n - 2; j0 >= 0; j0 -= PF) {
+    double zp[PF];
+#pragma unroll
+    for (int q = 0; q < PF; ++q) zp[q] = (j0 - q >= 0) ? z[(long long)(j0 - q) * ld] : 0.0;
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      const int j = j0 - q;
+      if (j < 0) break;
+      const double Um = e[j] / Dm;
+      u[(long long)j * ld] = Um;
+      Dm = d[j] - l - Um * e[j];
+      if (fabs(Dm) < piv) Dm = piv;
+      const double gam = fabs(zp[q] + Dm - (d[j] - l));
+      if (gam < best) { best = gam; r = j; }
+    }
   }
-  // solve outward from the twist index
+  // solve outward from the twist index (stored D+_j and U-_j prefetched likewise)
   double nrm2 = 1.0, big = 1.0;
   int sgn = 1;
   double zj = 1.0;
-  for (int j = r - 1; j >= 0; --j) {
-    const double Dpj = z[(long long)j * ld];
-    zj = -(e[j] / Dpj) * zj;
-    z[(long long)j * ld] = zj;
-    nrm2 += zj * zj;
-    if (fabs(zj) > big) { big = fabs(zj); sgn = (zj >= 0.0) ? 1 : -1; }
+  for (int j0 = r - 1; j0 >= 0; j0 -= PF) {
+    double dp[PF];
+#pragma unroll
+    for (int q = 0; q < PF; ++q) dp[q] = (j0 - q >= 0) ? z[(long long)(j0 - q) * ld] : 1.0;
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      const int j = j0 - q;
+      if (j < 0) break;
+      zj = -(e[j] / dp[q]) * zj;
+      z[(long long)j * ld] = zj;
+      nrm2 += zj * zj;
+      if (fabs(zj) > big) { big = fabs(zj); sgn = (zj >= 0.0) ? 1 : -1; }
+    }
   }
   z[(long long)r * ld] = 1.0;
   zj = 1.0;
-  for (int j = r; j < n - 1; ++j) {
-    zj = -u[(long long)j * ld] * zj;
-    z[(long long)(j + 1) * ld] = zj;
-    nrm2 += zj * zj;
-    if (fabs(zj) > big) { big = fabs(zj); sgn = (zj >= 0.0) ? 1 : -1; }
+  for (int j0 = r; j0 < n - 1; j0 += PF) {
+    double um[PF];
+#pragma unroll
+    for (int q = 0; q < PF; ++q) um[q] = (j0 + q < n - 1) ? u[(long long)(j0 + q) * ld] : 0.0;
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      const int j = j0 + q;
+      if (j >= n - 1) break;
+      zj = -um[q] * zj;
+      z[(long long)(j + 1) * ld] = zj;
+      nrm2 += zj * zj;
+      if (fabs(zj) > big) { big = fabs(zj); sgn = (zj >= 0.0) ? 1 : -1; }
+    }
   }
   const double sc = (sgn > 0 ? 1.0 : -1.0) / sqrt(nrm2);
   for (int j = 0; j < n; ++j) z[(long long)j * ld] *= sc;
