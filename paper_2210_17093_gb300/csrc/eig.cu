@@ -446,14 +446,29 @@ void apply_panel_fx(Exec& ex, EigWork& w, int n, const double* V, int nbp, int m
   const int kp = (int)fx_pad(m);
   fx_split(ex, V, nbp, m, n, 1, nullptr, b.vt, MOLGW_K_BACKTRANSFORM);     // (c, r) = V(r, c)
   fx_split(ex, Xk, nc, m, sc, sr, nullptr, b.xs, MOLGW_K_BACKTRANSFORM);   // (col, r) = X(r, col)
-  for (int g0 = 0; g0 < kp; g0 += kFxGroup) {
+  const int ns = fx_nsplit(kp);
+  if ((size_t)ns * nbp * nc > w.gk_cap) {
+    // partials would not fit: one launch per K group, accumulated in order
+    for (int g0 = 0; g0 < kp; g0 += kFxGroup) {
+      FxGemm g;
+      g.M = nbp; g.N = nc; g.K = std::min(kFxGroup, kp - g0); g.k0 = g0;
+      g.A = b.vt; g.B = b.xs;
+      g.out = w.tmp1; g.out_ld = nc;
+      g.accumulate = g0 > 0;
+      g.kclass = MOLGW_K_BACKTRANSFORM;
+      fx_gemm(ex, g);
+    }
+  } else {
+    // all K groups in one launch: per-group partials in the split-K workspace,
+    // then summed in group order into tmp1
     FxGemm g;
-    g.M = nbp; g.N = nc; g.K = std::min(kFxGroup, kp - g0); g.k0 = g0;
+    g.M = nbp; g.N = nc; g.K = kp;
     g.A = b.vt; g.B = b.xs;
-    g.out = w.tmp1; g.out_ld = nc;
-    g.accumulate = g0 > 0;
+    g.out = w.gk; g.out_ld = nc;
+    g.split_stride = (long long)nbp * nc;
     g.kclass = MOLGW_K_BACKTRANSFORM;
     fx_gemm(ex, g);
+    fx_reduce_rm(ex, w.gk, ns, (long long)nbp * nc, nbp, nc, w.tmp1, nc, 0.0);
   }
   GemmF64 g2;
   g2.M = nbp; g2.N = nc; g2.K = nbp;

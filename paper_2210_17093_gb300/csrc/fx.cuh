@@ -161,6 +161,36 @@ __global__ void k_fx_slices(Src f, long long rows, long long ld, FxMat dst) {
   }
 }
 
+// For sources contiguous along K (src[r*sr + k], e.g. a row-major operand): one warp
+// per (row, group), lanes along K, the group's maximum then its digits, both
+// passes coalesced.
+template <int NS>
+__global__ void k_fx_rows(const double* __restrict__ src, long long rows, long long cols, long long sr,
+                          const double* __restrict__ row_scale, FxMat dst) {
+  const int lane = threadIdx.x & 31;
+  const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const long long r = wg / dst.ngroups;
+  const int g = (int)(wg % dst.ngroups);
+  if (r >= rows) return;
+  const long long k0 = (long long)g * kFxGroup;
+  const long long k1 = (dst.ld < k0 + kFxGroup) ? dst.ld : k0 + kFxGroup;
+  const double rs = row_scale ? row_scale[r] : 1.0;
+  double m = 0.0;
+  for (long long k = k0 + lane; k < k1; k += 32)
+    if (k < cols) m = fmax(m, fabs(src[r * sr + k] * rs));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const double u = fx_unit(m);
+  if (lane == 0) dst.u[r * dst.ngroups + g] = u;
+  const double scale = ldexp(1.0, 8 * (NS - 1)) / u;
+  for (long long k = k0 + lane; k < k1; k += 32) {
+    const double x = (k < cols) ? src[r * sr + k] * rs : 0.0;
+    __nv_bfloat16 d[NS];
+    fx_digits<NS>(x, scale, d);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) ((__nv_bfloat16*)dst.s[i])[r * dst.ld + k] = d[i];
+  }
+}
+
 template <class Src>
 void fx_slice(Exec& ex, const Src& f, long long rows, FxMat dst, int kclass = MOLGW_K_MISC) {
   if (rows <= 0) return;
@@ -189,6 +219,10 @@ struct FxStrided {
 // zero for cols <= k < dst.ld; row_scale (optional) multiplies row r.
 void fx_split(Exec& ex, const double* src, long long rows, long long cols, long long sr, long long sk,
               const double* row_scale, FxMat dst, int kclass = MOLGW_K_MISC);
+
+// out[r][c] = beta*out[r][c] + sum_{s<ns} part[s][r][c]  (row-major partials)
+void fx_reduce_rm(Exec& ex, const double* part, int ns, long long split_stride, int M, int N, double* out,
+                  long long ldo, double beta);
 
 // out[r][c] = beta*out[r][c] + sum_{s<ns} part[s][c][r]  (col-major partials)
 void fx_reduce_cm(Exec& ex, const double* part, int ns, long long split_stride, int M, int N, double* out,

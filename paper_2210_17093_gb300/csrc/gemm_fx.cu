@@ -318,6 +318,19 @@ __global__ void __launch_bounds__(NT, 1) fx_gemm_kernel(const __grid_constant__ 
   }
 }
 
+__global__ void k_fx_reduce_rm(const double* __restrict__ part, int ns, long long ss, int M, int N, double* out,
+                               long long ldo, double beta) {
+  const long long total = (long long)M * N;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / N), c = (int)(idx % N);
+    double s = 0.0;
+    for (int k = 0; k < ns; ++k) s += part[k * ss + idx];
+    double* o = out + (long long)r * ldo + c;
+    *o = (beta == 0.0) ? s : s + beta * (*o);
+  }
+}
+
 __global__ void k_fx_reduce_cm(const double* __restrict__ part, int ns, long long ss, int M, int N, double* out,
                                long long ldo, double beta) {
   const long long total = (long long)M * N;
@@ -432,8 +445,27 @@ int fx_gemm(Exec& ex, const FxGemm& g) {
 
 void fx_split(Exec& ex, const double* src, long long rows, long long cols, long long sr, long long sk,
               const double* row_scale, FxMat dst, int kclass) {
+  if (sk == 1 && sr != 1) {
+    if (rows <= 0) return;
+    KScope ks(ex, kclass, 1);
+    const long long warps = rows * dst.ngroups;
+    const int blocks = ceil_div(warps, 8);
+    if (dst.ns == 7)
+      k_fx_rows<7><<<blocks, 256, 0, ex.st>>>(src, rows, cols, sr, row_scale, dst);
+    else
+      k_fx_rows<4><<<blocks, 256, 0, ex.st>>>(src, rows, cols, sr, row_scale, dst);
+    return;
+  }
   FxStrided f{src, sr, sk, rows, cols, row_scale};
   fx_slice(ex, f, rows, dst, kclass);
+}
+
+void fx_reduce_rm(Exec& ex, const double* part, int ns, long long split_stride, int M, int N, double* out,
+                  long long ldo, double beta) {
+  const long long total = (long long)M * N;
+  KScope ks(ex, MOLGW_K_MISC);
+  k_fx_reduce_rm<<<(int)std::min<long long>(ceil_div(total, 256), 152LL * 8), 256, 0, ex.st>>>(
+      part, ns, split_stride, M, N, out, ldo, beta);
 }
 
 void fx_reduce_cm(Exec& ex, const double* part, int ns, long long split_stride, int M, int N, double* out,
