@@ -376,6 +376,19 @@ def run_ours(args, wl):
                "meets_1meV": bool(err * 27211.386 <= 1.0),
                "stages_ms": {k: round(v[1], 3) for k, v in vbreak.items() if v[0]}}
         tc_ms = vbreak.get("gemm_tc", (0, 0.0))[1]
+        sg_ms = vbreak.get("sigma", (0, 0.0))[1]
+        if precision == "bf16x10" and sg_ms > 0:
+            # the fused denominator kernel of (e): per (p, m, s) it reads w (float64, one
+            # partial per 1024-wide group of n_aux) and writes w and g*w as 4 BF16 digits each
+            peaks = measured_peaks()
+            groups = -(-(-(-na // 64) * 64) // 1024)
+            nbytes = nb * nb * n * (8 * groups + 2 * 4 * 2)
+            out["sigma_assembly"] = {
+                "kernel": "k_fx_sigma_slices (float64 eps_p - eps_m -/+ Omega_s, g, digits of w and g w)",
+                "bytes": nbytes, "ms": sg_ms, "achieved_gbs": nbytes / (sg_ms / 1e3) / 1e9,
+                "frac_of_hbm": nbytes / (sg_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                "peak_gbs": peaks["hbm_gbs"], "peak_kind": peaks["kind"],
+                "note": "bound by the float64 pipe (~15 float64 operations per element), not by HBM"}
         if precision == "bf16x10" and tc_ms > 0:
             # ten BF16 digit products per useful multiply-add: w = B_m^T R (K = n_aux padded
             # to 64) and S = (g w) w^T (K = n_basis x n_ov padded to 64)
