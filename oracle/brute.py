@@ -139,6 +139,80 @@ def sigma_mp2_direct(g: np.ndarray, eps: np.ndarray, n_occ: int, eta: float, ome
     return out
 
 
+def antisymmetrised_spin_orbital(g: np.ndarray) -> np.ndarray:
+    """<PQ||RS> over spin orbitals P = 2 p + spin, from chemists' (pq|rs) of real orbitals.
+
+    <PQ|RS> = (pr|qs) delta(spin P, spin R) delta(spin Q, spin S); <PQ||RS> = <PQ|RS> - <PQ|SR>.
+    """
+    nb = g.shape[0]
+    n2 = 2 * nb
+    sp = np.arange(n2) % 2
+    orb = np.arange(n2) // 2
+    phys = g[orb[:, None, None, None], orb[None, None, :, None],
+             orb[None, :, None, None], orb[None, None, None, :]]          # (p r|q s) at [P, Q, R, S]
+    phys = phys * ((sp[:, None, None, None] == sp[None, None, :, None])
+                   & (sp[None, :, None, None] == sp[None, None, None, :]))
+    return phys - phys.transpose(0, 1, 3, 2)
+
+
+def sigma2_spin_orbital(g: np.ndarray, eps: np.ndarray, n_occ: int, eta: float, omega: float,
+                        part: str = "both") -> np.ndarray:
+    """Re of the second-order self-energy over spin orbitals, spatial (m, n) of spin up.
+
+    The antisymmetrised expansion of the self-energy to second order in v:
+      Sigma_mn(w) = 1/2 sum_{I A B} <mI||AB><AB||nI> / (w + e_I - e_A - e_B)     (2p1h)
+                  + 1/2 sum_{I J A} <mA||IJ><IJ||nA> / (w + e_A - e_I - e_J)     (2h1p)
+    with I, J occupied and A, B empty spin orbitals, every sum written out.
+    ``part`` selects "2p1h", "2h1p" or "both".
+    """
+    nb = eps.shape[0]
+    asy = antisymmetrised_spin_orbital(g)
+    e2 = np.repeat(eps, 2)
+    occ = [P for P in range(2 * nb) if P // 2 < n_occ]
+    vir = [P for P in range(2 * nb) if P // 2 >= n_occ]
+    out = np.zeros((nb, nb))
+    for m in range(nb):
+        for n in range(nb):
+            M, N = 2 * m, 2 * n
+            acc = 0.0
+            if part in ("both", "2p1h"):
+                for I in occ:
+                    for A in vir:
+                        for Bb in vir:
+                            x = omega + e2[I] - e2[A] - e2[Bb]
+                            acc += 0.5 * asy[M, I, A, Bb] * asy[A, Bb, N, I] * x / (x * x + eta * eta)
+            if part in ("both", "2h1p"):
+                for I in occ:
+                    for J in occ:
+                        for A in vir:
+                            x = omega + e2[A] - e2[I] - e2[J]
+                            acc += 0.5 * asy[M, A, I, J] * asy[I, J, N, A] * x / (x * x + eta * eta)
+            out[m, n] = acc
+    return out
+
+
+def sigma_mp2_printed(g: np.ndarray, eps: np.ndarray, n_occ: int, eta: float, omega: float,
+                      part: str = "both") -> np.ndarray:
+    """Re of Eq. (Sigma.c.MP2) exactly as printed, four nested loops, one frequency.
+
+    sum_{i a p} [2 (mp|ia)(pn|ai) - (mp|ia)(pi|an)] h_p, with
+    h_p = Re 1/(w + e_a - e_i - e_p) for occupied p ("2h1p"), Re 1/(w + e_i - e_a - e_p)
+    for empty p ("2p1h").
+    """
+    nb = eps.shape[0]
+    out = np.zeros((nb, nb))
+    for p in range(nb):
+        occ_p = p < n_occ
+        if (part == "2h1p" and not occ_p) or (part == "2p1h" and occ_p):
+            continue
+        for i in range(n_occ):
+            for a in range(n_occ, nb):
+                x = omega + (eps[a] - eps[i] - eps[p] if occ_p else eps[i] - eps[a] - eps[p])
+                gx = x / (x * x + eta * eta)
+                out += np.outer(g[:, p, i, a], 2.0 * g[p, :, a, i] - g[p, i, a, :]) * gx
+    return out
+
+
 def jacobi_eigh(A: np.ndarray, tol: float = 1e-15, max_sweeps: int = 100):
     """Cyclic Jacobi eigensolver for a small real symmetric matrix.
 

@@ -26,6 +26,10 @@ the design notes with its justification):
   R5  H0 = h + J with h_MO = diag(eps0) - J0 - Sigma_x0 (input read as an HF
       solution) unless h is supplied; h_MO follows the orbital rotation.
   R6  Aufbau occupations of the sorted updated energies; no mixing.
+  R7  Second-order exchange of Eq. (Sigma.c.MP2) for an occupied summed
+      orbital p (the 2h1p part): the factor is (p a|i n), the one the
+      antisymmetrised second-order expansion gives; the printed (p i|a n) is that
+      expansion's factor only for an empty p (the 2p1h part), which is kept.
 """
 from __future__ import annotations
 
@@ -191,6 +195,72 @@ def sigma_c_at(w: np.ndarray, eps: np.ndarray, Omega: np.ndarray, n_occ: int,
 
 
 # ----------------------------------------------------------------------------
+# Eqs. (Sigma.c.MP2) and (Sigma.c.qsMP2.real): the qsMP2 self-energy
+# ----------------------------------------------------------------------------
+def mp2_factors(B: np.ndarray, n_occ: int, p: int):
+    """The two integral factors of Eq. (Sigma.c.MP2) for one summed orbital p.
+
+    Returns (Ap, Xp), both [n, t] over all orbitals n and transitions t = (i, a):
+      Ap[n, t] = (n p|i a) = sum_P B^P_np B^P_ia           (direct factor),
+      Xp[n, t] = (p a|i n) for occupied p, (p i|a n) for empty p  (exchange
+      partner, reading R7), each = sum_P B^P_.. B^P_.. (Eq. MO.4.ERI).
+    The loop over i keeps every product two-dimensional.
+    """
+    nb = B.shape[1]
+    nv = nb - n_occ
+    i, a = transitions(nb, n_occ)
+    Ap = B[:, :, p].T @ B[:, i, a]                      # [n, t]
+    Xp = np.empty((nb, n_occ * nv))
+    for ii in range(n_occ):
+        cols = slice(ii * nv, (ii + 1) * nv)
+        if p < n_occ:
+            # (p a|i n) = sum_P B^P_pa B^P_in  -> [n, a]
+            Xp[:, cols] = B[:, ii, :].T @ B[:, p, n_occ:]
+        else:
+            # (p i|a n) = sum_P B^P_pi B^P_an  -> [n, a]
+            Xp[:, cols] = np.einsum("P,Pan->na", B[:, p, ii], B[:, n_occ:, :])
+    return Ap, Xp
+
+
+def sigma_mp2_at(B: np.ndarray, eps: np.ndarray, n_occ: int, eta: float,
+                 omega: float) -> np.ndarray:
+    """Re Sigma^MP2_c,mn(omega) for one frequency, all (m, n) (Eq. Sigma.c.MP2).
+
+    Sigma_mn(w) = sum_{p,i,a} (m p|i a) [2 (p n|a i) - X_p(n; i, a)] h_p(w; i, a),
+    the factor 2 being the closed-shell sum over sigma' of the direct term and
+    h_p = Re 1/(w + e_a - e_i - e_p - i eta) for occupied p,
+          Re 1/(w + e_i - e_a - e_p + i eta) for empty p   (reading R3).
+    """
+    nb = eps.shape[0]
+    i, a = transitions(nb, n_occ)
+    D = eps[a] - eps[i]
+    out = np.zeros((nb, nb))
+    for p in range(nb):
+        Ap, Xp = mp2_factors(B, n_occ, p)
+        x = omega - eps[p] + (D if p < n_occ else -D)
+        out += (Ap * g_real(x, eta)[None, :]) @ (2.0 * Ap - Xp).T
+    return out
+
+
+def sigma_mp2_rows(B: np.ndarray, eps: np.ndarray, n_occ: int, eta: float) -> np.ndarray:
+    """S_mn = Re Sigma^MP2_c,mn(omega = eps_m), Eq. (Sigma.c.MP2): row m at its own energy.
+
+    The same sum as ``sigma_mp2_at`` with the denominator taken per row.  The
+    qsMP2 matrix of Eq. (Sigma.c.qsMP2.real) is then 1/2 (S + S^T)
+    (``sigma_c_qs``), since Sigma^MP2(w) is symmetric for real orbitals.
+    """
+    nb = eps.shape[0]
+    i, a = transitions(nb, n_occ)
+    D = eps[a] - eps[i]
+    S = np.zeros((nb, nb))
+    for p in range(nb):
+        Ap, Xp = mp2_factors(B, n_occ, p)
+        x = eps[:, None] - eps[p] + (D if p < n_occ else -D)[None, :]   # [m, t]
+        S += (Ap * g_real(x, eta)) @ (2.0 * Ap - Xp).T
+    return S
+
+
+# ----------------------------------------------------------------------------
 # Eqs. (H), (GEP): quasiparticle update
 # ----------------------------------------------------------------------------
 def hf_core_mo(B: np.ndarray, eps: np.ndarray, n_occ: int) -> np.ndarray:
@@ -244,6 +314,31 @@ def qsgw_pass(L: np.ndarray, eps: np.ndarray, C: np.ndarray, n_occ: int,
         "sigma_x": Sx, "sigma_c": Sc, "J": J, "h_mo": h_mo,
         "eps_new": eps_new, "C_new": C_new, "h_mo_new": h_new, "U": U,
     }
+
+
+def qsmp2_pass(L: np.ndarray, eps: np.ndarray, C: np.ndarray, n_occ: int,
+               eta: float, h_mo: np.ndarray | None = None) -> dict:
+    """One RI-qsMP2 iteration: Eqs. (AO.to.MO) -> (Sigma.c.MP2, Sigma.c.qsMP2.real, K)
+    -> (H, GEP).  No RPA: the correlation self-energy is second order in v."""
+    B = ri_mo_transform(L, C)
+    if h_mo is None:
+        h_mo = hf_core_mo(B, eps, n_occ)
+    Sx = sigma_x(B, n_occ)
+    Sc = sigma_c_qs(sigma_mp2_rows(B, eps, n_occ, eta))
+    J = hartree(B, n_occ)
+    eps_new, C_new, h_new, U = qs_update(h_mo, J, Sx, Sc, C)
+    return {"B": B, "sigma_x": Sx, "sigma_c": Sc, "J": J, "h_mo": h_mo,
+            "eps_new": eps_new, "C_new": C_new, "h_mo_new": h_new, "U": U}
+
+
+def qsmp2_iterations(L, eps, C, n_occ, eta, n_iter, h_mo=None) -> list:
+    """n_iter successive qsMP2 iterations, each starting from the previous (eps', C')."""
+    out = []
+    for _ in range(n_iter):
+        r = qsmp2_pass(L, eps, C, n_occ, eta, h_mo)
+        out.append(r)
+        eps, C, h_mo = r["eps_new"], r["C_new"], r["h_mo_new"]
+    return out
 
 
 def qsgw_iterations(L, eps, C, n_occ, eta, n_iter, h_mo=None) -> list:
