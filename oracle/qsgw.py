@@ -204,22 +204,21 @@ def mp2_factors(B: np.ndarray, n_occ: int, p: int):
       Ap[n, t] = (n p|i a) = sum_P B^P_np B^P_ia           (direct factor),
       Xp[n, t] = (p a|i n) for occupied p, (p i|a n) for empty p  (exchange
       partner, reading R7), each = sum_P B^P_.. B^P_.. (Eq. MO.4.ERI).
-    The loop over i keeps every product two-dimensional.
+    Each factor is one matrix product over P.
     """
-    nb = B.shape[1]
+    na, nb = B.shape[0], B.shape[1]
     nv = nb - n_occ
     i, a = transitions(nb, n_occ)
-    Ap = B[:, :, p].T @ B[:, i, a]                      # [n, t]
-    Xp = np.empty((nb, n_occ * nv))
-    for ii in range(n_occ):
-        cols = slice(ii * nv, (ii + 1) * nv)
-        if p < n_occ:
-            # (p a|i n) = sum_P B^P_pa B^P_in  -> [n, a]
-            Xp[:, cols] = B[:, ii, :].T @ B[:, p, n_occ:]
-        else:
-            # (p i|a n) = sum_P B^P_pi B^P_an  -> [n, a]
-            Xp[:, cols] = np.einsum("P,Pan->na", B[:, p, ii], B[:, n_occ:, :])
-    return Ap, Xp
+    Ap = B[:, :, p].T @ B[:, i, a]                                       # [n, t]
+    if p < n_occ:
+        # (p a|i n) = sum_P B^P_pa B^P_in: [a, (i, n)] -> [n, (i, a)]
+        X = B[:, p, n_occ:].T @ B[:, :n_occ, :].reshape(na, n_occ * nb)
+        Xp = X.reshape(nv, n_occ, nb).transpose(2, 1, 0)
+    else:
+        # (p i|a n) = sum_P B^P_pi B^P_an: [i, (a, n)] -> [n, (i, a)]
+        X = B[:, p, :n_occ].T @ B[:, n_occ:, :].reshape(na, nv * nb)
+        Xp = X.reshape(n_occ, nv, nb).transpose(2, 0, 1)
+    return Ap, Xp.reshape(nb, n_occ * nv)
 
 
 def sigma_mp2_at(B: np.ndarray, eps: np.ndarray, n_occ: int, eta: float,
