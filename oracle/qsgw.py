@@ -30,6 +30,9 @@ the design notes with its justification):
       orbital p (the 2h1p part): the factor is (p a|i n), the one the
       antisymmetrised second-order expansion gives; the printed (p i|a n) is that
       expansion's factor only for an empty p (the 2p1h part), which is kept.
+  R8  G0W0 (the diagonal m = n of Eq. (Sigma.c.GW)): the quasiparticle
+      equation is solved to first order around eps_p (renormalisation factor Z_p),
+      starting from the input mean field whose potential is v = diag(eps) - h - J.
 """
 from __future__ import annotations
 
@@ -192,6 +195,56 @@ def sigma_c_at(w: np.ndarray, eps: np.ndarray, Omega: np.ndarray, n_occ: int,
         wm = w[:, :, m]                               # [s, p]
         out += (wm * gm[:, None]).T @ wm
     return out
+
+
+# ----------------------------------------------------------------------------
+# G0W0: the diagonal of Eq. (Sigma.c.GW) at eps_p, linearised (reading R8)
+# ----------------------------------------------------------------------------
+def g_real_derivative(x, eta: float):
+    """d/dx of x / (x^2 + eta^2) = (eta^2 - x^2) / (x^2 + eta^2)^2."""
+    d = x * x + eta * eta
+    return (eta * eta - x * x) / (d * d)
+
+
+def sigma_c_diag(w: np.ndarray, eps: np.ndarray, Omega: np.ndarray, n_occ: int, eta: float):
+    """Re Sigma^GW_c,pp(omega) and its omega-derivative at omega = eps_p, every p.
+
+    Sigma_pp(w) = sum_{m,s} (w^s_pm)^2 g(w - eps_m +/- Omega_s), Eq. (Sigma.c.GW) with
+    m = n, + Omega_s for occupied m and - Omega_s for empty m.
+    """
+    nb = eps.shape[0]
+    sig = np.zeros(nb)
+    dsig = np.zeros(nb)
+    for m in range(nb):
+        shift = Omega if m < n_occ else -Omega
+        x = eps[:, None] - eps[m] + shift[None, :]        # [p, s]
+        w2 = w[:, :, m].T ** 2                             # [p, s]
+        sig += np.sum(w2 * g_real(x, eta), axis=1)
+        dsig += np.sum(w2 * g_real_derivative(x, eta), axis=1)
+    return sig, dsig
+
+
+def g0w0_pass(L: np.ndarray, eps: np.ndarray, C: np.ndarray, n_occ: int, eta: float,
+              h_mo: np.ndarray | None = None) -> dict:
+    """One-shot G0W0 from (eps, C): Eqs. (AO.to.MO) -> (Casida) -> (w.residue) ->
+    the diagonal of (Sigma.c.GW), and the linearised quasiparticle equation
+      eps^QP_p = eps_p + Z_p [Sigma_x,pp + Sigma_c,pp(eps_p) - v_pp],
+      Z_p = 1 / (1 - dSigma_c,pp/dw (eps_p)),  v = diag(eps) - h_MO - J   (reading R8).
+    With h derived from the input read as HF (reading R5) Sigma_x,pp - v_pp = 0."""
+    B = ri_mo_transform(L, C)
+    J = hartree(B, n_occ)
+    Sx = sigma_x(B, n_occ)
+    if h_mo is None:
+        h_mo = hf_core_mo(B, eps, n_occ)
+    A, Bc, D = casida_AB(B, eps, n_occ)
+    Omega, XpY, _ = rpa_eigensolve(casida_M(A, Bc, D), D)
+    _, w = gw_residues(B, XpY, n_occ)
+    sig, dsig = sigma_c_diag(w, eps, Omega, n_occ, eta)
+    v = eps - np.diag(h_mo) - np.diag(J)
+    Z = 1.0 / (1.0 - dsig)
+    eqp = eps + Z * (np.diag(Sx) + sig - v)
+    return {"Omega": Omega, "w": w, "sigma_c_diag": sig, "dsigma_c_diag": dsig, "Z": Z,
+            "eps_qp": eqp, "sigma_x_diag": np.diag(Sx).copy(), "v_diag": v}
 
 
 # ----------------------------------------------------------------------------
