@@ -264,7 +264,7 @@ def run_ours(args, wl):
     import torch
 
     world, rank, local, dist = dist_setup()
-    from paper_2210_17093_gb300 import FLAG_EIG_TC, FLAG_TC_AB, Context
+    from paper_2210_17093_gb300 import FLAG_EIG_TC, FLAG_QSMP2, FLAG_TC_AB, Context
 
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
@@ -406,6 +406,52 @@ def run_ours(args, wl):
                              "peak_tflops": peaks["bf16_tflops"], "peak_kind": peaks["kind"] + " bf16 burst"}
         return out
 
+    def qsmp2_variant() -> dict:
+        """qsMP2 (MOLGW_FLAG_QSMP2) iterations on the same molecule: float64, no RPA."""
+        with Context(precision="fp64", device=local, eta=sy.ETA, stream=st, flags=FLAG_QSMP2) as q:
+            q.set_ri(0, nb, na, L_d)
+            q.set_orbitals(0, no, eps_d, C_d)
+            q.autotune()
+            for _ in range(args.warmup):
+                q.qs_step(0)
+            q.sync()
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            barrier(dist)
+            torch.cuda.synchronize()
+            q0.record(st)
+            for _ in range(args.steps):
+                q.qs_step(0)
+            q1.record(st)
+            torch.cuda.synchronize()
+            t_q = max_over_ranks(dist, q0.elapsed_time(q1) / 1e3) / args.steps
+            q.set_timing(["gemm_f64", "sigma", "misc"])
+            q.kernel_stats(reset=True)
+            q.qs_step(0)
+            qbreak = q.kernel_stats(reset=True)
+        # useful float64 flops: (p m|i a) and the exchange partner per summed orbital m,
+        # the contraction S += [g (2A - X)] A^T, plus (a), Sigma_x and (f)
+        f_sig = 2.0 * (2.0 * nb * nb * na * n) + 2.0 * nb ** 3 * n
+        f_all = f_sig + flops["ri_mo_transform"] + flops["sigma_x"] + flops["qs_update"]
+        sig_ms = qbreak.get("sigma", (0, 0.0))[1]
+        out = {"method": "qsMP2: Eqs. (Sigma.c.MP2), (Sigma.c.qsMP2.real), float64; (a), residues, (f)",
+               "ms_per_step": t_q * 1e3, "tflops": f_all / t_q / 1e12,
+               "speedup_vs_qsgw_fp64": (t_max / args.steps) / t_q,
+               "stages_ms": {k: round(v[1], 3) for k, v in qbreak.items() if v[0]},
+               "roofline": {"kernel": "sigma class (gemm_f64 residues and contraction, k_apply_g_mp2)",
+                            "bound": "alu", "achieved": (f_sig / (sig_ms / 1e3) / 1e12) if sig_ms > 0 else None,
+                            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": (f_sig / (sig_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS) if sig_ms > 0 else None}}
+        if world == 1 and not args.no_cpu_baseline:
+            from oracle import qsgw
+            mo = sy.molecule(nb, no, na, molecule_seed(wl, rank))
+            t0 = time.perf_counter()
+            qsgw.qsmp2_pass(mo["L"], mo["eps"], mo["C"], no, sy.ETA)
+            out["cpu_baseline"] = {"value": time.perf_counter() - t0, "unit": "s", "cores": os.cpu_count(),
+                                   "kind": "oracle", "sample": "1 oracle qsMP2 iteration of the same molecule"}
+        return out
+
+    qsmp2 = None if args.no_mp2 else qsmp2_variant()
     mixed = mixed_eig = fp64_eig = None
     if not args.no_mixed:
         ab = FLAG_TC_AB if args.mixed == "bf16x10" else 0
@@ -450,6 +496,7 @@ def run_ours(args, wl):
         "mixed": mixed,
         "mixed_eig_tc": mixed_eig,
         "fp64_eig_tc": fp64_eig,
+        "qsmp2": qsmp2,
         "e2e": {"value": t_e2e, "unit": "s",
                 "h2d_bytes_per_step": int((na * nb * nb + nb + nb * nb) * 8),
                 "d2h_bytes_per_step": int((nb + nb * nb) * 8)},
@@ -594,6 +641,7 @@ def main():
     ap.add_argument("--mixed", choices=["bf16x3", "tf32x3", "bf16x6", "bf16x10"], default="bf16x10",
                     help="precision of the split-precision path reported under 'mixed'")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-mp2", action="store_true", help="skip the qsMP2 line item")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

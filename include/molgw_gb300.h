@@ -88,11 +88,20 @@ enum molgw_flags {
                                     buffers and the set of molecules stay the same                  */
   MOLGW_FLAG_USE_STREAM = 1u << 3, /* run on opts.stream even when it is NULL (the legacy default stream) */
   MOLGW_FLAG_TC_AB = 1u << 4,      /* with a split precision: stages (a) and (b) on the tensor cores too */
-  MOLGW_FLAG_EIG_TC = 1u << 5      /* the trailing SYR2K update of the tridiagonalisation on the
+  MOLGW_FLAG_EIG_TC = 1u << 5,     /* the trailing SYR2K update of the tridiagonalisation on the
                                       tensor cores: 7 fixed-point BF16 digits per value (56 bits,
                                       values within 4x of their group maximum exact), exact sums,
                                       one float64 rounding -- float64 accuracy in the normwise
                                       sense, not float64 arithmetic; any precision            */
+  MOLGW_FLAG_QSMP2 = 1u << 6       /* qsMP2 instead of qsGW: Sigma_c is the second-order self-energy
+                                      of Eq. (Sigma.c.MP2), made static and Hermitian by
+                                      Eq. (Sigma.c.qsMP2.real).  Its second-order exchange factor
+                                      is (p a|i n) for an occupied summed orbital p (the
+                                      antisymmetrised second-order expansion; the printed (p i|a n)
+                                      holds for an empty p).  No RPA: sigma and qs_step run (a),
+                                      the MP2 residues and (f); rpa, rpa_matrix and the RPA items
+                                      return MOLGW_E_STATE.  MOLGW_PREC_FP64 only (else
+                                      MOLGW_E_ARG at create)                                   */
 };
 
 typedef struct {
@@ -138,15 +147,32 @@ int molgw_b200_rpa(molgw_ctx ctx, int mol, double* omega, double* xpy);
 
 /* Stages (a)-(e), reusing (a)-(c) when still valid for the current orbitals.
  * sigma_x[n_basis][n_basis] and sigma_c[n_basis][n_basis] (the Hermitised qsGW
- * correlation matrix) are in the basis of the current MOs; either may be NULL.
+ * correlation matrix, or the qsMP2 one with MOLGW_FLAG_QSMP2) are in the basis
+ * of the current MOs; either may be NULL.
  * mol = -1: every ready molecule, outputs must be NULL. */
 int molgw_b200_sigma(molgw_ctx ctx, int mol, double* sigma_x, double* sigma_c);
 
-/* One qsGW iteration: stages (a)-(f).  The updated energies and orbitals become
+/* One qsGW (with MOLGW_FLAG_QSMP2: qsMP2) iteration: stages (a)-(f).  The updated energies and orbitals become
  * the current ones; eps_out[n_basis] and C_out[n_basis][n_basis] receive them
  * (either may be NULL).  Occupations follow the aufbau order of eps'.
  * mol = -1: every ready molecule, outputs must be NULL. */
 int molgw_b200_qs_step(molgw_ctx ctx, int mol, double* eps_out, double* C_out);
+
+/* One-shot G0W0 (Sec. II.C: the conventional method keeps only the diagonal
+ * m = n of Eq. (Sigma.c.GW)) from the current orbitals, which stay current:
+ * stages (a)-(d) (reusing (a)-(c) when valid; the residues w in float64 at every
+ * precision), then for every p
+ *   Sigma_c,pp(eps_p) = sum_{m,s} (w^s_pm)^2 Re 1/(eps_p - eps_m +/- Omega_s -/+ i eta),
+ *   Z_p = 1 / (1 - dSigma_c,pp/domega (eps_p)),
+ *   eps^QP_p = eps_p + Z_p [Sigma_x,pp + Sigma_c,pp(eps_p) - v_pp],
+ * v = diag(eps) - h_MO - J the potential of the input mean field (0 net with
+ * Sigma_x for an input read as HF).  The quasiparticle equation is solved to
+ * first order around eps_p (the paper does not name the solver).  Outputs
+ * eps_qp[n_basis], z[n_basis], sigma_c_diag[n_basis] may each be NULL; mol = -1
+ * runs every ready molecule (outputs NULL; fetch MOLGW_ITEM_EPS_QP etc.).
+ * MOLGW_E_STATE with MOLGW_FLAG_QSMP2.  MOLGW_E_NOMEM if 2 n_basis x (blocks of m)
+ * exceeds the 16 M-double split-K scratch. */
+int molgw_b200_g0w0(molgw_ctx ctx, int mol, double* eps_qp, double* z, double* sigma_c_diag);
 
 /* Synchronise the context stream and return the latched device status (then
  * cleared). */
@@ -163,7 +189,10 @@ enum molgw_item {
   MOLGW_ITEM_J = 5,        /* Hartree J_pq, n_basis^2                                 */
   MOLGW_ITEM_H_MO = 6,     /* one-body h in the basis of the current MOs, n_basis^2    */
   MOLGW_ITEM_EPS = 7,      /* current eps, n_basis                                    */
-  MOLGW_ITEM_C = 8         /* current C, n_basis^2                                    */
+  MOLGW_ITEM_C = 8,        /* current C, n_basis^2                                    */
+  MOLGW_ITEM_EPS_QP = 9,   /* last molgw_b200_g0w0: eps^QP_p, n_basis                  */
+  MOLGW_ITEM_Z = 10,       /* last molgw_b200_g0w0: Z_p, n_basis                       */
+  MOLGW_ITEM_SIGMA_C_DIAG = 11  /* last molgw_b200_g0w0: Re Sigma_c,pp(eps_p), n_basis  */
 };
 int molgw_b200_fetch(molgw_ctx ctx, int mol, int item, double* out, size_t count);
 

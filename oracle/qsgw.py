@@ -26,11 +26,11 @@ the design notes with its justification):
   R5  H0 = h + J with h_MO = diag(eps0) - J0 - Sigma_x0 (input read as an HF
       solution) unless h is supplied; h_MO follows the orbital rotation.
   R6  Aufbau occupations of the sorted updated energies; no mixing.
-  R7  Second-order exchange of Eq. (Sigma.c.MP2) for an occupied summed
+  R11 Second-order exchange of Eq. (Sigma.c.MP2) for an occupied summed
       orbital p (the 2h1p part): the factor is (p a|i n), the one the
       antisymmetrised second-order expansion gives; the printed (p i|a n) is that
       expansion's factor only for an empty p (the 2p1h part), which is kept.
-  R8  G0W0 (the diagonal m = n of Eq. (Sigma.c.GW)): the quasiparticle
+  R12 G0W0 (the diagonal m = n of Eq. (Sigma.c.GW)): the quasiparticle
       equation is solved to first order around eps_p (renormalisation factor Z_p),
       starting from the input mean field whose potential is v = diag(eps) - h - J.
 """
@@ -198,7 +198,7 @@ def sigma_c_at(w: np.ndarray, eps: np.ndarray, Omega: np.ndarray, n_occ: int,
 
 
 # ----------------------------------------------------------------------------
-# G0W0: the diagonal of Eq. (Sigma.c.GW) at eps_p, linearised (reading R8)
+# G0W0: the diagonal of Eq. (Sigma.c.GW) at eps_p, linearised (reading R12)
 # ----------------------------------------------------------------------------
 def g_real_derivative(x, eta: float):
     """d/dx of x / (x^2 + eta^2) = (eta^2 - x^2) / (x^2 + eta^2)^2."""
@@ -229,7 +229,7 @@ def g0w0_pass(L: np.ndarray, eps: np.ndarray, C: np.ndarray, n_occ: int, eta: fl
     """One-shot G0W0 from (eps, C): Eqs. (AO.to.MO) -> (Casida) -> (w.residue) ->
     the diagonal of (Sigma.c.GW), and the linearised quasiparticle equation
       eps^QP_p = eps_p + Z_p [Sigma_x,pp + Sigma_c,pp(eps_p) - v_pp],
-      Z_p = 1 / (1 - dSigma_c,pp/dw (eps_p)),  v = diag(eps) - h_MO - J   (reading R8).
+      Z_p = 1 / (1 - dSigma_c,pp/dw (eps_p)),  v = diag(eps) - h_MO - J   (reading R12).
     With h derived from the input read as HF (reading R5) Sigma_x,pp - v_pp = 0."""
     B = ri_mo_transform(L, C)
     J = hartree(B, n_occ)
@@ -256,7 +256,7 @@ def mp2_factors(B: np.ndarray, n_occ: int, p: int):
     Returns (Ap, Xp), both [n, t] over all orbitals n and transitions t = (i, a):
       Ap[n, t] = (n p|i a) = sum_P B^P_np B^P_ia           (direct factor),
       Xp[n, t] = (p a|i n) for occupied p, (p i|a n) for empty p  (exchange
-      partner, reading R7), each = sum_P B^P_.. B^P_.. (Eq. MO.4.ERI).
+      partner, reading R11), each = sum_P B^P_.. B^P_.. (Eq. MO.4.ERI).
     Each factor is one matrix product over P.
     """
     na, nb = B.shape[0], B.shape[1]

@@ -125,6 +125,7 @@ int read_status(molgw_ctx c) {
 bool use_tc(molgw_ctx c) { return c->opts.precision != MOLGW_PREC_FP64; }
 bool use_fx(molgw_ctx c) { return c->opts.precision == MOLGW_PREC_BF16X10; }
 bool use_tc_ab(molgw_ctx c) { return use_tc(c) && (c->opts.flags & MOLGW_FLAG_TC_AB); }
+bool use_mp2(molgw_ctx c) { return (c->opts.flags & MOLGW_FLAG_QSMP2) != 0; }
 int tc_prec(molgw_ctx c) {
   if (c->opts.precision == MOLGW_PREC_TF32X3) return TC_TF32X3;
   if (c->opts.precision == MOLGW_PREC_BF16X6) return TC_BF16X6;
@@ -249,7 +250,7 @@ int ensure_scratch(molgw_ctx c, Lane& l, int nb, int na, long long nov) {
   Scratch& s = l.scr;
   const size_t want_w = std::max<size_t>((size_t)nb * nov,
                                          std::min<size_t>((size_t)nb * nb * nov, (size_t)48 << 20));
-  if (!use_tc(c)) ensure_packed(c, l, nb, na, nov);
+  if (!use_tc(c) && !use_mp2(c)) ensure_packed(c, l, nb, na, nov);
   if (nb <= s.nb_cap && na <= s.na_cap && want_w <= s.wblk_cap) return MOLGW_OK;
   if (l.ex.capturing) return MOLGW_E_STATE;
   cudaStreamSynchronize(l.st);
@@ -305,8 +306,9 @@ int ensure_tco(molgw_ctx c, Lane& l, int nb, int na, long long nov) {
 int lane_fit(molgw_ctx c, Lane& l, const MolBuf& m) {
   const bool full = (c->opts.flags & MOLGW_FLAG_FULL_XPY) != 0;
   int r = ensure_scratch(c, l, m.nb, m.na, m.nov);
-  if (!r) r = ensure_eig(c, l, (int)std::max<long long>(m.nov, m.nb),
-                         std::max<int>(std::max(m.na, m.nb), full ? (int)m.nov : 0));
+  if (!r && use_mp2(c)) r = ensure_eig(c, l, m.nb, m.nb);   // qs_update only
+  else if (!r) r = ensure_eig(c, l, (int)std::max<long long>(m.nov, m.nb),
+                              std::max<int>(std::max(m.na, m.nb), full ? (int)m.nov : 0));
   if (!r) r = ensure_eigfx(c, l);
   if (!r) r = ensure_tco(c, l, m.nb, m.na, m.nov);
   return r;
@@ -317,6 +319,8 @@ int lane_fit(molgw_ctx c, Lane& l, const MolBuf& m) {
 int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
   MolBuf& m = c->mols[mol];
   if (!m.have_ri || !m.have_orb) return MOLGW_E_STATE;
+  const bool mp2 = use_mp2(c);
+  if (mp2 && (upto < 'e' || upto == 'g')) return MOLGW_E_STATE;   // qsMP2 has no RPA stages
   const bool full = (c->opts.flags & MOLGW_FLAG_FULL_XPY) != 0;
   int r = lane_fit(c, l, m);
   if (r) return r;
@@ -362,7 +366,7 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
     m.rpa_valid = false;
     return launch_status();
   }
-  if (!m.rpa_valid) {
+  if (!m.rpa_valid && !mp2) {
     if (tc_ab && use_fx(c)) {
       r = stage_rpa_build_fx(ex, m, l.tco_base);
       if (r) return r;
@@ -375,12 +379,25 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
     stage_rpa_eigensolve(ex, m, l.eig, l.scr, full);
     m.rpa_valid = m.have_rpa = true;
   }
+  if (upto == 'g') {
+    // one-shot G0W0 from the current orbitals; they stay current
+    if (!m.jx_valid) {
+      stage_j_sigx(ex, m, l.scr);
+      m.jx_valid = m.have_jx = true;
+    }
+    r = stage_g0w0(ex, m, l.scr, c->opts.eta);
+    if (r) return r;
+    m.have_g0w0 = true;
+    return launch_status();
+  }
   if (upto >= 'e' && !m.sigma_valid) {
     if (!m.jx_valid) {
       stage_j_sigx(ex, m, l.scr);
       m.jx_valid = m.have_jx = true;
     }
-    if (use_fx(c)) {
+    if (mp2) {
+      stage_sigma_mp2(ex, m, l.scr, c->opts.eta);
+    } else if (use_fx(c)) {
       r = stage_sigma_fx(ex, m, l.fxo, l.scr, c->opts.eta);
       if (r) return r;
     } else if (tc) {
@@ -407,8 +424,9 @@ bool steady(const MolBuf& m) {
 }
 
 // Relative cost of one pass: the n_ov^3 eigensolve and the residue contraction.
-double pass_cost(const MolBuf& m) {
+double pass_cost(const MolBuf& m, bool mp2) {
   const double n = (double)m.nov;
+  if (mp2) return 2.0 * 2.0 * m.nb * (double)m.nb * n * m.na + 2.0 * m.nb * (double)m.nb * m.nb * n;
   return n * n * n + 2.0 * m.nb * (double)m.nb * n * m.na;
 }
 
@@ -427,7 +445,9 @@ Plan plan_batch(molgw_ctx c, const std::vector<int>& mols, int lanes = 0) {
   want = std::max(1, std::min(std::min(want, kMaxLanes), (int)mols.size()));
   std::vector<int> order(mols);
   std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int b) { return pass_cost(c->mols[a]) > pass_cost(c->mols[b]); });
+                   [&](int a, int b) {
+                     return pass_cost(c->mols[a], use_mp2(c)) > pass_cost(c->mols[b], use_mp2(c));
+                   });
   Plan p;
   p.lane_mols.resize(want);
   std::vector<double> load(want, 0.0);
@@ -436,7 +456,7 @@ Plan plan_batch(molgw_ctx c, const std::vector<int>& mols, int lanes = 0) {
     for (int j = 1; j < want; ++j)
       if (load[j] < load[best]) best = j;
     p.lane_mols[best].push_back(k);
-    load[best] += pass_cost(c->mols[k]);
+    load[best] += pass_cost(c->mols[k], use_mp2(c));
   }
   return p;
 }
@@ -599,6 +619,7 @@ int molgw_b200_create(const molgw_opts* o, molgw_ctx* out) {
   if (!o || o->struct_size != (int32_t)sizeof(molgw_opts)) return MOLGW_E_ARG;
   if (o->precision < MOLGW_PREC_FP64 || o->precision > MOLGW_PREC_BF16X10) return MOLGW_E_ARG;
   if (o->max_mols < 1 || !(o->eta > 0.0) || o->lanes < 0) return MOLGW_E_ARG;
+  if ((o->flags & MOLGW_FLAG_QSMP2) && o->precision != MOLGW_PREC_FP64) return MOLGW_E_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) { cudaGetLastError(); return MOLGW_E_CUDA; }
   if (o->device < 0 || o->device >= ndev) return MOLGW_E_ARG;
@@ -644,7 +665,7 @@ int molgw_b200_set_ri(molgw_ctx c, int mol, int n_basis, int n_aux, const double
   const size_t nl = (size_t)n_aux * n_basis * n_basis;
   m.have_ri = m.have_orb = false;
   m.b_valid = m.jx_valid = m.rpa_valid = m.sigma_valid = false;
-  m.have_b = m.have_rpa = m.have_jx = m.have_sigma = false;
+  m.have_b = m.have_rpa = m.have_jx = m.have_sigma = m.have_g0w0 = false;
   m.h_ready = false;
   if (m.ri_allocs.empty() || m.nb != n_basis || m.na != n_aux) {
     cudaStreamSynchronize(c->st);
@@ -705,13 +726,18 @@ int molgw_b200_set_orbitals(molgw_ctx c, int mol, int n_occ, const double* eps, 
     m.J = dalloc(m.orb_allocs, nn, &err);
     m.sigx = dalloc(m.orb_allocs, nn, &err);
     m.sigc = dalloc(m.orb_allocs, nn, &err);
+    m.g0w0 = dalloc(m.orb_allocs, 3 * (size_t)nb, &err);
     m.D = dalloc(m.orb_allocs, nov, &err);
     m.Om = dalloc(m.orb_allocs, nov, &err);
-    m.Xv = dalloc(m.orb_allocs, (size_t)nov * na, &err);
-    m.R = dalloc(m.orb_allocs, (size_t)nov * na, &err);
-    m.M = dalloc(m.orb_allocs, (size_t)nov * nov, &err);
-    m.ZT = dalloc(m.orb_allocs, (size_t)nov * nov, &err);
-    m.XpY = full ? dalloc(m.orb_allocs, (size_t)nov * nov, &err) : nullptr;
+    m.R = dalloc(m.orb_allocs, (size_t)nov * na, &err);     // qsMP2: B_ia
+    if (use_mp2(c)) {
+      m.Xv = m.M = m.ZT = m.XpY = nullptr;                   // no RPA
+    } else {
+      m.Xv = dalloc(m.orb_allocs, (size_t)nov * na, &err);
+      m.M = dalloc(m.orb_allocs, (size_t)nov * nov, &err);
+      m.ZT = dalloc(m.orb_allocs, (size_t)nov * nov, &err);
+      m.XpY = full ? dalloc(m.orb_allocs, (size_t)nov * nov, &err) : nullptr;
+    }
     if (err) { free_all(m.orb_allocs); m.eps = nullptr; m.alloc_no = 0; return err; }
     m.alloc_no = n_occ;
   }
@@ -725,7 +751,7 @@ int molgw_b200_set_orbitals(molgw_ctx c, int mol, int n_occ, const double* eps, 
   check_finite(ex, m.C, (long long)nb * nb);
   m.have_orb = true;
   m.b_valid = m.jx_valid = m.rpa_valid = m.sigma_valid = false;
-  m.have_b = m.have_rpa = m.have_jx = m.have_sigma = false;
+  m.have_b = m.have_rpa = m.have_jx = m.have_sigma = m.have_g0w0 = false;
   m.h_ready = false;
   if (h_core) {
     r = ensure_scratch(c, c->lanes[0], nb, na, nov);
@@ -779,6 +805,26 @@ int molgw_b200_sigma(molgw_ctx c, int mol, double* sigma_x, double* sigma_c) {
   return sync ? read_status(c) : MOLGW_OK;
 }
 
+int molgw_b200_g0w0(molgw_ctx c, int mol, double* eps_qp, double* z, double* sigma_c_diag) {
+  if (!c) return MOLGW_E_ARG;
+  DeviceGuard g(c->device);
+  if (mol == -1) {
+    if (eps_qp || z || sigma_c_diag) return MOLGW_E_ARG;
+    return run_mols(c, -1, 'g');
+  }
+  if (!mol_ok(c, mol)) return MOLGW_E_ARG;
+  MolBuf& m = c->mols[mol];
+  if (!ready(m)) return MOLGW_E_STATE;
+  int r = run_mols(c, mol, 'g');
+  if (r) return r;
+  bool sync = false;
+  if (eps_qp) r = copy_out(c, eps_qp, m.g0w0, m.nb, &sync);
+  if (!r && z) r = copy_out(c, z, m.g0w0 + m.nb, m.nb, &sync);
+  if (!r && sigma_c_diag) r = copy_out(c, sigma_c_diag, m.g0w0 + 2 * m.nb, m.nb, &sync);
+  if (r) return r;
+  return sync ? read_status(c) : MOLGW_OK;
+}
+
 int molgw_b200_qs_step(molgw_ctx c, int mol, double* eps_out, double* C_out) {
   if (!c) return MOLGW_E_ARG;
   DeviceGuard g(c->device);
@@ -822,6 +868,9 @@ int molgw_b200_fetch(molgw_ctx c, int mol, int item, double* out, size_t count) 
     case MOLGW_ITEM_H_MO: src = m.hmo; n = nn; avail = m.h_ready; break;
     case MOLGW_ITEM_EPS: src = m.eps; n = m.nb; avail = m.have_orb; break;
     case MOLGW_ITEM_C: src = m.C; n = nn; avail = m.have_orb; break;
+    case MOLGW_ITEM_EPS_QP: src = m.g0w0; n = m.nb; avail = m.have_g0w0; break;
+    case MOLGW_ITEM_Z: src = m.g0w0 + m.nb; n = m.nb; avail = m.have_g0w0; break;
+    case MOLGW_ITEM_SIGMA_C_DIAG: src = m.g0w0 + 2 * m.nb; n = m.nb; avail = m.have_g0w0; break;
     default: return MOLGW_E_ARG;
   }
   if (!avail) return MOLGW_E_STATE;

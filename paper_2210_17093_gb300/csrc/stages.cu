@@ -160,6 +160,95 @@ __global__ void k_gather_w_apply_g(const double* Wpk, const double* eps, const d
   }
 }
 
+// qsMP2: Bia[P][t] = B^P_ia and D_t = eps_a - eps_i for t = i*nv + (a - no).
+__global__ void k_mp2_bia(const double* B, const double* eps, int nb, int no, int na, double* Bia,
+                          double* D) {
+  const int nv = nb - no;
+  const long long nov = (long long)no * nv;
+  const long long nn = (long long)nb * nb;
+  const long long total = nov * na;
+  for (long long idx = gtid(); idx < total; idx += gstride()) {
+    const int P = (int)(idx / nov);
+    const long long t = idx % nov;
+    const int i = (int)(t / nv), a = no + (int)(t % nv);
+    Bia[idx] = B[P * nn + (long long)i * nb + a];
+    if (P == 0) D[t] = eps[a] - eps[i];
+  }
+}
+
+// qsMP2, Eq. (Sigma.c.MP2) with the frequency on row p: Pb (holding the exchange
+// partner X_m[p][t] on entry) <- g(eps_p - eps_m +/- D_t) (2 A_m[p][t] - X_m[p][t]),
+// A_m[p][t] = (p m|i a) in Wb; + D_t for occupied m (2h1p), - D_t for empty m (2p1h).
+__global__ void k_apply_g_mp2(const double* Wb, const double* eps, const double* D, int nb, int no, int m0,
+                              int mb, int nov, double eta, double* Pb) {
+  const long long K = (long long)mb * nov;
+  const long long total = (long long)nb * K;
+  const double eta2 = eta * eta;
+  for (long long idx = gtid(); idx < total; idx += gstride()) {
+    const int p = (int)(idx / K);
+    const long long k = idx % K;
+    const int mm = (int)(k / nov), t = (int)(k % nov);
+    const int m = m0 + mm;
+    const double x = (m < no) ? (eps[p] - eps[m]) + D[t] : (eps[p] - eps[m]) - D[t];
+    Pb[idx] = (2.0 * Wb[idx] - Pb[idx]) * (x / (x * x + eta2));
+  }
+}
+
+// G0W0, the diagonal of Eq. (Sigma.c.GW): for row p of one block of m (one CTA per
+// p), sum over (m, s) of (w^s_pm)^2 g(x) and (w^s_pm)^2 g'(x), x = eps_p - eps_m +/- Omega_s,
+// g' = (eta^2 - x^2) / (x^2 + eta^2)^2.  Fixed-order block reduction.
+__global__ void k_g0w0_block(const double* Wb, const double* eps, const double* Om, int nb, int no, int m0,
+                             int mb, int nov, double eta, double* part) {
+  const int p = blockIdx.x;
+  const long long K = (long long)mb * nov;
+  const double eta2 = eta * eta;
+  const double* w = Wb + (long long)p * K;
+  double a = 0.0, d = 0.0;
+  for (long long k = threadIdx.x; k < K; k += blockDim.x) {
+    const int mm = (int)(k / nov), s = (int)(k % nov);
+    const int m = m0 + mm;
+    const double x = (m < no) ? (eps[p] - eps[m]) + Om[s] : (eps[p] - eps[m]) - Om[s];
+    const double q = x * x + eta2;
+    const double w2 = w[k] * w[k];
+    a += w2 * (x / q);
+    d += w2 * ((eta2 - x * x) / (q * q));
+  }
+  __shared__ double sa[256], sd[256];
+  sa[threadIdx.x] = a;
+  sd[threadIdx.x] = d;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      sa[threadIdx.x] += sa[threadIdx.x + h];
+      sd[threadIdx.x] += sd[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[p] = sa[0];
+    part[nb + p] = sd[0];
+  }
+}
+
+// Linearised quasiparticle equation: Z_p = 1 / (1 - Sigma'_pp), v_pp = eps_p - h_pp - J_pp,
+// eps^QP_p = eps_p + Z_p (Sigma_x,pp + Sigma_c,pp - v_pp).  out = [eps^QP | Z | Sigma_c,pp].
+__global__ void k_g0w0_final(const double* part, int nblk, const double* eps, const double* hmo,
+                             const double* J, const double* sigx, int nb, double* out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nb) return;
+  double sg = 0.0, dg = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    sg += part[2LL * b * nb + p];
+    dg += part[2LL * b * nb + nb + p];
+  }
+  const long long pp = (long long)p * nb + p;
+  const double v = eps[p] - hmo[pp] - J[pp];
+  const double z = 1.0 / (1.0 - dg);
+  out[p] = eps[p] + z * (sigx[pp] + sg - v);
+  out[nb + p] = z;
+  out[2 * nb + p] = sg;
+}
+
 // out = 1/2 (S + S^T)
 __global__ void k_symmetrize(const double* S, int n, double* out) {
   const long long nn = (long long)n * n;
@@ -418,6 +507,102 @@ void stage_sigma(Exec& ex, MolBuf& m, Scratch& s, double eta) {
   }
   KScope ks(ex, MOLGW_K_MISC);
   k_symmetrize<<<grid_for(nn), 256, 0, ex.st>>>(s.S, nb, m.sigc);
+}
+
+// qsMP2 self-energy, Eqs. (Sigma.c.MP2) and (Sigma.c.qsMP2.real), float64.  Per
+// block of summed orbitals m: A_m[p][t] = (p m|i a) (one batched GEMM over the
+// block), the exchange partner X_m[p][t] = (m a|i p) for occupied m, (m i|a p) for
+// empty m (one GEMM per m, batched over i or a), then
+// S += [g (2 A - X)] A^T and Sigma_c = (S + S^T)/2.  Bia and D live in R and Om.
+void stage_sigma_mp2(Exec& ex, MolBuf& m, Scratch& s, double eta) {
+  const int nb = m.nb, na = m.na, no = m.no, nv = nb - no;
+  const int nov = (int)m.nov;
+  const long long nn = (long long)nb * nb;
+  {
+    KScope ks(ex, MOLGW_K_SIGMA);
+    k_mp2_bia<<<grid_for((long long)na * nov), 256, 0, ex.st>>>(m.B, m.eps, nb, no, na, m.R, m.Om);
+  }
+  const int mb = std::max(1, std::min(nb, (int)(s.wblk_cap / ((long long)nb * nov))));
+  for (int m0 = 0; m0 < nb; m0 += mb) {
+    const int cnt = std::min(mb, nb - m0);
+    const long long K = (long long)cnt * nov;
+    GemmF64 g;
+    g.M = nb; g.N = nov; g.K = na; g.batch = cnt;
+    g.A = m.B + (long long)m0 * nb; g.sa_m = 1; g.sa_k = nn; g.sa_b = nb;
+    g.B = m.R; g.sb_k = nov; g.sb_n = 1; g.sb_b = 0;
+    g.C = s.wblk; g.sc_m = K; g.sc_n = 1; g.sc_b = nov;
+    g.kclass = MOLGW_K_SIGMA;
+    gemm_f64(ex, g);
+    for (int mm = 0; mm < cnt; ++mm) {
+      const int mo = m0 + mm;
+      GemmF64 e;
+      e.M = nb; e.K = na;
+      e.sa_m = 1; e.sa_k = nn; e.sa_b = nb;
+      e.sb_k = nn; e.sb_n = 1; e.sb_b = 0;
+      e.C = s.pblk + (long long)mm * nov; e.sc_m = K;
+      e.kclass = MOLGW_K_SIGMA;
+      if (mo < no) {
+        // X[p][i*nv + a'] = sum_P B^P_ip B^P_{m, no+a'}: batch over i
+        e.N = nv; e.batch = no;
+        e.A = m.B;
+        e.B = m.B + (long long)mo * nb + no;
+        e.sc_n = 1; e.sc_b = nv;
+      } else {
+        // X[p][i*nv + a'] = sum_P B^P_{no+a', p} B^P_{m, i}: batch over a'
+        e.N = no; e.batch = nv;
+        e.A = m.B + (long long)no * nb;
+        e.B = m.B + (long long)mo * nb;
+        e.sc_n = nv; e.sc_b = 1;
+      }
+      gemm_f64(ex, e);
+    }
+    {
+      KScope ks(ex, MOLGW_K_SIGMA);
+      k_apply_g_mp2<<<grid_for(nb * K), 256, 0, ex.st>>>(s.wblk, m.eps, m.Om, nb, no, m0, cnt, nov, eta, s.pblk);
+    }
+    GemmF64 h;
+    h.M = nb; h.N = nb; h.K = (int)K;
+    h.A = s.pblk; h.sa_m = K; h.sa_k = 1;
+    h.B = s.wblk; h.sb_k = 1; h.sb_n = K;
+    h.C = s.S; h.sc_m = nb; h.sc_n = 1;
+    h.beta = (m0 == 0) ? 0.0 : 1.0;
+    h.ksplit = gemm_f64_pick_split(nb, nb, (int)K, 1, s.splitk_cap);
+    h.work = s.splitk;
+    h.kclass = MOLGW_K_SIGMA;
+    gemm_f64(ex, h);
+  }
+  KScope ks(ex, MOLGW_K_MISC);
+  k_symmetrize<<<grid_for(nn), 256, 0, ex.st>>>(s.S, nb, m.sigc);
+}
+
+// One-shot G0W0 from the current Omega, R (float64 residues at every precision):
+// w per block of m as in the float64 Sigma stage, the diagonal sums per block, then
+// the linearised quasiparticle energies into m.g0w0.  Needs 2 nb ceil(nb / mb)
+// doubles of split-K scratch.
+int stage_g0w0(Exec& ex, MolBuf& m, Scratch& s, double eta) {
+  const int nb = m.nb, na = m.na, no = m.no;
+  const int nov = (int)m.nov;
+  const long long nn = (long long)nb * nb;
+  const int mb = std::max(1, std::min(nb, (int)(s.wblk_cap / ((long long)nb * nov))));
+  const int nblk = ceil_div(nb, mb);
+  if ((size_t)2 * nb * nblk > s.splitk_cap) return MOLGW_E_NOMEM;
+  for (int b = 0; b < nblk; ++b) {
+    const int m0 = b * mb, cnt = std::min(mb, nb - m0);
+    const long long K = (long long)cnt * nov;
+    GemmF64 g;
+    g.M = nb; g.N = nov; g.K = na; g.batch = cnt;
+    g.A = m.B + (long long)m0 * nb; g.sa_m = 1; g.sa_k = nn; g.sa_b = nb;
+    g.B = m.R; g.sb_k = nov; g.sb_n = 1; g.sb_b = 0;
+    g.C = s.wblk; g.sc_m = K; g.sc_n = 1; g.sc_b = nov;
+    g.kclass = MOLGW_K_SIGMA;
+    gemm_f64(ex, g);
+    KScope ks(ex, MOLGW_K_SIGMA);
+    k_g0w0_block<<<nb, 256, 0, ex.st>>>(s.wblk, m.eps, m.Om, nb, no, m0, cnt, nov, eta,
+                                                  s.splitk + 2LL * b * nb);
+  }
+  KScope ks(ex, MOLGW_K_MISC);
+  k_g0w0_final<<<ceil_div(nb, 128), 128, 0, ex.st>>>(s.splitk, nblk, m.eps, m.hmo, m.J, m.sigx, nb, m.g0w0);
+  return MOLGW_OK;
 }
 
 void derive_h_from_hf(Exec& ex, MolBuf& m) {

@@ -26,6 +26,8 @@ struct MolBuf {
   double *Om = nullptr, *R = nullptr;          // n_ov, n_aux x n_ov
   double *XpY = nullptr;                       // n_ov x n_ov (FULL_XPY only)
   double *J = nullptr, *sigx = nullptr, *sigc = nullptr;  // nb x nb
+  double* g0w0 = nullptr;                      // G0W0: [eps_QP | Z | Sigma_c,pp(eps_p)], 3 nb
+  bool have_g0w0 = false;
   std::vector<void*> ri_allocs, orb_allocs;
 };
 
@@ -86,6 +88,8 @@ void stage_j_sigx(Exec& ex, MolBuf& m, Scratch& s);
 void stage_rpa_build(Exec& ex, MolBuf& m);
 void stage_rpa_eigensolve(Exec& ex, MolBuf& m, EigWork& w, Scratch& s, bool full_xpy);
 void stage_sigma(Exec& ex, MolBuf& m, Scratch& s, double eta);
+void stage_sigma_mp2(Exec& ex, MolBuf& m, Scratch& s, double eta);
+int stage_g0w0(Exec& ex, MolBuf& m, Scratch& s, double eta);
 void derive_h_from_hf(Exec& ex, MolBuf& m);
 void h_ao_to_mo(Exec& ex, MolBuf& m, const double* hao, Scratch& s);
 void stage_qs_update(Exec& ex, MolBuf& m, EigWork& w, Scratch& s);

@@ -22,8 +22,10 @@ FLAG_GRAPH = 4
 FLAG_USE_STREAM = 8
 FLAG_TC_AB = 16
 FLAG_EIG_TC = 32
+FLAG_QSMP2 = 64
 
-ITEM = {"B": 0, "Omega": 1, "R": 2, "sigma_x": 3, "sigma_c": 4, "J": 5, "h_mo": 6, "eps": 7, "C": 8}
+ITEM = {"B": 0, "Omega": 1, "R": 2, "sigma_x": 3, "sigma_c": 4, "J": 5, "h_mo": 6, "eps": 7, "C": 8,
+        "eps_qp": 9, "Z": 10, "sigma_c_diag": 11}
 KERNELS = ["gemm_f64", "tridiag_panel", "tridiag_syr2k", "bisect", "twisted", "backtransform",
            "sigma", "gemm_tc", "misc"]
 
@@ -36,7 +38,7 @@ EXPORTS = ["molgw_b200_create", "molgw_b200_set_ri", "molgw_b200_set_orbitals", 
            "molgw_b200_rpa_matrix", "molgw_b200_eigh", "molgw_b200_kernel_stats",
            "molgw_b200_launch_count", "molgw_b200_set_timing", "molgw_b200_destroy",
            "molgw_b200_status_string", "molgw_b200_eigh_noalloc", "molgw_b200_graph_replays",
-           "molgw_b200_tc_gemm", "molgw_b200_autotune", "molgw_b200_lanes"]
+           "molgw_b200_tc_gemm", "molgw_b200_autotune", "molgw_b200_lanes", "molgw_b200_g0w0"]
 NOALLOC_NMAX = 256
 
 
@@ -73,6 +75,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "molgw_b200_rpa": ([vp, ip, dp, dp], ip),
         "molgw_b200_sigma": ([vp, ip, dp, dp], ip),
         "molgw_b200_qs_step": ([vp, ip, dp, dp], ip),
+        "molgw_b200_g0w0": ([vp, ip, dp, dp, dp], ip),
         "molgw_b200_sync": ([vp], ip),
         "molgw_b200_fetch": ([vp, ip, ip, dp, sz], ip),
         "molgw_b200_rpa_matrix": ([vp, ip, dp], ip),
@@ -187,6 +190,11 @@ class Context:
         nb = self.sizes[mol][0] if mol in self.sizes else None
         _check(self._lib.molgw_b200_qs_step(self._hh(), mol, _ptr(eps_out, nb),
                                             _ptr(C_out, None if nb is None else nb * nb)), "qs_step")
+
+    def g0w0(self, mol: int, eps_qp=None, z=None, sigma_c_diag=None):
+        nb = self.sizes[mol][0] if mol in self.sizes else None
+        _check(self._lib.molgw_b200_g0w0(self._hh(), mol, _ptr(eps_qp, nb), _ptr(z, nb), _ptr(sigma_c_diag, nb)),
+               "g0w0")
 
     def sync(self):
         _check(self._lib.molgw_b200_sync(self._hh()), "sync")

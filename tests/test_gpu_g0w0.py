@@ -1,0 +1,84 @@
+"""One-shot G0W0 (molgw_b200_g0w0: the diagonal of Eq. Sigma.c.GW, linearised) against the oracle."""
+import numpy as np
+import pytest
+
+import synthetic as sy
+from helpers import lib_context, load_mol
+from oracle import qsgw
+
+pytestmark = pytest.mark.gpu
+ETA = sy.ETA
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x10"])
+@pytest.mark.parametrize("nb,no,na,seed", [(24, 5, 72, 0), (71, 13, 150, 2), (40, 1, 90, 7)])
+def test_g0w0_against_oracle(prec, nb, no, na, seed):
+    """(a)-(c) in float64 at both precisions and the residues in float64: float64 tolerances."""
+    m = sy.molecule(nb, no, na, seed)
+    r = qsgw.g0w0_pass(m["L"], m["eps"], m["C"], no, ETA)
+    with lib_context(precision=prec) as ctx:
+        load_mol(ctx, 0, m)
+        e, z, s = np.empty(nb), np.empty(nb), np.empty(nb)
+        ctx.g0w0(0, e, z, s)
+    assert np.max(np.abs(s - r["sigma_c_diag"])) <= 1e-10 * np.max(np.abs(r["sigma_c_diag"]))
+    assert np.max(np.abs(z - r["Z"])) < 1e-9
+    assert np.max(np.abs(e - r["eps_qp"])) < 1e-8
+
+
+def test_g0w0_with_explicit_h_core():
+    nb, no, na = 30, 6, 80
+    m = sy.molecule(nb, no, na, 8)
+    rng = np.random.default_rng(3)
+    h = rng.standard_normal((nb, nb))
+    h = 0.5 * (h + h.T)
+    B = qsgw.ri_mo_transform(m["L"], m["C"])
+    r = qsgw.g0w0_pass(m["L"], m["eps"], m["C"], no, ETA, h_mo=m["C"].T @ h @ m["C"])
+    with lib_context() as ctx:
+        load_mol(ctx, 0, m, h_core=h)
+        e = np.empty(nb)
+        ctx.g0w0(0, e)
+    assert np.max(np.abs(e - r["eps_qp"])) < 1e-8
+    assert B.shape[0] == na
+
+
+def test_g0w0_leaves_the_orbitals_current():
+    m = sy.molecule(40, 8, 96, 9)
+    out = []
+    for do_g0w0 in (False, True):
+        with lib_context() as ctx:
+            load_mol(ctx, 0, m)
+            if do_g0w0:
+                ctx.g0w0(0, np.empty(40))
+            e = np.empty(40)
+            ctx.qs_step(0, e)
+            out.append(e)
+    assert np.array_equal(out[0], out[1])
+
+
+def test_g0w0_batch_equals_solo():
+    mols = [sy.batch_molecule(s) for s in (110, 111, 112)]
+    solo = []
+    for m in mols:
+        with lib_context() as ctx:
+            load_mol(ctx, 0, m)
+            e = np.empty(m["n_basis"])
+            ctx.g0w0(0, e)
+            solo.append(e)
+    with lib_context(max_mols=3, lanes=3) as ctx:
+        for k, m in enumerate(mols):
+            load_mol(ctx, k, m)
+        ctx.g0w0(-1)
+        ctx.sync()
+        for k, m in enumerate(mols):
+            e = np.empty(m["n_basis"])
+            ctx.fetch(k, "eps_qp", e)
+            assert np.array_equal(e, solo[k])
+
+
+def test_g0w0_not_with_qsmp2():
+    from paper_2210_17093_gb300 import MolgwError
+    m = sy.molecule(24, 5, 72, 0)
+    with lib_context(flags=64) as ctx:
+        load_mol(ctx, 0, m)
+        with pytest.raises(MolgwError):
+            ctx.g0w0(0, np.empty(24))

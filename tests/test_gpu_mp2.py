@@ -1,0 +1,126 @@
+"""qsMP2 (MOLGW_FLAG_QSMP2, Eqs. Sigma.c.MP2 and Sigma.c.qsMP2.real) against the oracle.
+
+The float64 path is held to the float64 tolerances: Sigma entries to 1e-10 of
+their maximum (measured ~1e-14), quasiparticle energies to 1e-8 Ha.
+"""
+import numpy as np
+import pytest
+
+import synthetic as sy
+from helpers import lib_context, load_mol, rel_max
+from oracle import qsgw
+
+pytestmark = pytest.mark.gpu
+ETA = sy.ETA
+FLAG_QSMP2 = 64
+
+
+def occ_projector(C, no):
+    Co = C[:, :no]
+    return Co @ Co.T
+
+
+@pytest.mark.parametrize("nb,no,na,seed", [
+    (24, 5, 72, 0),      # the small workload: one tile
+    (71, 13, 150, 2),    # several tiles and ragged tails in every GEMM dimension
+    (37, 1, 60, 3),      # one occupied orbital: only opposite-spin pairs
+    (33, 32, 50, 4),     # one empty orbital
+])
+def test_qsmp2_pass_against_oracle(nb, no, na, seed):
+    m = sy.molecule(nb, no, na, seed)
+    r = qsgw.qsmp2_pass(m["L"], m["eps"], m["C"], no, ETA)
+    with lib_context(flags=FLAG_QSMP2) as ctx:
+        load_mol(ctx, 0, m)
+        sx = np.empty((nb, nb))
+        sc = np.empty((nb, nb))
+        ctx.sigma(0, sx, sc)
+        eps = np.empty(nb)
+        C = np.empty((nb, nb))
+        ctx.qs_step(0, eps, C)
+    assert rel_max(sx, r["sigma_x"]) < 1e-12
+    assert rel_max(sc, r["sigma_c"]) < 1e-10
+    assert np.max(np.abs(eps - r["eps_new"])) < 1e-8
+    assert np.max(np.abs(occ_projector(C, no) - occ_projector(r["C_new"], no))) < 1e-8
+
+
+def test_qsmp2_iterations_against_oracle():
+    nb, no, na = 40, 8, 96
+    m = sy.molecule(nb, no, na, 6)
+    ref = qsgw.qsmp2_iterations(m["L"], m["eps"], m["C"], no, ETA, 3)
+    with lib_context(flags=FLAG_QSMP2) as ctx:
+        load_mol(ctx, 0, m)
+        for r in ref:
+            eps = np.empty(nb)
+            ctx.qs_step(0, eps)
+            assert np.max(np.abs(eps - r["eps_new"])) < 1e-8
+
+
+def test_qsmp2_full_size_against_oracle():
+    """n_basis 200, n_occ 40, n_aux 600 (the float64 bench workload's shape): every
+    entry of Sigma_c and every quasiparticle energy."""
+    nb, no, na = 200, 40, 600
+    m = sy.molecule(nb, no, na, 1)
+    r = qsgw.qsmp2_pass(m["L"], m["eps"], m["C"], no, ETA)
+    with lib_context(flags=FLAG_QSMP2) as ctx:
+        load_mol(ctx, 0, m)
+        sc = np.empty((nb, nb))
+        ctx.sigma(0, None, sc)
+        eps = np.empty(nb)
+        ctx.qs_step(0, eps)
+    assert rel_max(sc, r["sigma_c"]) < 1e-10
+    assert np.max(np.abs(eps - r["eps_new"])) < 1e-8
+
+
+def test_qsmp2_batch_lanes_equal_solo():
+    mols = [sy.batch_molecule(s) for s in (100, 101, 102, 103)]
+    solo = []
+    for m in mols:
+        with lib_context(flags=FLAG_QSMP2) as ctx:
+            load_mol(ctx, 0, m)
+            e = np.empty(m["n_basis"])
+            ctx.qs_step(0, e)
+            solo.append(e)
+    with lib_context(flags=FLAG_QSMP2, max_mols=4, lanes=4) as ctx:
+        for k, m in enumerate(mols):
+            load_mol(ctx, k, m)
+        ctx.qs_step(-1)
+        ctx.sync()
+        for k, m in enumerate(mols):
+            e = np.empty(m["n_basis"])
+            ctx.fetch(k, "eps", e)
+            assert np.array_equal(e, solo[k])
+
+
+def test_qsmp2_graph_replay_equals_eager():
+    mols = [sy.batch_molecule(s) for s in (104, 105)]
+    out = {}
+    for flags in (FLAG_QSMP2, FLAG_QSMP2 | 4):
+        with lib_context(flags=flags, max_mols=2) as ctx:
+            for k, m in enumerate(mols):
+                load_mol(ctx, k, m)
+            for _ in range(3):
+                ctx.qs_step(-1)
+            ctx.sync()
+            out[flags] = []
+            for k, m in enumerate(mols):
+                e = np.empty(m["n_basis"])
+                ctx.fetch(k, "eps", e)
+                out[flags].append(e)
+    for a, b in zip(out[FLAG_QSMP2], out[FLAG_QSMP2 | 4]):
+        assert np.array_equal(a, b)
+
+
+def test_qsmp2_has_no_rpa_and_needs_float64():
+    from paper_2210_17093_gb300 import MolgwError
+    m = sy.molecule(24, 5, 72, 0)
+    with lib_context(flags=FLAG_QSMP2) as ctx:
+        load_mol(ctx, 0, m)
+        with pytest.raises(MolgwError):
+            ctx.rpa(0, np.empty(5 * 19))
+        with pytest.raises(MolgwError):
+            ctx.rpa_matrix(0, np.empty((5 * 19) ** 2))
+        ctx.qs_step(0)
+        with pytest.raises(MolgwError):
+            ctx.fetch(0, "Omega", np.empty(5 * 19))
+    with pytest.raises(MolgwError):
+        lib_context(precision="bf16x10", flags=FLAG_QSMP2)

@@ -1,4 +1,4 @@
-"""Pins of the G0W0 part of the oracle (the diagonal of Eq. Sigma.c.GW, reading R8)."""
+"""Pins of the G0W0 part of the oracle (the diagonal of Eq. Sigma.c.GW, reading R12)."""
 import math
 
 import numpy as np

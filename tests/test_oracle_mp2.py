@@ -4,7 +4,7 @@ The matrix form in ``oracle.qsgw`` (``mp2_factors``, ``sigma_mp2_at``,
 ``sigma_mp2_rows``, ``qsmp2_pass``) is checked against a closed form worked out by
 hand for two levels, against the antisymmetrised second-order expansion over
 explicit spin orbitals (``oracle.brute.sigma2_spin_orbital``), against the
-printed equation where reading R7 leaves it unchanged, and against invariances.
+printed equation where reading R11 leaves it unchanged, and against invariances.
 """
 import numpy as np
 import pytest
@@ -55,10 +55,10 @@ def test_spin_orbital_expansion(seed, nb, no, na):
         assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
 
 
-def test_printed_equation_where_reading_r7_keeps_it():
+def test_printed_equation_where_reading_r11_keeps_it():
     """Empty p (2p1h): the printed factors are the expansion's.  Occupied p (2h1p):
     the printed exchange factor (pi|an) differs from the expansion's (pa|in),
-    which is why reading R7 is needed."""
+    which is why reading R11 is needed."""
     m = sy.molecule(6, 2, 5, 8)
     g = brute.eri_mo(m["L"], m["C"])
     w = 0.21
