@@ -437,7 +437,7 @@ def run_ours(args, wl):
         out = {"method": "qsMP2: Eqs. (Sigma.c.MP2), (Sigma.c.qsMP2.real), float64; (a), residues, (f)",
                "ms_per_step": t_q * 1e3, "tflops": f_all / t_q / 1e12,
                "speedup_vs_qsgw_fp64": (t_max / args.steps) / t_q,
-               "stages_ms": {k: round(v[1], 3) for k, v in qbreak.items() if v[0]},
+               "stages_ms": {k: round(v[1], 3) for k, v in qbreak.items() if v[0] and v[1] > 0},
                "roofline": {"kernel": "sigma class (gemm_f64 residues and contraction, k_apply_g_mp2)",
                             "bound": "alu", "achieved": (f_sig / (sig_ms / 1e3) / 1e12) if sig_ms > 0 else None,
                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
