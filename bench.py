@@ -406,13 +406,15 @@ def run_ours(args, wl):
                              "peak_tflops": peaks["bf16_tflops"], "peak_kind": peaks["kind"] + " bf16 burst"}
         return out
 
-    def qsmp2_variant() -> dict:
-        """qsMP2 (MOLGW_FLAG_QSMP2) iterations on the same molecule: float64, no RPA."""
-        with Context(precision="fp64", device=local, eta=sy.ETA, stream=st, flags=FLAG_QSMP2) as q:
+    def qsmp2_variant(precision: str, flags: int, ref_eps=None) -> dict:
+        """qsMP2 (MOLGW_FLAG_QSMP2) iterations on the same molecule: no RPA."""
+        with Context(precision=precision, device=local, eta=sy.ETA, stream=st, flags=FLAG_QSMP2 | flags) as q:
             q.set_ri(0, nb, na, L_d)
             q.set_orbitals(0, no, eps_d, C_d)
             q.autotune()
-            for _ in range(args.warmup):
+            e1 = torch.empty(nb, dtype=torch.float64).pin_memory()
+            q.qs_step(0, e1)
+            for _ in range(max(0, args.warmup - 1)):
                 q.qs_step(0)
             q.sync()
             q0 = torch.cuda.Event(enable_timing=True)
@@ -425,33 +427,62 @@ def run_ours(args, wl):
             q1.record(st)
             torch.cuda.synchronize()
             t_q = max_over_ranks(dist, q0.elapsed_time(q1) / 1e3) / args.steps
-            q.set_timing(["gemm_f64", "sigma", "misc"])
+            q.set_timing(["gemm_f64", "sigma", "gemm_tc", "misc"])
             q.kernel_stats(reset=True)
             q.qs_step(0)
             qbreak = q.kernel_stats(reset=True)
-        # useful float64 flops: (p m|i a) and the exchange partner per summed orbital m,
-        # the contraction S += [g (2A - X)] A^T, plus (a), Sigma_x and (f)
+        # useful flops: (p m|i a) and the exchange partner per summed orbital m, the
+        # contraction S += [g (2A - X)] A^T, plus (a), Sigma_x and (f)
         f_sig = 2.0 * (2.0 * nb * nb * na * n) + 2.0 * nb ** 3 * n
         f_all = f_sig + flops["ri_mo_transform"] + flops["sigma_x"] + flops["qs_update"]
-        sig_ms = qbreak.get("sigma", (0, 0.0))[1]
-        out = {"method": "qsMP2: Eqs. (Sigma.c.MP2), (Sigma.c.qsMP2.real), float64; (a), residues, (f)",
-               "ms_per_step": t_q * 1e3, "tflops": f_all / t_q / 1e12,
+        out = {"precision": precision, "flags": FLAG_QSMP2 | flags,
+               "method": "qsMP2: Eqs. (Sigma.c.MP2), (Sigma.c.qsMP2.real); (a), residues, (f)",
+               "ms_per_step": t_q * 1e3, "tflops_useful": f_all / t_q / 1e12,
                "speedup_vs_qsgw_fp64": (t_max / args.steps) / t_q,
                "stages_ms": {k: round(v[1], 3) for k, v in qbreak.items() if v[0] and v[1] > 0},
-               "roofline": {"kernel": "sigma class (gemm_f64 residues and contraction, k_apply_g_mp2)",
-                            "bound": "alu", "achieved": (f_sig / (sig_ms / 1e3) / 1e12) if sig_ms > 0 else None,
-                            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": (f_sig / (sig_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS) if sig_ms > 0 else None}}
+               "eps_step1": e1.numpy().copy()}
+        if precision == "fp64":
+            sig_ms = qbreak.get("sigma", (0, 0.0))[1]
+            out["roofline"] = {"kernel": "sigma class (gemm_f64 residues and contraction, k_apply_g_mp2)",
+                               "bound": "alu", "achieved": (f_sig / (sig_ms / 1e3) / 1e12) if sig_ms > 0 else None,
+                               "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": (f_sig / (sig_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS) if sig_ms > 0 else None}
+        else:
+            tc_ms = qbreak.get("gemm_tc", (0, 0.0))[1]
+            peaks = measured_peaks()
+            pad = lambda k: -(-k // 64) * 64
+            ex_flops = 10 * 2 * (2 * nb * nb * n * pad(na) + nb * nb * nb * pad(n))
+            if flags & FLAG_TC_AB:
+                ex_flops += 10 * 2 * (2 * na * nb * nb * pad(nb))
+            out["tensor"] = {"kernels": "gemm_tc class: fx_gemm_kernel<4> (direct factor, exchange partner, "
+                                        "Sigma contraction" + (", (a)" if flags & FLAG_TC_AB else "") + ")",
+                             "executed_tflops": ex_flops / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None,
+                             "frac_of_bf16_peak": ex_flops / (tc_ms / 1e3) / 1e12 / peaks["bf16_tflops"]
+                             if tc_ms > 0 else None,
+                             "peak_tflops": peaks["bf16_tflops"], "peak_kind": peaks["kind"] + " bf16 burst"}
+        if ref_eps is not None:
+            err = float(np.max(np.abs(out["eps_step1"] - ref_eps)))
+            out["qp_error_vs_qsmp2_fp64_meV"] = err * 27211.386
+            out["qp_error_relative"] = err / float(np.max(np.abs(ref_eps)))
+            out["qp_max_abs_ha"] = float(np.max(np.abs(ref_eps)))
+        return out
+
+    def qsmp2_lines() -> dict:
+        q64 = qsmp2_variant("fp64", 0)
+        qfx = qsmp2_variant("bf16x10", FLAG_TC_AB, q64["eps_step1"])
+        qfx["speedup_vs_qsmp2_fp64"] = q64["ms_per_step"] / qfx["ms_per_step"]
+        q64.pop("eps_step1")
+        qfx.pop("eps_step1")
         if world == 1 and not args.no_cpu_baseline:
             from oracle import qsgw
             mo = sy.molecule(nb, no, na, molecule_seed(wl, rank))
             t0 = time.perf_counter()
             qsgw.qsmp2_pass(mo["L"], mo["eps"], mo["C"], no, sy.ETA)
-            out["cpu_baseline"] = {"value": time.perf_counter() - t0, "unit": "s", "cores": os.cpu_count(),
+            q64["cpu_baseline"] = {"value": time.perf_counter() - t0, "unit": "s", "cores": os.cpu_count(),
                                    "kind": "oracle", "sample": "1 oracle qsMP2 iteration of the same molecule"}
-        return out
+        return {"fp64": q64, "mixed": qfx}
 
-    qsmp2 = None if args.no_mp2 else qsmp2_variant()
+    qsmp2 = None if args.no_mp2 else qsmp2_lines()
     mixed = mixed_eig = fp64_eig = None
     if not args.no_mixed:
         ab = FLAG_TC_AB if args.mixed == "bf16x10" else 0

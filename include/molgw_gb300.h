@@ -100,8 +100,10 @@ enum molgw_flags {
                                       antisymmetrised second-order expansion; the printed (p i|a n)
                                       holds for an empty p).  No RPA: sigma and qs_step run (a),
                                       the MP2 residues and (f); rpa, rpa_matrix and the RPA items
-                                      return MOLGW_E_STATE.  MOLGW_PREC_FP64 only (else
-                                      MOLGW_E_ARG at create)                                   */
+                                      return MOLGW_E_STATE.  MOLGW_PREC_FP64, or MOLGW_PREC_BF16X10
+                                      (the three contractions on the fixed-point engine, the
+                                      denominators float64); other precisions MOLGW_E_ARG at
+                                      create                                                   */
 };
 
 typedef struct {

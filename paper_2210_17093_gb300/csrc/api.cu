@@ -283,7 +283,8 @@ int ensure_scratch(molgw_ctx c, Lane& l, int nb, int na, long long nov) {
 int ensure_tco(molgw_ctx c, Lane& l, int nb, int na, long long nov) {
   if (!use_tc(c)) return MOLGW_OK;
   const int prec = tc_prec(c);
-  const size_t want = use_fx(c) ? (std::max(fx_sigma_bytes(nb, na, nov, fx_mblock(nb, na, nov)),
+  const bool mp2 = use_mp2(c);
+  const size_t want = use_fx(c) ? (std::max(fx_sigma_bytes(nb, na, nov, fx_mblock(nb, na, nov, mp2), mp2),
                                             use_tc_ab(c) ? fx_ab_bytes(nb, na, nov) : (size_t)0) + 7) / 8
                                 : tc_orb_doubles(prec, nb, na, nov, tc_mblock(prec, nb, nov));
   if (want <= l.tco_cap) return MOLGW_OK;
@@ -329,7 +330,7 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
   const bool tc_ab = use_tc_ab(c);
   TcBufs& tb = l.tco;
   if (use_fx(c)) {
-    fx_bufs_carve(l.fxo, m.nb, m.na, m.nov, fx_mblock(m.nb, m.na, m.nov), l.tco_base);
+    fx_bufs_carve(l.fxo, m.nb, m.na, m.nov, fx_mblock(m.nb, m.na, m.nov, mp2), l.tco_base, mp2);
   } else if (tc) {
     const int prec = tc_prec(c);
     tc_bufs_carve(tb, prec, m.nb, m.na, m.nov, tc_mblock(prec, m.nb, m.nov), (double*)l.tco_base);
@@ -395,7 +396,10 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
       stage_j_sigx(ex, m, l.scr);
       m.jx_valid = m.have_jx = true;
     }
-    if (mp2) {
+    if (mp2 && use_fx(c)) {
+      r = stage_sigma_mp2_fx(ex, m, l.fxo, l.scr, c->opts.eta);
+      if (r) return r;
+    } else if (mp2) {
       stage_sigma_mp2(ex, m, l.scr, c->opts.eta);
     } else if (use_fx(c)) {
       r = stage_sigma_fx(ex, m, l.fxo, l.scr, c->opts.eta);
@@ -619,7 +623,8 @@ int molgw_b200_create(const molgw_opts* o, molgw_ctx* out) {
   if (!o || o->struct_size != (int32_t)sizeof(molgw_opts)) return MOLGW_E_ARG;
   if (o->precision < MOLGW_PREC_FP64 || o->precision > MOLGW_PREC_BF16X10) return MOLGW_E_ARG;
   if (o->max_mols < 1 || !(o->eta > 0.0) || o->lanes < 0) return MOLGW_E_ARG;
-  if ((o->flags & MOLGW_FLAG_QSMP2) && o->precision != MOLGW_PREC_FP64) return MOLGW_E_ARG;
+  if ((o->flags & MOLGW_FLAG_QSMP2) && o->precision != MOLGW_PREC_FP64 && o->precision != MOLGW_PREC_BF16X10)
+    return MOLGW_E_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) { cudaGetLastError(); return MOLGW_E_CUDA; }
   if (o->device < 0 || o->device >= ndev) return MOLGW_E_ARG;

@@ -509,6 +509,12 @@ void stage_sigma(Exec& ex, MolBuf& m, Scratch& s, double eta) {
   k_symmetrize<<<grid_for(nn), 256, 0, ex.st>>>(s.S, nb, m.sigc);
 }
 
+// qsMP2: B_ia into R ([P][t]) and D_t into Om, the "R" and "Omega" of the residue GEMM.
+void mp2_prepare(Exec& ex, MolBuf& m) {
+  KScope ks(ex, MOLGW_K_SIGMA);
+  k_mp2_bia<<<grid_for((long long)m.na * m.nov), 256, 0, ex.st>>>(m.B, m.eps, m.nb, m.no, m.na, m.R, m.Om);
+}
+
 // qsMP2 self-energy, Eqs. (Sigma.c.MP2) and (Sigma.c.qsMP2.real), float64.  Per
 // block of summed orbitals m: A_m[p][t] = (p m|i a) (one batched GEMM over the
 // block), the exchange partner X_m[p][t] = (m a|i p) for occupied m, (m i|a p) for
@@ -518,10 +524,7 @@ void stage_sigma_mp2(Exec& ex, MolBuf& m, Scratch& s, double eta) {
   const int nb = m.nb, na = m.na, no = m.no, nv = nb - no;
   const int nov = (int)m.nov;
   const long long nn = (long long)nb * nb;
-  {
-    KScope ks(ex, MOLGW_K_SIGMA);
-    k_mp2_bia<<<grid_for((long long)na * nov), 256, 0, ex.st>>>(m.B, m.eps, nb, no, na, m.R, m.Om);
-  }
+  mp2_prepare(ex, m);
   const int mb = std::max(1, std::min(nb, (int)(s.wblk_cap / ((long long)nb * nov))));
   for (int m0 = 0; m0 < nb; m0 += mb) {
     const int cnt = std::min(mb, nb - m0);

@@ -58,12 +58,14 @@ struct FxBufs {
   FxMat Bt, Rt;                // rows (m, p) and s, K = P
   double* wbuf = nullptr;      // w of a block: [K group][s][(m, p)]
   void* wp_base = nullptr;     // arena of the sliced w and g*w of a block
+  double* xbuf = nullptr;      // qsMP2: the exchange partners of a block, per K group
 };
-int fx_mblock(int nb, int na, long long nov);
+// m values per block; mp2 adds the exchange partners' float64 partials to each block
+int fx_mblock(int nb, int na, long long nov, bool mp2 = false);
 // lane arena of stages (a), (b) on the fixed-point engine: C, T = L C and Xv as digits
 size_t fx_ab_bytes(int nb, int na, long long nov);
-size_t fx_sigma_bytes(int nb, int na, long long nov, int mb);
-void fx_bufs_carve(FxBufs& f, int nb, int na, long long nov, int mb, void* base);
+size_t fx_sigma_bytes(int nb, int na, long long nov, int mb, bool mp2 = false);
+void fx_bufs_carve(FxBufs& f, int nb, int na, long long nov, int mb, void* base, bool mp2 = false);
 
 struct Scratch {
   double* rho = nullptr;        // n_aux
@@ -103,6 +105,8 @@ int stage_ri_mo_transform_tc(Exec& ex, MolBuf& m, TcBufs& t);
 int stage_rpa_build_tc(Exec& ex, MolBuf& m, TcBufs& t);
 int stage_sigma_tc(Exec& ex, MolBuf& m, TcBufs& t, Scratch& s, double eta);
 int stage_sigma_fx(Exec& ex, MolBuf& m, FxBufs& f, Scratch& s, double eta);
+int stage_sigma_mp2_fx(Exec& ex, MolBuf& m, FxBufs& f, Scratch& s, double eta);
+void mp2_prepare(Exec& ex, MolBuf& m);
 int stage_ri_mo_transform_fx(Exec& ex, MolBuf& m, const FxMat& L, void* arena);
 int stage_rpa_build_fx(Exec& ex, MolBuf& m, void* arena);
 

@@ -272,6 +272,41 @@ __device__ __forceinline__ double recip_newton(double d) {
 
 constexpr int kSigRows = 4;   // rows p per block of k_fx_sigma_slices
 
+// Digits of the two tiles held in shared memory (kSigRows rows each of one K group):
+// warps 0..3 slice tile `tw` into W, warps 4..7 tile `tp` into P, one (row, group)
+// scale each.
+__device__ __forceinline__ void sigma_tiles_to_digits(const double* tw, const double* tp, int p0, int nb, int g,
+                                                      long long k0, long long K, const FxMat& W, const FxMat& P) {
+  const int t = threadIdx.x;
+  const int warp = t >> 5, lane = t & 31;
+  const int row = warp % kSigRows;
+  const bool isP = warp >= kSigRows;
+  const double* tile = (isP ? tp : tw) + row * kFxGroup;
+  const FxMat& D = isP ? P : W;
+  const int pr = p0 + row;
+  if (pr >= nb) return;
+  // max |x| on the bit patterns: for non-negative doubles the integer order is the value order
+  long long mb = 0;
+  for (int kk = lane; kk < kFxGroup; kk += 32) {
+    const long long b = __double_as_longlong(tile[kk]) & 0x7fffffffffffffffLL;
+    mb = b > mb ? b : mb;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long b = __shfl_xor_sync(0xffffffffu, mb, o);
+    mb = b > mb ? b : mb;
+  }
+  const double u = fx_unit(__longlong_as_double(mb));
+  if (lane == 0) D.u[(long long)pr * D.ngroups + g] = u;
+  const double scale24 = 0x1p24 / u;            // a power of two: exact
+  for (int kk = lane; kk < kFxGroup && k0 + kk < K; kk += 32) {
+    __nv_bfloat16 d[kFxSlices];
+    fx_digits<kFxSlices>(tile[kk], scale24, d);
+    const long long o = (long long)pr * D.ld + k0 + kk;
+#pragma unroll
+    for (int i = 0; i < kFxSlices; ++i) ((__nv_bfloat16*)D.s[i])[o] = d[i];
+  }
+}
+
 // Slices of w and g*w for rows p0 .. p0+3 and one K group (K = mm*sp + s): w is
 // the float64 sum of the group partials of the residue GEMM, x = (eps_p - eps_m)
 // -/+ Omega_s in float64 and g = x / (x^2 + eta^2); each value is formed once,
@@ -308,33 +343,57 @@ __global__ void __launch_bounds__(256) k_fx_sigma_slices(const double* __restric
     tp[r * kFxGroup + kk] = gw;
   }
   __syncthreads();
-  const int warp = t >> 5, lane = t & 31;
-  const int row = warp % kSigRows;
-  const bool isP = warp >= kSigRows;
-  const double* tile = (isP ? tp : tw) + row * kFxGroup;
-  const FxMat& D = isP ? P : W;
-  const int pr = p0 + row;
-  if (pr >= nb) return;
-  // max |x| on the bit patterns: for non-negative doubles the integer order is the value order
-  long long mb = 0;
-  for (int kk = lane; kk < kFxGroup; kk += 32) {
-    const long long b = __double_as_longlong(tile[kk]) & 0x7fffffffffffffffLL;
-    mb = b > mb ? b : mb;
+  sigma_tiles_to_digits(tw, tp, p0, nb, g, k0, K, W, P);
+}
+
+// qsMP2, Eq. (Sigma.c.MP2) with the frequency on row p, for rows p0 .. p0+3 and one
+// K group (K = mm*sp + t, t = i*nv + a'): A = (p m|i a) from the group partials of
+// the direct GEMM (layout of w above), X the exchange partner from its GEMM's
+// partials -- (m a|i p) at [mm][i][p][a'] for occupied m, (m i|a p) at [mm][a'][p][i]
+// for empty m -- and x = (eps_p - eps_m) +/- D_t in float64.  Tiles: A, and
+// g(x) (2 A - X).
+__global__ void __launch_bounds__(256) k_fx_mp2_slices(const double* __restrict__ wbuf,
+                                                       const double* __restrict__ xbuf, int nsplit,
+                                                       long long split_stride, long long ldw, int sp, int nov,
+                                                       int nb, int no, int m0, int cnt,
+                                                       const double* __restrict__ eps,
+                                                       const double* __restrict__ dt, double eta2, FxMat W,
+                                                       FxMat P) {
+  extern __shared__ double sh[];
+  double* tw = sh;
+  double* tp = sh + kSigRows * kFxGroup;
+  const int p0 = blockIdx.x * kSigRows, g = blockIdx.y;
+  const long long K = W.ld;
+  const long long k0 = (long long)g * kFxGroup;
+  const int nv = nb - no;
+  const int t = threadIdx.x;
+  const int r = t % kSigRows;
+  const int p = p0 + r;
+  for (int kk = t / kSigRows; kk < kFxGroup; kk += 256 / kSigRows) {
+    const long long k = k0 + kk;
+    double a = 0.0, pv = 0.0;
+    if (p < nb && k < K) {
+      const int mm = (int)(k / sp), s = (int)(k - (long long)mm * sp);
+      if (mm < cnt && s < nov) {
+        const long long o = (long long)s * ldw + (long long)mm * nb + p;
+        const int m = m0 + mm;
+        const int i = s / nv, ap = s - i * nv;
+        const long long ox = (long long)mm * nb * nov +
+                             ((m < no) ? ((long long)i * nb + p) * nv + ap : ((long long)ap * nb + p) * no + i);
+        double x = 0.0;
+        for (int j = 0; j < nsplit; ++j) {
+          a += wbuf[j * split_stride + o];
+          x += xbuf[j * split_stride + ox];
+        }
+        const double d = (eps[p] - eps[m]) + ((m < no) ? dt[s] : -dt[s]);   // float64 difference
+        pv = (2.0 * a - x) * (d * recip_newton(d * d + eta2));
+      }
+    }
+    tw[r * kFxGroup + kk] = a;
+    tp[r * kFxGroup + kk] = pv;
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    const long long b = __shfl_xor_sync(0xffffffffu, mb, o);
-    mb = b > mb ? b : mb;
-  }
-  const double u = fx_unit(__longlong_as_double(mb));
-  if (lane == 0) D.u[(long long)pr * D.ngroups + g] = u;
-  const double scale24 = 0x1p24 / u;            // a power of two: exact
-  for (int kk = lane; kk < kFxGroup && k0 + kk < K; kk += 32) {
-    __nv_bfloat16 d[kFxSlices];
-    fx_digits<kFxSlices>(tile[kk], scale24, d);
-    const long long o = (long long)pr * D.ld + k0 + kk;
-#pragma unroll
-    for (int i = 0; i < kFxSlices; ++i) ((__nv_bfloat16*)D.s[i])[o] = d[i];
-  }
+  __syncthreads();
+  sigma_tiles_to_digits(tw, tp, p0, nb, g, k0, K, W, P);
 }
 }  // namespace
 
@@ -407,23 +466,25 @@ int stage_rpa_build_fx(Exec& ex, MolBuf& m, void* arena) {
   return MOLGW_OK;
 }
 
-int fx_mblock(int nb, int na, long long nov) {
+int fx_mblock(int nb, int na, long long nov, bool mp2) {
   const long long sp = fx_pad(nov);
-  const long long per_m = (long long)fx_nsplit((int)fx_pad(na)) * nb * nov * 8 + 2 * (long long)fx_mat_bytes(nb, sp);
+  const long long per_m = (mp2 ? 2 : 1) * (long long)fx_nsplit((int)fx_pad(na)) * nb * nov * 8 +
+                          2 * (long long)fx_mat_bytes(nb, sp);
   return (int)std::max<long long>(1, std::min<long long>(nb, kFxBlockBytes / std::max<long long>(per_m, 1)));
 }
 
-size_t fx_sigma_bytes(int nb, int na, long long nov, int mb) {
+size_t fx_sigma_bytes(int nb, int na, long long nov, int mb, bool mp2) {
   const long long nap = fx_pad(na), sp = fx_pad(nov);
   size_t t = 0;
   t += fx_mat_bytes((long long)nb * nb, nap);                            // B^T
-  t += fx_mat_bytes(nov, nap);                                           // R^T
+  t += fx_mat_bytes(nov, nap);                                           // R^T (qsMP2: B_ia^T)
   t += (size_t)fx_nsplit((int)nap) * mb * nb * nov * sizeof(double);     // w of a block
   t += 2 * fx_mat_bytes(nb, (long long)mb * sp) + 1024;                  // sliced w, g*w
+  if (mp2) t += (size_t)fx_nsplit((int)nap) * mb * nb * nov * sizeof(double) + 512;   // exchange partners
   return t;
 }
 
-void fx_bufs_carve(FxBufs& f, int nb, int na, long long nov, int mb, void* base) {
+void fx_bufs_carve(FxBufs& f, int nb, int na, long long nov, int mb, void* base, bool mp2) {
   const long long nap = fx_pad(na);
   char* p = (char*)base;
   f.mb = mb;
@@ -434,6 +495,12 @@ void fx_bufs_carve(FxBufs& f, int nb, int na, long long nov, int mb, void* base)
   f.wbuf = (double*)p;
   p += (size_t)fx_nsplit((int)nap) * mb * nb * nov * sizeof(double);
   f.wp_base = (void*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
+  f.xbuf = nullptr;
+  if (mp2) {
+    const long long sp = fx_pad(nov);
+    const uintptr_t x = (uintptr_t)f.wp_base + 2 * fx_mat_bytes(nb, (long long)mb * sp) + 1024;
+    f.xbuf = (double*)((x + 255) & ~(uintptr_t)255);
+  }
 }
 
 int stage_sigma_fx(Exec& ex, MolBuf& m, FxBufs& f, Scratch& s, double eta) {
@@ -472,6 +539,89 @@ int stage_sigma_fx(Exec& ex, MolBuf& m, FxBufs& f, Scratch& s, double eta) {
                                                    m.eps, m.Om, eta * eta, W, P);
     }
     // S += P W^T over K, at most max_splits K groups per launch
+    const long long kmax = (long long)max_splits * kFxGroup;
+    for (long long k0 = 0; k0 < K; k0 += kmax) {
+      FxGemm gs;
+      gs.M = nb; gs.N = nb;
+      gs.K = (int)std::min(kmax, K - k0);
+      gs.k0 = (int)k0;
+      gs.A = P; gs.B = W;
+      gs.out = s.splitk;
+      gs.out_ld = nb;
+      gs.split_stride = nn;
+      gs.col_major = true;
+      r = fx_gemm(ex, gs);
+      if (r) return r;
+      fx_reduce_cm(ex, s.splitk, fx_nsplit(gs.K), nn, nb, nb, s.S, nb, first ? 0.0 : 1.0);
+      first = false;
+    }
+  }
+  symmetrize(ex, s.S, nb, m.sigc);
+  return MOLGW_OK;
+}
+
+// qsMP2 on the fixed-point engine (BF16X10): per block of summed orbitals m, the
+// direct factor (p m|i a) as one GEMM of B^T (rows (m, p)) with B_ia^T, the
+// exchange partner as one GEMM per m of B^T row ranges ((i, p) x (m, a) for occupied
+// m, (a, p) x (m, i) for empty m), then k_fx_mp2_slices and S += P W^T as in
+// stage_sigma_fx.  Every K sum is exact per 1024-wide group; the denominators float64.
+int stage_sigma_mp2_fx(Exec& ex, MolBuf& m, FxBufs& f, Scratch& s, double eta) {
+  const int nb = m.nb, na = m.na, no = m.no, nv = nb - no;
+  const long long nov = m.nov, nn = (long long)nb * nb;
+  const long long nap = fx_pad(na), sp = fx_pad(nov);
+  if (!f.xbuf) return MOLGW_E_STATE;
+  mp2_prepare(ex, m);
+  fx_split(ex, m.R, nov, na, 1, nov, nullptr, f.Rt);
+  fx_split(ex, m.B, nn, na, 1, nn, nullptr, f.Bt);
+  const int nsw = fx_nsplit((int)nap);
+  const int max_splits = (int)std::max<long long>(1, (long long)s.splitk_cap / std::max<long long>(nn, 1));
+  bool first = true;
+  for (int m0 = 0; m0 < nb; m0 += f.mb) {
+    const int cnt = std::min(f.mb, nb - m0);
+    const long long rows = (long long)cnt * nb;
+    FxGemm gw;
+    gw.M = (int)rows; gw.N = (int)nov; gw.K = (int)nap;
+    gw.A = fx_rows(f.Bt, (long long)m0 * nb, rows);
+    gw.B = f.Rt;
+    gw.out = f.wbuf;
+    gw.out_ld = rows;
+    gw.split_stride = rows * nov;
+    gw.col_major = true;
+    int r = fx_gemm(ex, gw);
+    if (r) return r;
+    for (int mm = 0; mm < cnt; ++mm) {
+      const int mo = m0 + mm;
+      FxGemm gx;
+      gx.K = (int)nap;
+      gx.out = f.xbuf + (long long)mm * nb * nov;
+      gx.split_stride = rows * nov;
+      if (mo < no) {
+        // [(i, p)][a'] = sum_P B^P_ip B^P_{m, no+a'}
+        gx.M = no * nb; gx.N = nv;
+        gx.A = fx_rows(f.Bt, 0, (long long)no * nb);
+        gx.B = fx_rows(f.Bt, (long long)mo * nb + no, nv);
+        gx.out_ld = nv;
+      } else {
+        // [(a', p)][i] = sum_P B^P_{no+a', p} B^P_{m, i}
+        gx.M = nv * nb; gx.N = no;
+        gx.A = fx_rows(f.Bt, (long long)no * nb, (long long)nv * nb);
+        gx.B = fx_rows(f.Bt, (long long)mo * nb, no);
+        gx.out_ld = no;
+      }
+      r = fx_gemm(ex, gx);
+      if (r) return r;
+    }
+    const long long K = (long long)cnt * sp;
+    FxMat W = fx_mat_carve(f.wp_base, nb, K);
+    FxMat P = fx_mat_carve((char*)f.wp_base + ((fx_mat_bytes(nb, K) + 255) / 256 * 256), nb, K);
+    {
+      KScope ks(ex, MOLGW_K_SIGMA);
+      const size_t shm = 2 * kSigRows * kFxGroup * sizeof(double);
+      cudaFuncSetAttribute(k_fx_mp2_slices, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      dim3 grid(ceil_div(nb, kSigRows), W.ngroups);
+      k_fx_mp2_slices<<<grid, 256, shm, ex.st>>>(f.wbuf, f.xbuf, nsw, rows * nov, rows, (int)sp, (int)nov, nb, no,
+                                                 m0, cnt, m.eps, m.Om, eta * eta, W, P);
+    }
     const long long kmax = (long long)max_splits * kFxGroup;
     for (long long k0 = 0; k0 < K; k0 += kmax) {
       FxGemm gs;

@@ -139,4 +139,57 @@ def test_qsmp2_has_no_rpa_and_needs_float64():
         with pytest.raises(MolgwError):
             ctx.fetch(0, "Omega", np.empty(5 * 19))
     with pytest.raises(MolgwError):
-        lib_context(precision="bf16x10", flags=FLAG_QSMP2)
+        lib_context(precision="bf16x3", flags=FLAG_QSMP2)
+
+
+@pytest.mark.parametrize("flags", [FLAG_QSMP2, FLAG_QSMP2 | 16])
+@pytest.mark.parametrize("nb,no,na,seed", [(24, 5, 72, 0), (71, 13, 150, 2), (37, 1, 60, 3), (33, 32, 50, 4)])
+def test_qsmp2_fixed_point_within_1mev(flags, nb, no, na, seed):
+    """BF16X10: the three qsMP2 contractions (and with MOLGW_FLAG_TC_AB stage (a)) on
+    the fixed-point engine, denominators float64: Sigma_c to 1e-7 of its maximum, the
+    quasiparticle energies to 1 meV or 5e-8 of their largest magnitude.  Unscreened,
+    these strongly coupled inputs put qsMP2 energies at 1e2 - 3e5 Ha (residues of
+    order one over denominators within eta of zero), where 1 meV would be 1e-11
+    relative; B from the fixed-point (a) is exact to ~5e-9 of its maximum and
+    Sigma_c goes as B^4."""
+    m = sy.molecule(nb, no, na, seed)
+    r = qsgw.qsmp2_pass(m["L"], m["eps"], m["C"], no, ETA)
+    with lib_context(precision="bf16x10", flags=flags) as ctx:
+        load_mol(ctx, 0, m)
+        sc = np.empty((nb, nb))
+        ctx.sigma(0, None, sc)
+        eps = np.empty(nb)
+        ctx.qs_step(0, eps)
+    assert rel_max(sc, r["sigma_c"]) < 1e-7
+    assert np.max(np.abs(eps - r["eps_new"])) < max(3.675e-5, 5e-8 * np.max(np.abs(r["eps_new"])))
+
+
+def test_qsmp2_fixed_point_full_size():
+    nb, no, na = 200, 40, 600
+    m = sy.molecule(nb, no, na, 1)
+    r = qsgw.qsmp2_pass(m["L"], m["eps"], m["C"], no, ETA)
+    with lib_context(precision="bf16x10", flags=FLAG_QSMP2 | 16) as ctx:
+        load_mol(ctx, 0, m)
+        eps = np.empty(nb)
+        ctx.qs_step(0, eps)
+    assert np.max(np.abs(eps - r["eps_new"])) < max(3.675e-5, 5e-8 * np.max(np.abs(r["eps_new"])))
+
+
+def test_qsmp2_fixed_point_batch_lanes_equal_solo():
+    mols = [sy.batch_molecule(s) for s in (120, 121, 122)]
+    solo = []
+    for m in mols:
+        with lib_context(precision="bf16x10", flags=FLAG_QSMP2 | 16) as ctx:
+            load_mol(ctx, 0, m)
+            e = np.empty(m["n_basis"])
+            ctx.qs_step(0, e)
+            solo.append(e)
+    with lib_context(precision="bf16x10", flags=FLAG_QSMP2 | 16, max_mols=3, lanes=3) as ctx:
+        for k, m in enumerate(mols):
+            load_mol(ctx, k, m)
+        ctx.qs_step(-1)
+        ctx.sync()
+        for k, m in enumerate(mols):
+            e = np.empty(m["n_basis"])
+            ctx.fetch(k, "eps", e)
+            assert np.array_equal(e, solo[k])
