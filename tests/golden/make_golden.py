@@ -1,9 +1,12 @@
-"""Writes tests/golden/qsgw_nb24_no5_na72_seed0.json from the CPU oracle only.
+"""Writes the files of tests/golden/ from the CPU oracle only.
 
 Workload: one closed-shell molecule, n_basis=24, n_occ=5, n_aux=72, seed 0,
-eta = 1e-3 Ha, one RI-qsGW pass (Eqs. AO.to.MO, Casida, w.residue, Sigma.c.GW,
-Sigma.c.qsGW.real, K, H, GEP of arXiv 2210.17093).  The values are the oracle's;
-the paper prints no worked example.  Run from the repository root:
+eta = 1e-3 Ha.  qsgw_nb24_no5_na72_seed0.json: one RI-qsGW pass (Eqs. AO.to.MO,
+Casida, w.residue, Sigma.c.GW, Sigma.c.qsGW.real, K, H, GEP of arXiv 2210.17093).
+qsmp2_g0w0_nb24_no5_na72_seed0.json: one qsMP2 pass (Eqs. Sigma.c.MP2,
+Sigma.c.qsMP2.real) and the one-shot G0W0 energies (diagonal of Eq. Sigma.c.GW,
+linearised).  The values are the oracle's; the paper prints no worked example.
+Run from the repository root:
     python tests/golden/make_golden.py
 """
 import json
@@ -17,6 +20,7 @@ import synthetic as sy  # noqa: E402
 from oracle import qsgw  # noqa: E402
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "qsgw_nb24_no5_na72_seed0.json")
+OUT2 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "qsmp2_g0w0_nb24_no5_na72_seed0.json")
 
 
 def main():
@@ -32,6 +36,18 @@ def main():
     }
     with open(OUT, "w") as f:
         json.dump(doc, f, indent=0)
+    q = qsgw.qsmp2_pass(m["L"], m["eps"], m["C"], 5, sy.ETA)
+    g = qsgw.g0w0_pass(m["L"], m["eps"], m["C"], 5, sy.ETA)
+    doc2 = {
+        "source": "oracle/qsgw.py qsmp2_pass and g0w0_pass; arXiv 2210.17093 Sec. II.C-D",
+        "workload": {"n_basis": 24, "n_occ": 5, "n_aux": 72, "seed": 0, "eta": sy.ETA},
+        "qsmp2_sigma_c": q["sigma_c"].tolist(),
+        "qsmp2_eps_new": q["eps_new"].tolist(),
+        "g0w0_eps_qp": g["eps_qp"].tolist(),
+        "g0w0_z": g["Z"].tolist(),
+    }
+    with open(OUT2, "w") as f:
+        json.dump(doc2, f, indent=0)
 
 
 if __name__ == "__main__":

@@ -92,3 +92,16 @@ def test_large_eta_returns_the_input():
         shift.append(np.max(np.abs(r["eps_qp"] - m["eps"])))
         assert np.max(np.abs(r["Z"] - 1.0)) < 1e-9
     assert shift[0] < 1e-8 and 50.0 < shift[0] / shift[1] < 200.0
+
+
+def test_golden_regression():
+    """The oracle still reproduces the stored small-workload values (tests/golden)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "qsmp2_g0w0_nb24_no5_na72_seed0.json")
+    doc = json.load(open(path))
+    w = doc["workload"]
+    m = sy.molecule(w["n_basis"], w["n_occ"], w["n_aux"], w["seed"])
+    r = qsgw.g0w0_pass(m["L"], m["eps"], m["C"], w["n_occ"], w["eta"])
+    np.testing.assert_allclose(r["eps_qp"], doc["g0w0_eps_qp"], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(r["Z"], doc["g0w0_z"], rtol=1e-12, atol=1e-12)

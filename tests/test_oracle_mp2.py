@@ -143,3 +143,16 @@ def test_qsmp2_iterations_keep_orthonormal_orbitals():
         C = r["C_new"]
         assert np.allclose(C.T @ C, np.eye(10), atol=1e-12)
         assert np.all(np.diff(r["eps_new"]) >= 0)
+
+
+def test_golden_regression():
+    """The oracle still reproduces the stored small-workload values (tests/golden)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "qsmp2_g0w0_nb24_no5_na72_seed0.json")
+    doc = json.load(open(path))
+    w = doc["workload"]
+    m = sy.molecule(w["n_basis"], w["n_occ"], w["n_aux"], w["seed"])
+    r = qsgw.qsmp2_pass(m["L"], m["eps"], m["C"], w["n_occ"], w["eta"])
+    np.testing.assert_allclose(r["sigma_c"], doc["qsmp2_sigma_c"], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(r["eps_new"], doc["qsmp2_eps_new"], rtol=1e-12, atol=1e-12)
