@@ -53,6 +53,7 @@ struct molgw_ctx_s {
   int64_t graph_replays = 0;
   int graph_lanes = 0;           // lane count of the captured plan
   int tuned_lanes = 0;           // molgw_b200_autotune's choice (0: none)
+  int g0w0_p0 = 0, g0w0_p1 = 0;  // state window of the G0W0 call in flight (clipped per molecule)
   GemmTuner tuner;               // float64 GEMM tile choices (molgw_b200_autotune)
 };
 
@@ -386,7 +387,7 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
       stage_j_sigx(ex, m, l.scr);
       m.jx_valid = m.have_jx = true;
     }
-    r = stage_g0w0(ex, m, l.scr, c->opts.eta);
+    r = stage_g0w0(ex, m, l.scr, c->opts.eta, std::min(c->g0w0_p0, m.nb), std::min(c->g0w0_p1, m.nb));
     if (r) return r;
     m.have_g0w0 = true;
     return launch_status();
@@ -810,9 +811,12 @@ int molgw_b200_sigma(molgw_ctx c, int mol, double* sigma_x, double* sigma_c) {
   return sync ? read_status(c) : MOLGW_OK;
 }
 
-int molgw_b200_g0w0(molgw_ctx c, int mol, double* eps_qp, double* z, double* sigma_c_diag) {
-  if (!c) return MOLGW_E_ARG;
+int molgw_b200_g0w0_window(molgw_ctx c, int mol, int p_begin, int p_end, double* eps_qp, double* z,
+                           double* sigma_c_diag) {
+  if (!c || p_begin < 0 || p_end <= p_begin) return MOLGW_E_ARG;
   DeviceGuard g(c->device);
+  c->g0w0_p0 = p_begin;
+  c->g0w0_p1 = p_end;
   if (mol == -1) {
     if (eps_qp || z || sigma_c_diag) return MOLGW_E_ARG;
     return run_mols(c, -1, 'g');
@@ -820,14 +824,22 @@ int molgw_b200_g0w0(molgw_ctx c, int mol, double* eps_qp, double* z, double* sig
   if (!mol_ok(c, mol)) return MOLGW_E_ARG;
   MolBuf& m = c->mols[mol];
   if (!ready(m)) return MOLGW_E_STATE;
+  if (p_end > m.nb) return MOLGW_E_ARG;
   int r = run_mols(c, mol, 'g');
   if (r) return r;
   bool sync = false;
-  if (eps_qp) r = copy_out(c, eps_qp, m.g0w0, m.nb, &sync);
-  if (!r && z) r = copy_out(c, z, m.g0w0 + m.nb, m.nb, &sync);
-  if (!r && sigma_c_diag) r = copy_out(c, sigma_c_diag, m.g0w0 + 2 * m.nb, m.nb, &sync);
+  const int np = p_end - p_begin;
+  if (eps_qp) r = copy_out(c, eps_qp, m.g0w0 + p_begin, np, &sync);
+  if (!r && z) r = copy_out(c, z, m.g0w0 + m.nb + p_begin, np, &sync);
+  if (!r && sigma_c_diag) r = copy_out(c, sigma_c_diag, m.g0w0 + 2 * m.nb + p_begin, np, &sync);
   if (r) return r;
   return sync ? read_status(c) : MOLGW_OK;
+}
+
+int molgw_b200_g0w0(molgw_ctx c, int mol, double* eps_qp, double* z, double* sigma_c_diag) {
+  if (!c) return MOLGW_E_ARG;
+  const int nb = (mol >= 0 && mol_ok(c, mol)) ? c->mols[mol].nb : (1 << 30);
+  return molgw_b200_g0w0_window(c, mol, 0, nb, eps_qp, z, sigma_c_diag);
 }
 
 int molgw_b200_qs_step(molgw_ctx c, int mol, double* eps_out, double* C_out) {

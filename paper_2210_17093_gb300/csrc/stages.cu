@@ -197,12 +197,12 @@ __global__ void k_apply_g_mp2(const double* Wb, const double* eps, const double*
 // G0W0, the diagonal of Eq. (Sigma.c.GW): for row p of one block of m (one CTA per
 // p), sum over (m, s) of (w^s_pm)^2 g(x) and (w^s_pm)^2 g'(x), x = eps_p - eps_m +/- Omega_s,
 // g' = (eta^2 - x^2) / (x^2 + eta^2)^2.  Fixed-order block reduction.
-__global__ void k_g0w0_block(const double* Wb, const double* eps, const double* Om, int nb, int no, int m0,
-                             int mb, int nov, double eta, double* part) {
-  const int p = blockIdx.x;
+__global__ void k_g0w0_block(const double* Wb, const double* eps, const double* Om, int nb, int no, int p0,
+                             int m0, int mb, int nov, double eta, double* part) {
+  const int pl = blockIdx.x, p = p0 + pl, np = gridDim.x;
   const long long K = (long long)mb * nov;
   const double eta2 = eta * eta;
-  const double* w = Wb + (long long)p * K;
+  const double* w = Wb + (long long)pl * K;
   double a = 0.0, d = 0.0;
   for (long long k = threadIdx.x; k < K; k += blockDim.x) {
     const int mm = (int)(k / nov), s = (int)(k % nov);
@@ -225,21 +225,23 @@ __global__ void k_g0w0_block(const double* Wb, const double* eps, const double* 
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    part[p] = sa[0];
-    part[nb + p] = sd[0];
+    part[pl] = sa[0];
+    part[np + pl] = sd[0];
   }
 }
 
 // Linearised quasiparticle equation: Z_p = 1 / (1 - Sigma'_pp), v_pp = eps_p - h_pp - J_pp,
-// eps^QP_p = eps_p + Z_p (Sigma_x,pp + Sigma_c,pp - v_pp).  out = [eps^QP | Z | Sigma_c,pp].
+// eps^QP_p = eps_p + Z_p (Sigma_x,pp + Sigma_c,pp - v_pp), for p0 <= p < p0 + np.
+// out = [eps^QP | Z | Sigma_c,pp], each of length nb, indexed by p.
 __global__ void k_g0w0_final(const double* part, int nblk, const double* eps, const double* hmo,
-                             const double* J, const double* sigx, int nb, double* out) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= nb) return;
+                             const double* J, const double* sigx, int nb, int p0, int np, double* out) {
+  const int pl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pl >= np) return;
+  const int p = p0 + pl;
   double sg = 0.0, dg = 0.0;
   for (int b = 0; b < nblk; ++b) {
-    sg += part[2LL * b * nb + p];
-    dg += part[2LL * b * nb + nb + p];
+    sg += part[2LL * b * np + pl];
+    dg += part[2LL * b * np + np + pl];
   }
   const long long pp = (long long)p * nb + p;
   const double v = eps[p] - hmo[pp] - J[pp];
@@ -578,33 +580,36 @@ void stage_sigma_mp2(Exec& ex, MolBuf& m, Scratch& s, double eta) {
   k_symmetrize<<<grid_for(nn), 256, 0, ex.st>>>(s.S, nb, m.sigc);
 }
 
-// One-shot G0W0 from the current Omega, R (float64 residues at every precision):
-// w per block of m as in the float64 Sigma stage, the diagonal sums per block, then
-// the linearised quasiparticle energies into m.g0w0.  Needs 2 nb ceil(nb / mb)
-// doubles of split-K scratch.
-int stage_g0w0(Exec& ex, MolBuf& m, Scratch& s, double eta) {
+// One-shot G0W0 from the current Omega, R (float64 residues at every precision) for
+// the states p0 <= p < p1: w^s_pm for those rows only, per block of m, the diagonal
+// sums per block, then the linearised quasiparticle energies into m.g0w0[p].  Needs
+// 2 (p1 - p0) ceil(nb / mb) doubles of split-K scratch.
+int stage_g0w0(Exec& ex, MolBuf& m, Scratch& s, double eta, int p0, int p1) {
   const int nb = m.nb, na = m.na, no = m.no;
   const int nov = (int)m.nov;
   const long long nn = (long long)nb * nb;
-  const int mb = std::max(1, std::min(nb, (int)(s.wblk_cap / ((long long)nb * nov))));
+  const int np = p1 - p0;
+  if (np <= 0) return MOLGW_OK;
+  const int mb = std::max(1, std::min(nb, (int)(s.wblk_cap / ((long long)np * nov))));
   const int nblk = ceil_div(nb, mb);
-  if ((size_t)2 * nb * nblk > s.splitk_cap) return MOLGW_E_NOMEM;
+  if ((size_t)2 * np * nblk > s.splitk_cap) return MOLGW_E_NOMEM;
   for (int b = 0; b < nblk; ++b) {
     const int m0 = b * mb, cnt = std::min(mb, nb - m0);
     const long long K = (long long)cnt * nov;
     GemmF64 g;
-    g.M = nb; g.N = nov; g.K = na; g.batch = cnt;
-    g.A = m.B + (long long)m0 * nb; g.sa_m = 1; g.sa_k = nn; g.sa_b = nb;
+    g.M = np; g.N = nov; g.K = na; g.batch = cnt;
+    g.A = m.B + (long long)m0 * nb + p0; g.sa_m = 1; g.sa_k = nn; g.sa_b = nb;
     g.B = m.R; g.sb_k = nov; g.sb_n = 1; g.sb_b = 0;
     g.C = s.wblk; g.sc_m = K; g.sc_n = 1; g.sc_b = nov;
     g.kclass = MOLGW_K_SIGMA;
     gemm_f64(ex, g);
     KScope ks(ex, MOLGW_K_SIGMA);
-    k_g0w0_block<<<nb, 256, 0, ex.st>>>(s.wblk, m.eps, m.Om, nb, no, m0, cnt, nov, eta,
-                                                  s.splitk + 2LL * b * nb);
+    k_g0w0_block<<<np, 256, 0, ex.st>>>(s.wblk, m.eps, m.Om, nb, no, p0, m0, cnt, nov, eta,
+                                         s.splitk + 2LL * b * np);
   }
   KScope ks(ex, MOLGW_K_MISC);
-  k_g0w0_final<<<ceil_div(nb, 128), 128, 0, ex.st>>>(s.splitk, nblk, m.eps, m.hmo, m.J, m.sigx, nb, m.g0w0);
+  k_g0w0_final<<<ceil_div(np, 128), 128, 0, ex.st>>>(s.splitk, nblk, m.eps, m.hmo, m.J, m.sigx, nb, p0, np,
+                                                      m.g0w0);
   return MOLGW_OK;
 }
 

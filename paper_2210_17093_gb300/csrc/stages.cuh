@@ -91,7 +91,7 @@ void stage_rpa_build(Exec& ex, MolBuf& m);
 void stage_rpa_eigensolve(Exec& ex, MolBuf& m, EigWork& w, Scratch& s, bool full_xpy);
 void stage_sigma(Exec& ex, MolBuf& m, Scratch& s, double eta);
 void stage_sigma_mp2(Exec& ex, MolBuf& m, Scratch& s, double eta);
-int stage_g0w0(Exec& ex, MolBuf& m, Scratch& s, double eta);
+int stage_g0w0(Exec& ex, MolBuf& m, Scratch& s, double eta, int p0, int p1);
 void derive_h_from_hf(Exec& ex, MolBuf& m);
 void h_ao_to_mo(Exec& ex, MolBuf& m, const double* hao, Scratch& s);
 void stage_qs_update(Exec& ex, MolBuf& m, EigWork& w, Scratch& s);

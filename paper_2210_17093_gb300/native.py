@@ -38,7 +38,8 @@ EXPORTS = ["molgw_b200_create", "molgw_b200_set_ri", "molgw_b200_set_orbitals", 
            "molgw_b200_rpa_matrix", "molgw_b200_eigh", "molgw_b200_kernel_stats",
            "molgw_b200_launch_count", "molgw_b200_set_timing", "molgw_b200_destroy",
            "molgw_b200_status_string", "molgw_b200_eigh_noalloc", "molgw_b200_graph_replays",
-           "molgw_b200_tc_gemm", "molgw_b200_autotune", "molgw_b200_lanes", "molgw_b200_g0w0"]
+           "molgw_b200_tc_gemm", "molgw_b200_autotune", "molgw_b200_lanes", "molgw_b200_g0w0",
+           "molgw_b200_g0w0_window"]
 NOALLOC_NMAX = 256
 
 
@@ -76,6 +77,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "molgw_b200_sigma": ([vp, ip, dp, dp], ip),
         "molgw_b200_qs_step": ([vp, ip, dp, dp], ip),
         "molgw_b200_g0w0": ([vp, ip, dp, dp, dp], ip),
+        "molgw_b200_g0w0_window": ([vp, ip, ip, ip, dp, dp, dp], ip),
         "molgw_b200_sync": ([vp], ip),
         "molgw_b200_fetch": ([vp, ip, ip, dp, sz], ip),
         "molgw_b200_rpa_matrix": ([vp, ip, dp], ip),
@@ -195,6 +197,11 @@ class Context:
         nb = self.sizes[mol][0] if mol in self.sizes else None
         _check(self._lib.molgw_b200_g0w0(self._hh(), mol, _ptr(eps_qp, nb), _ptr(z, nb), _ptr(sigma_c_diag, nb)),
                "g0w0")
+
+    def g0w0_window(self, mol: int, p_begin: int, p_end: int, eps_qp=None, z=None, sigma_c_diag=None):
+        n = p_end - p_begin
+        _check(self._lib.molgw_b200_g0w0_window(self._hh(), mol, p_begin, p_end, _ptr(eps_qp, n), _ptr(z, n),
+                                                _ptr(sigma_c_diag, n)), "g0w0_window")
 
     def sync(self):
         _check(self._lib.molgw_b200_sync(self._hh()), "sync")

@@ -92,3 +92,34 @@ def test_g0w0_not_with_qsmp2():
         load_mol(ctx, 0, m)
         with pytest.raises(MolgwError):
             ctx.g0w0(0, np.empty(24))
+
+
+def test_g0w0_state_window():
+    """The window p_begin <= p < p_end (frontier states here) gives the full call's values
+    for those states (up to the summation grouping, which follows the window's size)."""
+    nb, no, na = 71, 13, 150
+    m = sy.molecule(nb, no, na, 2)
+    with lib_context() as ctx:
+        load_mol(ctx, 0, m)
+        e_all, z_all = np.empty(nb), np.empty(nb)
+        ctx.g0w0(0, e_all, z_all)
+        lo, hi = no - 3, no + 3
+        e, z, s = np.empty(hi - lo), np.empty(hi - lo), np.empty(hi - lo)
+        ctx.g0w0_window(0, lo, hi, e, z, s)
+        full = np.empty(nb)
+        ctx.fetch(0, "eps_qp", full)
+    np.testing.assert_allclose(e, e_all[lo:hi], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(z, z_all[lo:hi], rtol=1e-10, atol=1e-13)
+    np.testing.assert_array_equal(full[lo:hi], e)
+    r = qsgw.g0w0_pass(m["L"], m["eps"], m["C"], no, ETA)
+    np.testing.assert_allclose(s, r["sigma_c_diag"][lo:hi], rtol=0, atol=1e-10 * np.max(np.abs(r["sigma_c_diag"])))
+
+
+def test_g0w0_window_arguments():
+    from paper_2210_17093_gb300 import MolgwError
+    m = sy.molecule(24, 5, 72, 0)
+    with lib_context() as ctx:
+        load_mol(ctx, 0, m)
+        for lo, hi in ((3, 3), (-1, 2), (20, 25)):
+            with pytest.raises(MolgwError):
+                ctx.g0w0_window(0, lo, hi)
