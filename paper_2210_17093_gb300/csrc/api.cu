@@ -331,7 +331,7 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
   const bool tc_ab = use_tc_ab(c);
   TcBufs& tb = l.tco;
   if (use_fx(c)) {
-    fx_bufs_carve(l.fxo, m.nb, m.na, m.nov, fx_mblock(m.nb, m.na, m.nov, mp2), l.tco_base, mp2);
+    fx_bufs_carve(l.fxo, m.nb, m.na, m.nov, fx_mblock(m.nb, m.na, m.nov, mp2), l.tco_base, mp2, m.no);
   } else if (tc) {
     const int prec = tc_prec(c);
     tc_bufs_carve(tb, prec, m.nb, m.na, m.nov, tc_mblock(prec, m.nb, m.nov), (double*)l.tco_base);

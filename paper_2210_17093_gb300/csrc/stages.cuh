@@ -59,13 +59,14 @@ struct FxBufs {
   double* wbuf = nullptr;      // w of a block: [K group][s][(m, p)]
   void* wp_base = nullptr;     // arena of the sliced w and g*w of a block
   double* xbuf = nullptr;      // qsMP2: the exchange partners of a block, per K group
+  FxMat Bo, Bv;                // qsMP2: rows (m, i) and (m, a) of B^T, K = P
 };
 // m values per block; mp2 adds the exchange partners' float64 partials to each block
 int fx_mblock(int nb, int na, long long nov, bool mp2 = false);
 // lane arena of stages (a), (b) on the fixed-point engine: C, T = L C and Xv as digits
 size_t fx_ab_bytes(int nb, int na, long long nov);
 size_t fx_sigma_bytes(int nb, int na, long long nov, int mb, bool mp2 = false);
-void fx_bufs_carve(FxBufs& f, int nb, int na, long long nov, int mb, void* base, bool mp2 = false);
+void fx_bufs_carve(FxBufs& f, int nb, int na, long long nov, int mb, void* base, bool mp2 = false, int no = 0);
 
 struct Scratch {
   double* rho = nullptr;        // n_aux

@@ -260,14 +260,14 @@ namespace {
 
 constexpr long long kFxBlockBytes = 1LL << 30;   // w and its slices per block of m
 
-// 1/d by Newton-Raphson iteration from a float32 seed (two steps: each squares
-// the relative error, 2^-23 -> 2^-46 -> below float64 rounding); d > 0.
+// 1/d by one Newton-Raphson step from a float32 seed: the relative error goes from
+// ~2^-23 to ~2^-46, far below the 2^-32 (relative to a group's maximum) of the
+// fixed-point digits made from it.  The range test runs on the float32 copy.  d > 0.
 __device__ __forceinline__ double recip_newton(double d) {
-  if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
-  double r = (double)__frcp_rn((float)d);
-  r = r * (2.0 - d * r);
-  r = r * (2.0 - d * r);
-  return r;
+  const float df = (float)d;
+  if (!(df > 1e-30f && df < 1e30f)) return 1.0 / d;
+  const double r = (double)__frcp_rn(df);
+  return fma(r, fma(-d, r, 1.0), r);
 }
 
 constexpr int kSigRows = 4;   // rows p per block of k_fx_sigma_slices
@@ -348,10 +348,10 @@ __global__ void __launch_bounds__(256) k_fx_sigma_slices(const double* __restric
 
 // qsMP2, Eq. (Sigma.c.MP2) with the frequency on row p, for rows p0 .. p0+3 and one
 // K group (K = mm*sp + t, t = i*nv + a'): A = (p m|i a) from the group partials of
-// the direct GEMM (layout of w above), X the exchange partner from its GEMM's
-// partials -- (m a|i p) at [mm][i][p][a'] for occupied m, (m i|a p) at [mm][a'][p][i]
-// for empty m -- and x = (eps_p - eps_m) +/- D_t in float64.  Tiles: A, and
-// g(x) (2 A - X).
+// the direct GEMM (layout of w above), X the exchange partner from its GEMMs'
+// partials -- (m a|i p) at [mm][a'][i][p] for occupied m, (m i|a p) at [mm][i][a'][p]
+// for empty m, p fastest as in w -- and x = (eps_p - eps_m) +/- D_t in float64.
+// Tiles: A, and g(x) (2 A - X).
 __global__ void __launch_bounds__(256) k_fx_mp2_slices(const double* __restrict__ wbuf,
                                                        const double* __restrict__ xbuf, int nsplit,
                                                        long long split_stride, long long ldw, int sp, int nov,
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(256) k_fx_mp2_slices(const double* __restrict_
         const int m = m0 + mm;
         const int i = s / nv, ap = s - i * nv;
         const long long ox = (long long)mm * nb * nov +
-                             ((m < no) ? ((long long)i * nb + p) * nv + ap : ((long long)ap * nb + p) * no + i);
+                             ((m < no) ? ((long long)ap * no + i) * nb + p : (long long)s * nb + p);
         double x = 0.0;
         for (int j = 0; j < nsplit; ++j) {
           a += wbuf[j * split_stride + o];
@@ -480,11 +480,14 @@ size_t fx_sigma_bytes(int nb, int na, long long nov, int mb, bool mp2) {
   t += fx_mat_bytes(nov, nap);                                           // R^T (qsMP2: B_ia^T)
   t += (size_t)fx_nsplit((int)nap) * mb * nb * nov * sizeof(double);     // w of a block
   t += 2 * fx_mat_bytes(nb, (long long)mb * sp) + 1024;                  // sliced w, g*w
-  if (mp2) t += (size_t)fx_nsplit((int)nap) * mb * nb * nov * sizeof(double) + 512;   // exchange partners
+  if (mp2) {
+    t += (size_t)fx_nsplit((int)nap) * mb * nb * nov * sizeof(double) + 512;   // exchange partners
+    t += fx_mat_bytes((long long)nb * nb, nap) + 2048;   // B_occ^T and B_vir^T: nb^2 rows together
+  }
   return t;
 }
 
-void fx_bufs_carve(FxBufs& f, int nb, int na, long long nov, int mb, void* base, bool mp2) {
+void fx_bufs_carve(FxBufs& f, int nb, int na, long long nov, int mb, void* base, bool mp2, int no) {
   const long long nap = fx_pad(na);
   char* p = (char*)base;
   f.mb = mb;
@@ -500,6 +503,11 @@ void fx_bufs_carve(FxBufs& f, int nb, int na, long long nov, int mb, void* base,
     const long long sp = fx_pad(nov);
     const uintptr_t x = (uintptr_t)f.wp_base + 2 * fx_mat_bytes(nb, (long long)mb * sp) + 1024;
     f.xbuf = (double*)((x + 255) & ~(uintptr_t)255);
+    const uintptr_t b = (uintptr_t)(f.xbuf + (size_t)fx_nsplit((int)nap) * mb * nb * nov);
+    char* q = (char*)((b + 255) & ~(uintptr_t)255);
+    f.Bo = fx_mat_carve(q, (long long)nb * no, nap);
+    q += fx_mat_bytes((long long)nb * no, nap);
+    f.Bv = fx_mat_carve(q, (long long)nb * (nb - no), nap);
   }
 }
 
@@ -560,11 +568,24 @@ int stage_sigma_fx(Exec& ex, MolBuf& m, FxBufs& f, Scratch& s, double eta) {
   return MOLGW_OK;
 }
 
+// element (r = m cq + q, k = P) = B[P][m][q0 + q], q < cq: a column range of every B_P
+struct BColSrc {
+  const double* B;
+  long long nb, q0, cq, rows, na;
+  __device__ double operator()(long long r, long long k) const {
+    if (r >= rows || k >= na) return 0.0;
+    const long long m = r / cq, q = r - m * cq;
+    return B[(k * nb + m) * nb + q0 + q];
+  }
+};
+
 // qsMP2 on the fixed-point engine (BF16X10): per block of summed orbitals m, the
 // direct factor (p m|i a) as one GEMM of B^T (rows (m, p)) with B_ia^T, the
-// exchange partner as one GEMM per m of B^T row ranges ((i, p) x (m, a) for occupied
-// m, (a, p) x (m, i) for empty m), then k_fx_mp2_slices and S += P W^T as in
-// stage_sigma_fx.  Every K sum is exact per 1024-wide group; the denominators float64.
+// exchange partners of the block's occupied m as one GEMM (rows (i, p) of B^T against
+// rows (m, a) of B_vir^T) and of its empty m as another ((a, p) of B^T against (m, i)
+// of B_occ^T), so that each operand is read once per block; then k_fx_mp2_slices and
+// S += P W^T as in stage_sigma_fx.  Every K sum is exact per 1024-wide group; the
+// denominators float64.
 int stage_sigma_mp2_fx(Exec& ex, MolBuf& m, FxBufs& f, Scratch& s, double eta) {
   const int nb = m.nb, na = m.na, no = m.no, nv = nb - no;
   const long long nov = m.nov, nn = (long long)nb * nb;
@@ -573,6 +594,8 @@ int stage_sigma_mp2_fx(Exec& ex, MolBuf& m, FxBufs& f, Scratch& s, double eta) {
   mp2_prepare(ex, m);
   fx_split(ex, m.R, nov, na, 1, nov, nullptr, f.Rt);
   fx_split(ex, m.B, nn, na, 1, nn, nullptr, f.Bt);
+  fx_slice(ex, BColSrc{m.B, nb, 0, no, (long long)nb * no, na}, (long long)nb * no, f.Bo, MOLGW_K_SIGMA);
+  fx_slice(ex, BColSrc{m.B, nb, no, nv, (long long)nb * nv, na}, (long long)nb * nv, f.Bv, MOLGW_K_SIGMA);
   const int nsw = fx_nsplit((int)nap);
   const int max_splits = (int)std::max<long long>(1, (long long)s.splitk_cap / std::max<long long>(nn, 1));
   bool first = true;
@@ -589,25 +612,30 @@ int stage_sigma_mp2_fx(Exec& ex, MolBuf& m, FxBufs& f, Scratch& s, double eta) {
     gw.col_major = true;
     int r = fx_gemm(ex, gw);
     if (r) return r;
-    for (int mm = 0; mm < cnt; ++mm) {
-      const int mo = m0 + mm;
+    // X_m at xbuf + mm nb n_ov: [a'][i][p] for occupied m, [i][a'][p] for empty m
+    const int cnt_o = std::max(0, std::min(m0 + cnt, no) - m0);
+    const int mv0 = std::max(m0, no), cnt_v = m0 + cnt - mv0;
+    if (cnt_o > 0) {
       FxGemm gx;
-      gx.K = (int)nap;
-      gx.out = f.xbuf + (long long)mm * nb * nov;
+      gx.M = no * nb; gx.N = cnt_o * nv; gx.K = (int)nap;
+      gx.A = fx_rows(f.Bt, 0, (long long)no * nb);
+      gx.B = fx_rows(f.Bv, (long long)m0 * nv, (long long)cnt_o * nv);
+      gx.out = f.xbuf;
+      gx.out_ld = (long long)no * nb;
       gx.split_stride = rows * nov;
-      if (mo < no) {
-        // [(i, p)][a'] = sum_P B^P_ip B^P_{m, no+a'}
-        gx.M = no * nb; gx.N = nv;
-        gx.A = fx_rows(f.Bt, 0, (long long)no * nb);
-        gx.B = fx_rows(f.Bt, (long long)mo * nb + no, nv);
-        gx.out_ld = nv;
-      } else {
-        // [(a', p)][i] = sum_P B^P_{no+a', p} B^P_{m, i}
-        gx.M = nv * nb; gx.N = no;
-        gx.A = fx_rows(f.Bt, (long long)no * nb, (long long)nv * nb);
-        gx.B = fx_rows(f.Bt, (long long)mo * nb, no);
-        gx.out_ld = no;
-      }
+      gx.col_major = true;
+      r = fx_gemm(ex, gx);
+      if (r) return r;
+    }
+    if (cnt_v > 0) {
+      FxGemm gx;
+      gx.M = nv * nb; gx.N = cnt_v * no; gx.K = (int)nap;
+      gx.A = fx_rows(f.Bt, (long long)no * nb, (long long)nv * nb);
+      gx.B = fx_rows(f.Bo, (long long)mv0 * no, (long long)cnt_v * no);
+      gx.out = f.xbuf + (long long)(mv0 - m0) * nb * nov;
+      gx.out_ld = (long long)nv * nb;
+      gx.split_stride = rows * nov;
+      gx.col_major = true;
       r = fx_gemm(ex, gx);
       if (r) return r;
     }
