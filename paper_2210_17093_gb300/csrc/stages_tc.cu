@@ -333,7 +333,8 @@ __global__ void __launch_bounds__(256) k_fx_sigma_slices(const double* __restric
       const int mm = (int)(k / sp), s = (int)(k - (long long)mm * sp);
       if (mm < cnt && s < nov) {
         const long long o = (long long)s * ldw + (long long)mm * nb + p;
-        for (int j = 0; j < nsplit; ++j) w += wbuf[j * split_stride + o];
+        w = wbuf[o];
+        for (int j = 1; j < nsplit; ++j) w += wbuf[j * split_stride + o];
         const int m = m0 + mm;
         const double x = (eps[p] - eps[m]) + ((m < no) ? om[s] : -om[s]);   // float64 difference
         gw = w * (x * recip_newton(x * x + eta2));
@@ -380,8 +381,9 @@ __global__ void __launch_bounds__(256) k_fx_mp2_slices(const double* __restrict_
         const int i = s / nv, ap = s - i * nv;
         const long long ox = (long long)mm * nb * nov +
                              ((m < no) ? ((long long)ap * no + i) * nb + p : (long long)s * nb + p);
-        double x = 0.0;
-        for (int j = 0; j < nsplit; ++j) {
+        a = wbuf[o];
+        double x = xbuf[ox];
+        for (int j = 1; j < nsplit; ++j) {
           a += wbuf[j * split_stride + o];
           x += xbuf[j * split_stride + ox];
         }
