@@ -153,8 +153,9 @@ struct EigWork {
 // Workspace sizes in doubles for matrices up to n and back-transformations of
 // up to ncols (>= 64) columns at a time.
 constexpr int kMaxPanelGrid = 320;   // CTAs of the tridiagonalisation panel kernel, at most
+constexpr size_t kGridBarDoubles = 136; // the panel kernel's barrier block
 constexpr size_t eig_part_doubles(size_t n) {
-  return 2 * ((n + 31) / 32 + 1) + ((n + 31) / 32 + 1) * 128 + 128 + 2 * n * 128 + 8 +
+  return 2 * ((n + 31) / 32 + 1) + ((n + 31) / 32 + 1) * 128 + 128 + 2 * n * 128 + kGridBarDoubles +
          ((n + 63) / 64) * ((n + 63) / 64 + 1) / 2 * 64 + (size_t)kMaxPanelGrid * n + 64;
 }
 constexpr size_t eig_gk_doubles(size_t n, size_t ncols) {

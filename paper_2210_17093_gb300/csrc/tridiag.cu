@@ -45,7 +45,10 @@ struct GridBar {
   unsigned int gen;
   int abort;
   int pad;
+  unsigned int n0, n1;          // CTAs that were first on their SM, and the others
+  unsigned int sm_slot[256];    // CTAs seen per SM id (mod 256)
 };
+static_assert(sizeof(GridBar) <= kGridBarDoubles * sizeof(double), "grid barrier block");
 
 struct PanelParams {
   int n, k0, nbp, k1;
@@ -154,7 +157,6 @@ __device__ __forceinline__ double vval(const PanelParams& p, int i, int r, doubl
 __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
   __shared__ double sh[40];
   __shared__ double Wi[NBP], Vi[NBP], vtv[NBP], wtv[NBP];
-  __shared__ double dots[RT / 32][2 * NBP];
   __shared__ double tile[TB * (TB + 1)];
   __shared__ double vJ[TB], vR[TB];
   const int n = p.n, k0 = p.k0;
@@ -163,30 +165,44 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
   const int t = threadIdx.x;
   const int nrbt = (n + TB - 1) / TB;
   unsigned int epoch = 0;                 // grid barriers passed in this launch
+  // Order of the P1/P3 row chunks over the CTAs: the first CTA of every SM before any
+  // second one, so that while the chunks are fewer than the SMs no SM runs two of
+  // them (their float64 work would share one SM's float64 pipe).  Ranks come from
+  // counters in the barrier block; the order is a permutation of 0..gridDim.x-1 and
+  // takes effect after the first grid barrier, when the count of first CTAs is final.
+  __shared__ int s_rank[3];
+  if (t == 0) {
+    unsigned int sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    const unsigned int slot = atomicAdd(&p.bar->sm_slot[sm & 255u], 1u);
+    s_rank[0] = (slot == 0) ? 0 : 1;
+    s_rank[1] = (int)atomicAdd((slot == 0) ? &p.bar->n0 : &p.bar->n1, 1u);
+  }
+  int L = blockIdx.x;
 
   for (int j = 0; j < p.nbp; ++j) {
     const int i = k0 + j;
     // ---------------- P1: column update ----------------
-    double alpha_w = 0.0;
-    if (j > 0) {
-      const double s = sum_partials(p.p_wv, ceil_div_d(n - i, RC), sh);
-      alpha_w = -0.5 * ldg_cg(p.tau + i - 1) * s;
-    }
-    for (int c = t; c < j; c += blockDim.x) {
-      double w = ldg_cg(p.Wp + i + (long long)c * ld);
-      if (c == j - 1) w = ldg_cg(p.scal + 3) + alpha_w;   // W(i, j-1) before its correction; v_{i-1}(i) = 1
-      Wi[c] = w;
-      Vi[c] = ldg_cg(A + i + (long long)(k0 + c) * ld);
-    }
-    __syncthreads();
     // 32 rows per chunk, eight lanes per row share the loop over the panel's columns.
     // Besides the update, each chunk adds up V(r,:) a(r) and W(r,:) a(r) over its
     // rows r >= i+2 (a = the updated, still unscaled column): the dot products
     // V^T v and W^T v of P3 are these sums times the reflector's scale plus the
     // row i+1 terms (v(i+1) = 1).
-    const int rl = t >> 3, q8 = t & 7, wl = t >> 5;
+    const int rl = t >> 3, q8 = t & 7;
     const int n1 = ceil_div_d(n - i, RC);
-    for (int ch = blockIdx.x; ch < n1; ch += gridDim.x) {
+    double alpha_w = 0.0;
+    if (j > 0) {
+      const double s = sum_partials(p.p_wv, n1, sh);
+      alpha_w = -0.5 * ldg_cg(p.tau + i - 1) * s;
+    }
+    if (t < j) {
+      double w = ldg_cg(p.Wp + i + (long long)t * ld);
+      if (t == j - 1) w = ldg_cg(p.scal + 3) + alpha_w;   // W(i, j-1) before its correction; v_{i-1}(i) = 1
+      Wi[t] = w;
+      Vi[t] = ldg_cg(A + i + (long long)(k0 + t) * ld);
+    }
+    __syncthreads();
+    for (int ch = L; ch < n1; ch += gridDim.x) {
       const int r = i + ch * RC + rl;
       double upd = 0.0, wcorr = 0.0;
       double vs[NBP / 8], ws[NBP / 8];
@@ -216,38 +232,80 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
         if (r == i + 1) p.scal[0] = a;
         if (r >= i + 2) sq = a * a;
       }
-      // dot partials over the chunk's rows: lanes of one q8 hold 8 columns each
+      // dot partials over the chunk's rows: the chunk's rows of V and W go to shared
+      // memory (row stride 2 NBP + 1) with a(r) beside them, and two threads per column
+      // sum sixteen rows each with fused multiply-adds (a third of the float64
+      // instructions of a shuffle reduction, on a pipe that P1 otherwise saturates)
       const double aa = (r < n && r >= i + 2) ? a : 0.0;
+      double* vw = tile;                         // [RC][2 NBP + 1]
+      double* av = tile + RC * (2 * NBP + 1);    // [RC]
 #pragma unroll
       for (int k = 0; k < NBP / 8; ++k) {
-        double dv = vs[k] * aa, dw = ws[k] * aa;
-        dv += __shfl_xor_sync(0xffffffffu, dv, 8);
-        dv += __shfl_xor_sync(0xffffffffu, dv, 16);
-        dw += __shfl_xor_sync(0xffffffffu, dw, 8);
-        dw += __shfl_xor_sync(0xffffffffu, dw, 16);
-        if ((t & 31) < 8) {
-          dots[wl][q8 + 8 * k] = dv;
-          dots[wl][NBP + q8 + 8 * k] = dw;
-        }
+        vw[rl * (2 * NBP + 1) + q8 + 8 * k] = vs[k];
+        vw[rl * (2 * NBP + 1) + NBP + q8 + 8 * k] = ws[k];
       }
-      const double s = blk_reduce_sum(sq, sh);   // includes a __syncthreads after the dots
+      if (q8 == 0) av[rl] = aa;
+      const double s = blk_reduce_sum(sq, sh);   // its __syncthreads publish vw and av
       if (t == 0) p.p_ss[ch] = s;
-      for (int c = t; c < 2 * j; c += blockDim.x) {
-        const int col = (c < j) ? c : NBP + (c - j);
+      {
+        const int c = t >> 1, hf = t & 1;
         double d2 = 0.0;
+        if (c < 2 * j) {
+          const int col = (c < j) ? c : NBP + (c - j);
 #pragma unroll
-        for (int w8 = 0; w8 < RT / 32; ++w8) d2 += dots[w8][col];
-        p.p_vw[(long long)ch * (2 * NBP) + c] = d2;
+          for (int k = 0; k < RC / 2; ++k) {
+            const int row = hf * (RC / 2) + k;
+            d2 = fma(vw[row * (2 * NBP + 1) + col], av[row], d2);
+          }
+        }
+        d2 += __shfl_xor_sync(0xffffffffu, d2, 1);
+        if (c < 2 * j && hf == 0) p.p_vw[(long long)ch * (2 * NBP) + c] = d2;
       }
       __syncthreads();
     }
     if (!grid_sync(p.bar, p.status, epoch)) return;
+    if (j == 0) {
+      if (t == 0) s_rank[2] = (s_rank[0] == 0) ? s_rank[1] : (int)ld_acquire(&p.bar->n0) + s_rank[1];
+      __syncthreads();
+      L = s_rank[2];
+    }
 
     // ---------------- P2: reflector and y = A22 v ----------------
-    const Refl h = householder(p, i, sh);
     const int lo = i + 1;
     const int rb0 = lo / TB;
     const int nrb = nrbt - rb0;
+    // The stored (lower and diagonal) tiles of A22 in row-major order (R, J <= R),
+    // split into equal contiguous ranges.  Each tile is read once and used twice:
+    // y_R += A_RJ v_J (accumulated per thread along the row, stored per CTA and row
+    // block) and, below the diagonal, y_J += A_RJ^T v_R (reduced over the four lanes
+    // that share a column, stored per tile).
+    const long long T = (long long)nrb * (nrb + 1) / 2;
+    const long long f0 = (long long)blockIdx.x * T / gridDim.x;
+    const long long f1 = (long long)(blockIdx.x + 1) * T / gridDim.x;
+    const int rr = t % TB, cq = t / TB;
+    double nxt[16];
+    double vraw = 0.0;
+    // (R, J) of the first tile of the range: R - rb0 = the largest a with a(a+1)/2 <= f0
+    // (integer search; later tiles advance J, then R).  Its elements, and the raw
+    // column entries behind v_J, are loaded before the reflector's norm is summed.
+    int R0 = rb0, J0 = rb0;
+    if (f0 < f1) {
+      long long a = 0;
+      while ((a + 1) * (a + 2) / 2 <= f0) ++a;
+      R0 = rb0 + (int)a;
+      J0 = rb0 + (int)(f0 - a * (a + 1) / 2);
+      const int gr = R0 * TB + rr;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int gc = J0 * TB + cq + 4 * k;
+        nxt[k] = (gr < n && gc < n) ? ldg_cg(A + gr + (long long)gc * ld) : 0.0;
+      }
+      if (t < TB) {
+        const int r = J0 * TB + t;
+        if (r >= lo && r < n && r != i + 1) vraw = ldg_cg(A + r + (long long)i * ld);
+      }
+    }
+    const Refl h = householder(p, i, sh);
     {
       // V^T v = V(i+1,:) + scale * (sum over the P1 chunks), the same for W^T v:
       // the first CTAs finish these 2j sums (one warp per value) for P3
@@ -263,27 +321,12 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
         }
       }
     }
-    // The stored (lower and diagonal) tiles of A22 in row-major order (R, J <= R),
-    // split into equal contiguous ranges.  Each tile is read once and used twice:
-    // y_R += A_RJ v_J (accumulated per thread along the row, stored per CTA and row
-    // block) and, below the diagonal, y_J += A_RJ^T v_R (reduced over the four lanes
-    // that share a column, stored per tile).
-    const long long T = (long long)nrb * (nrb + 1) / 2;
-    const long long f0 = (long long)blockIdx.x * T / gridDim.x;
-    const long long f1 = (long long)(blockIdx.x + 1) * T / gridDim.x;
     if (f0 < f1) {
-      const int rr = t % TB, cq = t / TB;
       const int x = t >> 2, q = t & 3;          // row / column x of the tile, quarter q of the other index
-      double nxt[16];
       double vnxt = 0.0;
-      // (R, J) of the first tile of the range: R - rb0 = the largest a with a(a+1)/2 <= f0
-      // (integer search; later tiles advance J, then R)
-      int R0 = rb0, J0 = rb0;
-      {
-        long long a = 0;
-        while ((a + 1) * (a + 2) / 2 <= f0) ++a;
-        R0 = rb0 + (int)a;
-        J0 = rb0 + (int)(f0 - a * (a + 1) / 2);
+      if (t < TB) {
+        const int r = J0 * TB + t;
+        vnxt = (r == i + 1) ? 1.0 : ((r >= lo && r < n) ? vraw * h.scale : 0.0);   // vval of the first tile
       }
       auto load_tile = [&](int R, int J) {
         const int gr = R * TB + rr;
@@ -297,7 +340,6 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
           vnxt = (r >= lo && r < n) ? vval(p, i, r, h.scale) : 0.0;
         }
       };
-      load_tile(R0, J0);
       double acc = 0.0;          // y_R partial of row x, this thread's column quarter
       int Rcur = -1;
       int R = R0, J = J0;
@@ -349,13 +391,13 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
     if (!grid_sync(p.bar, p.status, epoch)) return;
 
     // ---------------- P3: W column ----------------
+    const int n3 = ceil_div_d(n - i - 1, RC);
     for (int c = t; c < 2 * j; c += blockDim.x) {
       const double v = ldg_cg(p.vwf + c);
       if (c < j) vtv[c] = v; else wtv[c - j] = v;
     }
     __syncthreads();
-    const int n3 = ceil_div_d(n - i - 1, RC);
-    for (int ch = blockIdx.x; ch < n3; ch += gridDim.x) {
+    for (int ch = L; ch < n3; ch += gridDim.x) {
       const int r = lo + ch * RC + rl;
       double y = 0.0;
       if (r < n) {
@@ -477,7 +519,7 @@ void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
   p.vwf = base;    base += 2 * NBP;
   p.VW = base;     base += (long long)n * 2 * NBP;
   p.WV = base;     base += (long long)n * 2 * NBP;
-  p.bar = reinterpret_cast<GridBar*>(base);   base += 2;
+  p.bar = reinterpret_cast<GridBar*>(base);   base += kGridBarDoubles;
   p.p_t = base;    base += (long long)nrbt * (nrbt + 1) / 2 * TB;
   p.p_y = base;
   // Concurrent lanes each take a share of the co-resident CTAs, so that the
