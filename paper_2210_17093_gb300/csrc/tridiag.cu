@@ -121,6 +121,22 @@ __device__ __forceinline__ double blk_reduce_sum(double v, double* sh) {
   return s;  // valid in thread 0
 }
 
+// Sum over a chunk's rows of values held by the lanes with (thread & 7) == 0 (four per
+// warp, the rest zero): two shuffle steps per warp, eight warp sums in thread 0, where
+// the result is valid.  Two __syncthreads, like blk_reduce_sum.
+__device__ __forceinline__ double chunk_rows_sum(double v, double* sh) {
+  v += __shfl_xor_sync(0xffffffffu, v, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 16);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+  return s;
+}
+
 // Sum of `cnt` partials, the same value and order in every thread of every CTA.
 __device__ double sum_partials(const double* p, int cnt, double* sh) {
   double v = 0.0;
@@ -245,7 +261,7 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
         vw[rl * (2 * NBP + 1) + NBP + q8 + 8 * k] = ws[k];
       }
       if (q8 == 0) av[rl] = aa;
-      const double s = blk_reduce_sum(sq, sh);   // its __syncthreads publish vw and av
+      const double s = chunk_rows_sum(sq, sh);   // its __syncthreads publish vw and av
       if (t == 0) p.p_ss[ch] = s;
       {
         const int c = t >> 1, hf = t & 1;
@@ -412,7 +428,7 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
           if ((long long)c * T / gridDim.x == (long long)(c + 1) * T / gridDim.x) continue;
           y += ldg_cg(p.p_y + (long long)c * n + r);
         }
-#pragma unroll 4
+#pragma unroll 8
         for (int R2 = Rr + 1 + q8; R2 < nrbt; R2 += 8) {
           const long long ft = (long long)(R2 - rb0) * (R2 - rb0 + 1) / 2 + a;
           y += ldg_cg(p.p_t + ft * TB + (r - Rr * TB));
@@ -435,7 +451,7 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
         part = w * v;
         if (r >= i + 2) A[r + (long long)i * ld] = v;
       }
-      const double s = blk_reduce_sum(part, sh);
+      const double s = chunk_rows_sum(part, sh);
       if (t == 0) p.p_wv[ch] = s;
     }
     if (blockIdx.x == 0 && t == 0) {
