@@ -14,22 +14,26 @@ ETA = sy.ETA
 @pytest.mark.parametrize("nb,no,na,seed", [(24, 5, 72, 0), (71, 13, 150, 2), (40, 1, 90, 7)])
 def test_g0w0_against_oracle(prec, nb, no, na, seed):
     """(a)-(c) in float64 at both precisions and the residues in float64: float64
-    tolerances.  The energy bar is 1e-8 Ha, or ten times the spread of the oracle's own
-    result under 2-ulp changes of its input energies when that is larger (Z_p reaches
-    0.002 here: Sigma'_pp ~ 400 next to a pole)."""
+    tolerances.  The bars for eps^QP (1e-8 Ha) and Z (1e-8) widen to ten times the
+    spread of the oracle's own result under 2-ulp changes of its input energies when
+    that is larger.  Next to a pole Z_p = 1 / (1 - Sigma'_pp) reaches 0.002 (Sigma'_pp ~
+    400, and d Sigma'/d Omega ~ w^2 / eta^3), so rounding-level changes of Omega move
+    Z by ~1e-9."""
     m = sy.molecule(nb, no, na, seed)
     r = qsgw.g0w0_pass(m["L"], m["eps"], m["C"], no, ETA)
-    spread = 0.0
+    spread = spread_z = 0.0
     for k in range(3):
         rng = np.random.default_rng(k)
         ep = m["eps"] * (1.0 + 4.4e-16 * rng.choice([-1.0, 1.0], m["eps"].shape))
-        spread = max(spread, np.max(np.abs(qsgw.g0w0_pass(m["L"], ep, m["C"], no, ETA)["eps_qp"] - r["eps_qp"])))
+        rp = qsgw.g0w0_pass(m["L"], ep, m["C"], no, ETA)
+        spread = max(spread, np.max(np.abs(rp["eps_qp"] - r["eps_qp"])))
+        spread_z = max(spread_z, np.max(np.abs(rp["Z"] - r["Z"])))
     with lib_context(precision=prec) as ctx:
         load_mol(ctx, 0, m)
         e, z, s = np.empty(nb), np.empty(nb), np.empty(nb)
         ctx.g0w0(0, e, z, s)
     assert np.max(np.abs(s - r["sigma_c_diag"])) <= 1e-10 * np.max(np.abs(r["sigma_c_diag"]))
-    assert np.max(np.abs(z - r["Z"])) < 1e-9
+    assert np.max(np.abs(z - r["Z"])) < max(1e-8, 10.0 * spread_z), spread_z
     assert np.max(np.abs(e - r["eps_qp"])) < max(1e-8, 10.0 * spread), spread
 
 
