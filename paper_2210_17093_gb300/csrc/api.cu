@@ -3,6 +3,8 @@
 
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "stages.cuh"
 
 using namespace molgw;
@@ -316,6 +318,14 @@ int lane_fit(molgw_ctx c, Lane& l, const MolBuf& m) {
   return r;
 }
 
+// An NVTX range over one stage of a pass (shown by Nsight tools; free without one).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+
 // Run the pass of one molecule on lane l up to a stage: 'b' (M), 'c' (rpa),
 // 'e' (sigma), 'f' (qs step).
 int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
@@ -338,6 +348,7 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
     tb.L = c->tcb[mol].L;
   }
   if (!m.b_valid) {
+    Range rg("(a) ri_mo_transform");
     if (tc_ab && use_fx(c)) {
       r = stage_ri_mo_transform_fx(ex, m, c->tcb[mol].Lfx, l.tco_base);
       if (r) return r;
@@ -350,12 +361,14 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
     m.b_valid = m.have_b = true;
   }
   if (!m.h_ready) {
+    Range rg("J, Sigma_x, h_MO");
     stage_j_sigx(ex, m, l.scr);
     derive_h_from_hf(ex, m);
     m.jx_valid = m.have_jx = true;
     m.h_ready = true;
   }
   if (upto == 'b') {
+    Range rg("(b) rpa_build");
     if (tc_ab && use_fx(c)) {
       r = stage_rpa_build_fx(ex, m, l.tco_base);
       if (r) return r;
@@ -369,20 +382,25 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
     return launch_status();
   }
   if (!m.rpa_valid && !mp2) {
-    if (tc_ab && use_fx(c)) {
-      r = stage_rpa_build_fx(ex, m, l.tco_base);
-      if (r) return r;
-    } else if (tc_ab) {
-      r = stage_rpa_build_tc(ex, m, tb);
-      if (r) return r;
-    } else {
-      stage_rpa_build(ex, m);
+    {
+      Range rg("(b) rpa_build");
+      if (tc_ab && use_fx(c)) {
+        r = stage_rpa_build_fx(ex, m, l.tco_base);
+        if (r) return r;
+      } else if (tc_ab) {
+        r = stage_rpa_build_tc(ex, m, tb);
+        if (r) return r;
+      } else {
+        stage_rpa_build(ex, m);
+      }
     }
+    Range rg("(c) rpa_eigensolve");
     stage_rpa_eigensolve(ex, m, l.eig, l.scr, full);
     m.rpa_valid = m.have_rpa = true;
   }
   if (upto == 'g') {
     // one-shot G0W0 from the current orbitals; they stay current
+    Range rg("G0W0");
     if (!m.jx_valid) {
       stage_j_sigx(ex, m, l.scr);
       m.jx_valid = m.have_jx = true;
@@ -393,6 +411,7 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
     return launch_status();
   }
   if (upto >= 'e' && !m.sigma_valid) {
+    Range rg(mp2 ? "(d)+(e) qsMP2 self-energy" : "(d)+(e) gw_residues, sigma_assembly");
     if (!m.jx_valid) {
       stage_j_sigx(ex, m, l.scr);
       m.jx_valid = m.have_jx = true;
@@ -414,6 +433,7 @@ int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
     m.sigma_valid = m.have_sigma = true;
   }
   if (upto == 'f') {
+    Range rg("(f) qs_update");
     stage_qs_update(ex, m, l.eig, l.scr);
     m.b_valid = m.jx_valid = m.rpa_valid = m.sigma_valid = false;
   }
