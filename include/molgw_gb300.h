@@ -189,6 +189,13 @@ int molgw_b200_g0w0_window(molgw_ctx ctx, int mol, int p_begin, int p_end, doubl
  * cleared). */
 int molgw_b200_sync(molgw_ctx ctx);
 
+/* Test hook for the error paths: latches `code` (MOLGW_E_TIMEOUT, MOLGW_E_NOCONV or
+ * MOLGW_E_NUMERIC, the codes device-side checks raise) into the context's status
+ * word from a one-thread kernel on the context stream, as a bounded wait that ran
+ * out would; the next synchronising call returns it and clears it.  No device fault
+ * is made and no kernel is stopped.  MOLGW_E_ARG for any other code. */
+int molgw_b200_inject_fault(molgw_ctx ctx, int code);
+
 /* Copy an intermediate of the last pass of molecule `mol` into out[count]
  * (count must equal the item's size).  Items: */
 enum molgw_item {

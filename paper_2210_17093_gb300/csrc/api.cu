@@ -114,6 +114,9 @@ int copy_out(molgw_ctx c, double* dst, const double* src, size_t n, bool* need_s
   return cuda_status(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, c->st));
 }
 
+// Latches a device-detected error code the way the kernels' checks do (test hook).
+__global__ void k_inject_status(int* status, int code) { set_status(status, code); }
+
 int read_status(molgw_ctx c) {
   cudaError_t e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return MOLGW_E_CUDA;
@@ -885,6 +888,13 @@ int molgw_b200_sync(molgw_ctx c) {
   if (!c) return MOLGW_E_ARG;
   DeviceGuard g(c->device);
   return read_status(c);
+}
+
+int molgw_b200_inject_fault(molgw_ctx c, int code) {
+  if (!c || (code != MOLGW_E_TIMEOUT && code != MOLGW_E_NOCONV && code != MOLGW_E_NUMERIC)) return MOLGW_E_ARG;
+  DeviceGuard g(c->device);
+  k_inject_status<<<1, 1, 0, c->st>>>(c->d_status, code);
+  return launch_status();
 }
 
 int molgw_b200_fetch(molgw_ctx c, int mol, int item, double* out, size_t count) {

@@ -39,7 +39,7 @@ EXPORTS = ["molgw_b200_create", "molgw_b200_set_ri", "molgw_b200_set_orbitals", 
            "molgw_b200_launch_count", "molgw_b200_set_timing", "molgw_b200_destroy",
            "molgw_b200_status_string", "molgw_b200_eigh_noalloc", "molgw_b200_graph_replays",
            "molgw_b200_tc_gemm", "molgw_b200_autotune", "molgw_b200_lanes", "molgw_b200_g0w0",
-           "molgw_b200_g0w0_window"]
+           "molgw_b200_g0w0_window", "molgw_b200_inject_fault"]
 NOALLOC_NMAX = 256
 
 
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "molgw_b200_g0w0": ([vp, ip, dp, dp, dp], ip),
         "molgw_b200_g0w0_window": ([vp, ip, ip, ip, dp, dp, dp], ip),
         "molgw_b200_sync": ([vp], ip),
+        "molgw_b200_inject_fault": ([vp, ip], ip),
         "molgw_b200_fetch": ([vp, ip, ip, dp, sz], ip),
         "molgw_b200_rpa_matrix": ([vp, ip, dp], ip),
         "molgw_b200_eigh": ([vp, ip, dp, dp, dp], ip),
@@ -205,6 +206,10 @@ class Context:
 
     def sync(self):
         _check(self._lib.molgw_b200_sync(self._hh()), "sync")
+
+    def inject_fault(self, code: int):
+        """Latch a device-side error code (test hook; see molgw_b200_inject_fault)."""
+        _check(self._lib.molgw_b200_inject_fault(self._hh(), code), "inject_fault")
 
     def fetch(self, mol: int, item: str, out):
         n = out.size if isinstance(out, np.ndarray) else out.numel()
