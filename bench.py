@@ -549,7 +549,7 @@ def run_batch(args):
     import torch
 
     world, rank, local, dist = dist_setup()
-    from paper_2210_17093_gb300 import FLAG_GRAPH, FLAG_TC_AB, Context
+    from paper_2210_17093_gb300 import FLAG_EIG_TC, FLAG_GRAPH, FLAG_TC_AB, Context
 
     torch.cuda.set_device(local)
     seeds = batch_seeds(rank)
@@ -562,7 +562,7 @@ def run_batch(args):
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     host = [(pin(m["L"]), pin(m["eps"]), pin(m["C"])) for m in mols]
     prec = args.batch_precision
-    flags = FLAG_GRAPH | (FLAG_TC_AB if prec != "fp64" else 0)
+    flags = FLAG_GRAPH | (FLAG_TC_AB if prec != "fp64" else 0) | (0 if args.batch_no_eig_tc else FLAG_EIG_TC)
     with Context(precision=prec, device=local, eta=sy.ETA, stream=st, max_mols=len(mols),
                  flags=flags, lanes=0) as ctx:
         def load():
@@ -625,7 +625,9 @@ def run_batch(args):
                                f"{min(nbs)}..{max(nbs)} (U{{40..160}}), n_occ = round(n_basis/5), n_aux = 3 n_basis, "
                                f"seeds {seeds[0]}..{seeds[-1]}; one qs_step(-1) per step on autotuned lanes, "
                                f"graph replay", "molecules": len(mols), "precision": prec,
-                   "stages_on_tensor_cores": "(a), (b), (d), (e)" if prec != "fp64" else "none", "eta_ha": sy.ETA,
+                   "stages_on_tensor_cores": ("(a), (b), (d), (e)" if prec != "fp64" else "none")
+                   + ("; the eigensolvers' SYR2K and back-transformation GEMMs on 7-digit fixed point "
+                      "(float64 accuracy)" if flags & FLAG_EIG_TC else ""), "eta_ha": sy.ETA,
                    "l2": "inputs larger than L2 (RI factors and Casida matrices of 64 molecules, ~10 GB)"},
         "tflops": sum(flops.values()) / (t_max / args.steps) / 1e12,
         "gpu_launches": int(launches), "graph_replays": int(replays), "autotuned_lanes": tuned_lanes,
@@ -673,6 +675,8 @@ def main():
                     help="precision of the split-precision path reported under 'mixed'")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-mp2", action="store_true", help="skip the qsMP2 line item")
+    ap.add_argument("--batch-no-eig-tc", action="store_true",
+                    help="workload D: keep the eigensolvers' trailing updates in float64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -162,3 +162,23 @@ def test_bf16x10_tc_ab_lanes_match_solo():
     hist, _, _ = run_batch(mols, precision="bf16x10", flags=FLAG_TC_AB)
     for k, m in enumerate(mols):
         assert np.max(np.abs(hist[0][k]["eps"] - solo(m))) < 1e-7, k
+
+
+def test_bf16x10_eig_tc_batch_graph_matches_solo():
+    """The batch configuration of the bench: fixed point for (a), (b), (d), (e), the
+    eigensolvers' trailing updates on the 7-digit engine, autotuned lanes, graph replay,
+    against solo runs of each molecule (three steps)."""
+    from paper_2210_17093_gb300 import FLAG_EIG_TC, FLAG_GRAPH, FLAG_TC_AB
+    mols = [sy.batch_molecule(s) for s in (100, 105, 108, 122, 131)]
+    flags = FLAG_TC_AB | FLAG_EIG_TC
+
+    def solo(m):
+        with lib_context(stream=None, precision="bf16x10", eta=sy.ETA, flags=flags) as ctx:
+            load_mol(ctx, 0, m, device=False)
+            ctx.qs_step(0)
+            return fetch(ctx, 0, m, "eps")
+
+    hist, _, replays = run_batch(mols, precision="bf16x10", flags=flags | FLAG_GRAPH, steps=3)
+    assert replays >= 1
+    for k, m in enumerate(mols):
+        assert np.max(np.abs(hist[0][k]["eps"] - solo(m))) < 1e-7, k
