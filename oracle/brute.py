@@ -97,6 +97,36 @@ def singlet_residues_spin_orbital(L, C, eps, n_occ, tol=1e-8):
     return np.array(sing_O), np.array(sing_w), np.array(trip_O)
 
 
+def casida_spin_orbital_open(L: np.ndarray, Cs, epss, n_occs):
+    """Full non-Hermitian Casida problem of Eq. (Casida.AB.XY) over spin orbitals with
+    one set of MOs per spin: rows/columns (i, a, s), spin up first.
+
+    A = (e_a^s - e_i^s) delta + (i a s|j b s'), B = (i a s|b j s'), the integrals
+    (pq s|rt s') = sum C^s C^s C^s' C^s' (mu nu|la ta) by the four-index transformation
+    of Eq. (AO.to.MO) with the "+" Coulomb sign (reading R1).
+    Returns eigenvalues ascending.
+    """
+    g = eri_ao(L)
+    gmo = {}
+    for s1 in (0, 1):
+        for s2 in (0, 1):
+            x = np.einsum("mp,mnlt->pnlt", Cs[s1], g)
+            x = np.einsum("nq,pnlt->pqlt", Cs[s1], x)
+            x = np.einsum("lr,pqlt->pqrt", Cs[s2], x)
+            gmo[s1, s2] = np.einsum("ts,pqrt->pqrs", Cs[s2], x)
+    nb = Cs[0].shape[0]
+    idx = [(i, a, s) for s in (0, 1) for i in range(n_occs[s]) for a in range(n_occs[s], nb)]
+    n = len(idx)
+    A = np.zeros((n, n))
+    Bm = np.zeros((n, n))
+    for u, (i, a, s) in enumerate(idx):
+        for v, (j, b, sp) in enumerate(idx):
+            A[u, v] = gmo[s, sp][i, a, j, b] + ((epss[s][a] - epss[s][i]) if u == v else 0.0)
+            Bm[u, v] = gmo[s, sp][i, a, b, j]
+    vals = np.linalg.eigvals(np.block([[A, Bm], [-Bm, -A]]))
+    return np.sort(vals.real)
+
+
 def sigma_c_loops(w, eps, Omega, n_occ, eta, omega_rows=True):
     """Re Sigma_c,pq(eps_p) by four nested loops over p, q, m, s (Eq. Sigma.c.GW)."""
     nb = eps.shape[0]

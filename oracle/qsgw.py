@@ -393,6 +393,74 @@ def qsmp2_iterations(L, eps, C, n_occ, eta, n_iter, h_mo=None) -> list:
     return out
 
 
+# ----------------------------------------------------------------------------
+# Open shell: the sigma-resolved equations of Sec. II (GEP, H, J, D, K,
+# Casida.AB.XY, Casida.A/B, w.residue, Sigma.c.GW) with one set of orbitals per spin
+# ----------------------------------------------------------------------------
+def casida_M_open(Bs, epss, n_occs):
+    """M = D^(1/2) (A + B) D^(1/2) over the transitions of both spins, up first.
+
+    Eqs. (Casida.A/B) with spins written out: A_{t s, u s'} = D_t delta + (t s|u s'),
+    B_{t s, u s'} = (t s|u s') ("+" sign, reading R1), so A - B = diag(D) and
+    M = D^2 + 2 D^(1/2) K D^(1/2) with K_{t s, u s'} = sum_P B^{P s}_t B^{P s'}_u.
+    Returns (M, D, Bt [na, n_ov_up + n_ov_dn]).
+    """
+    Dl, Bl = [], []
+    for B, eps, no in zip(Bs, epss, n_occs):
+        i, a = transitions(eps.shape[0], no)
+        Dl.append(eps[a] - eps[i])
+        Bl.append(B[:, i, a])
+    D = np.concatenate(Dl)
+    Bt = np.concatenate(Bl, axis=1)
+    K = Bt.T @ Bt
+    sq = np.sqrt(D)
+    return np.diag(D * D) + 2.0 * sq[:, None] * K * sq[None, :], D, Bt
+
+
+def rpa_eigensolve_open(M: np.ndarray, D: np.ndarray):
+    """Omega ascending and X + Y = D^(1/2) Z Omega^(-1/2) (no spin factor: the sum over
+    sigma' of Eq. (w.residue) runs over the spin-resolved transitions themselves)."""
+    lam, Z = np.linalg.eigh(M)
+    if lam[0] <= 0.0:
+        raise FloatingPointError("RPA instability: M has a non-positive eigenvalue")
+    Z = fix_gauge(Z)
+    Omega = np.sqrt(lam)
+    return Omega, np.sqrt(D)[:, None] * Z / np.sqrt(Omega)[None, :], Z
+
+
+def hartree_open(B: np.ndarray, Bs, n_occs) -> np.ndarray:
+    """J_pq in the basis of B's orbitals: sum_P B^P_pq sum_{s} sum_{i in occ s} B^{P s}_ii (Eq. J)."""
+    rho = sum(np.einsum("Pii->P", Bx[:, :no, :no]) for Bx, no in zip(Bs, n_occs))
+    return np.einsum("Ppq,P->pq", B, rho, optimize=True)
+
+
+def qsgw_pass_open(L, epss, Cs, n_occs, eta, h_mos=None) -> dict:
+    """One open-shell RI-qsGW iteration; epss, Cs, n_occs, h_mos are (up, down) pairs.
+
+    Per spin s: B^s = C^sT L C^s; the spin-resolved Casida problem (casida_M_open);
+    w^{v}_{pq s} = sum_P B^{P s}_pq R_Pv with R = Bt (X+Y); Sigma_c^s from Eq.
+    (Sigma.c.GW) with the spin-s energies and occupations, made static by Eq.
+    (Sigma.c.qsGW.real); Sigma_x^s = -sum_{i in occ s} (p i s|i q s); J from both
+    spins; H^s = h^s + J^s + Sigma_x^s + Sigma_c^s (Eqs. H, GEP).  h^s defaults to
+    the HF reading R5 applied per spin.
+    """
+    Bs = [ri_mo_transform(L, C) for C in Cs]
+    M, D, Bt = casida_M_open(Bs, epss, n_occs)
+    Omega, XpY, Z = rpa_eigensolve_open(M, D)
+    R = Bt @ XpY
+    out = {"Omega": Omega, "D": D, "M": M, "XpY": XpY, "R": R, "spin": []}
+    for k, (B, eps, C, no) in enumerate(zip(Bs, epss, Cs, n_occs)):
+        w = np.einsum("Ppq,Ps->spq", B, R, optimize=True)
+        Sx = sigma_x(B, no)
+        J = hartree_open(B, Bs, n_occs)
+        h = h_mos[k] if h_mos is not None else np.diag(eps) - J - Sx
+        Sc = sigma_c_qs(sigma_c_rows(w, eps, Omega, no, eta))
+        eps_new, C_new, h_new, U = qs_update(h, J, Sx, Sc, C)
+        out["spin"].append({"B": B, "w": w, "sigma_x": Sx, "sigma_c": Sc, "J": J, "h_mo": h,
+                            "eps_new": eps_new, "C_new": C_new, "h_mo_new": h_new})
+    return out
+
+
 def qsgw_iterations(L, eps, C, n_occ, eta, n_iter, h_mo=None) -> list:
     """n_iter successive qsGW iterations, each starting from the previous (eps', C')."""
     out = []
