@@ -33,6 +33,9 @@ the design notes with its justification):
   R12 G0W0 (the diagonal m = n of Eq. (Sigma.c.GW)): the quasiparticle
       equation is solved to first order around eps_p (renormalisation factor Z_p),
       starting from the input mean field whose potential is v = diag(eps) - h - J.
+  R13 Open shell: reading R1 for every spin pair of the spin-resolved Casida
+      problem (A = D + K, B = K), so X + Y = D^(1/2) Z Omega^(-1/2) with no spin
+      factor; h spin independent, read per spin from its HF solution when absent.
 """
 from __future__ import annotations
 

@@ -99,6 +99,17 @@ double* dalloc(std::vector<void*>& v, size_t n_doubles, int* err) {
   return (double*)p;
 }
 
+void free_all(std::vector<void*>& v);
+
+// Release the spin-down channel of an open-shell molecule (if any).
+void drop_open(MolBuf& m) {
+  if (!m.dn) return;
+  free_all(m.dn->ri_allocs);
+  free_all(m.dn->orb_allocs);
+  m.dn.reset();
+  m.nov_up = 0;
+}
+
 void free_all(std::vector<void*>& v) {
   for (void* p : v) cudaFree(p);
   v.clear();
@@ -329,11 +340,72 @@ struct Range {
   Range& operator=(const Range&) = delete;
 };
 
+// Open shell (float64): both spin channels through (a), J, Sigma_x and h; one RPA over
+// the transitions of both spins (up first); (d)+(e) and (f) per channel, the
+// spin-down channel reading R and Omega of the spin-up MolBuf.
+int run_pass_open(molgw_ctx c, Lane& l, int mol, char upto) {
+  MolBuf& m = c->mols[mol];
+  MolBuf& d = *m.dn;
+  if (upto == 'g') return MOLGW_E_STATE;   // G0W0 is closed-shell only
+  int r = lane_fit(c, l, m);
+  if (r) return r;
+  Exec& ex = l.ex;
+  if (!m.b_valid) {
+    Range rg("(a) ri_mo_transform, both spins");
+    stage_ri_mo_transform(ex, m);
+    stage_ri_mo_transform(ex, d);
+    m.b_valid = m.have_b = true;
+  }
+  if (!m.h_ready) {
+    Range rg("J, Sigma_x, h_MO, both spins");
+    stage_j_sigx(ex, m, l.scr, &d);
+    stage_j_sigx(ex, d, l.scr, &m);
+    derive_h_from_hf(ex, m);
+    derive_h_from_hf(ex, d);
+    m.jx_valid = m.have_jx = true;
+    m.h_ready = true;
+  }
+  if (upto == 'b') {
+    Range rg("(b) rpa_build");
+    stage_rpa_build(ex, m);
+    m.rpa_valid = false;
+    return launch_status();
+  }
+  if (!m.rpa_valid) {
+    {
+      Range rg("(b) rpa_build");
+      stage_rpa_build(ex, m);
+    }
+    Range rg("(c) rpa_eigensolve");
+    stage_rpa_eigensolve(ex, m, l.eig, l.scr, false);
+    m.rpa_valid = m.have_rpa = true;
+  }
+  if (upto >= 'e' && !m.sigma_valid) {
+    Range rg("(d)+(e) gw_residues, sigma_assembly, both spins");
+    if (!m.jx_valid) {
+      stage_j_sigx(ex, m, l.scr, &d);
+      stage_j_sigx(ex, d, l.scr, &m);
+      m.jx_valid = m.have_jx = true;
+    }
+    stage_sigma(ex, m, l.scr, c->opts.eta);
+    stage_sigma(ex, d, l.scr, c->opts.eta);
+    m.sigma_valid = m.have_sigma = true;
+  }
+  if (upto == 'f') {
+    Range rg("(f) qs_update, both spins");
+    stage_qs_update(ex, m, l.eig, l.scr);
+    stage_qs_update(ex, d, l.eig, l.scr);
+    m.b_valid = m.jx_valid = m.rpa_valid = m.sigma_valid = false;
+  }
+  return launch_status();
+}
+
 // Run the pass of one molecule on lane l up to a stage: 'b' (M), 'c' (rpa),
 // 'e' (sigma), 'f' (qs step).
 int run_pass(molgw_ctx c, Lane& l, int mol, char upto) {
   MolBuf& m = c->mols[mol];
   if (!m.have_ri || !m.have_orb) return MOLGW_E_STATE;
+  if (m.dn) return run_pass_open(c, l, mol, upto);
   const bool mp2 = use_mp2(c);
   if (mp2 && (upto < 'e' || upto == 'g')) return MOLGW_E_STATE;   // qsMP2 has no RPA stages
   const bool full = (c->opts.flags & MOLGW_FLAG_FULL_XPY) != 0;
@@ -696,6 +768,14 @@ int molgw_b200_set_ri(molgw_ctx c, int mol, int n_basis, int n_aux, const double
   m.b_valid = m.jx_valid = m.rpa_valid = m.sigma_valid = false;
   m.have_b = m.have_rpa = m.have_jx = m.have_sigma = m.have_g0w0 = false;
   m.h_ready = false;
+  if (m.dn) {
+    cudaStreamSynchronize(c->st);
+    ++c->gen;
+    drop_open(m);
+    free_all(m.orb_allocs);
+    m.eps = nullptr;
+    m.alloc_no = 0;
+  }
   if (m.ri_allocs.empty() || m.nb != n_basis || m.na != n_aux) {
     cudaStreamSynchronize(c->st);
     ++c->gen;
@@ -742,9 +822,10 @@ int molgw_b200_set_orbitals(molgw_ctx c, int mol, int n_occ, const double* eps, 
   if (n_occ < 1 || n_occ >= nb) return MOLGW_E_ARG;
   const long long nov = (long long)n_occ * (nb - n_occ);
   const bool full = (c->opts.flags & MOLGW_FLAG_FULL_XPY) != 0;
-  if (m.orb_allocs.empty() || m.alloc_no != n_occ) {
+  if (m.orb_allocs.empty() || m.alloc_no != n_occ || m.dn) {
     cudaStreamSynchronize(c->st);
     ++c->gen;
+    drop_open(m);
     free_all(m.orb_allocs);
     m.have_orb = false;
     int err = 0;
@@ -794,6 +875,99 @@ int molgw_b200_set_orbitals(molgw_ctx c, int mol, int n_occ, const double* eps, 
   return launch_status();
 }
 
+int molgw_b200_set_orbitals_open(molgw_ctx c, int mol, int n_occ_up, int n_occ_dn, const double* eps_up,
+                                 const double* eps_dn, const double* C_up, const double* C_dn,
+                                 const double* h_core) {
+  if (!mol_ok(c, mol) || !eps_up || !eps_dn || !C_up || !C_dn) return MOLGW_E_ARG;
+  if (c->opts.precision != MOLGW_PREC_FP64 || (c->opts.flags & (MOLGW_FLAG_QSMP2 | MOLGW_FLAG_FULL_XPY)))
+    return MOLGW_E_ARG;
+  DeviceGuard g(c->device);
+  MolBuf& m = c->mols[mol];
+  if (!m.have_ri) return MOLGW_E_STATE;
+  const int nb = m.nb, na = m.na;
+  if (n_occ_up < 0 || n_occ_dn < 0 || n_occ_up >= nb || n_occ_dn >= nb || n_occ_up + n_occ_dn < 1)
+    return MOLGW_E_ARG;
+  const long long nov_up = (long long)n_occ_up * (nb - n_occ_up);
+  const long long nov = nov_up + (long long)n_occ_dn * (nb - n_occ_dn);
+  const int key = -(1 + n_occ_up * 65536 + n_occ_dn);    // allocation key of this occupation pair
+  const size_t nn = (size_t)nb * nb;
+  if (m.orb_allocs.empty() || m.alloc_no != key || !m.dn) {
+    cudaStreamSynchronize(c->st);
+    ++c->gen;
+    drop_open(m);
+    free_all(m.orb_allocs);
+    m.have_orb = false;
+    int err = 0;
+    m.eps = dalloc(m.orb_allocs, nb, &err);
+    m.C = dalloc(m.orb_allocs, nn, &err);
+    m.hmo = dalloc(m.orb_allocs, nn, &err);
+    m.J = dalloc(m.orb_allocs, nn, &err);
+    m.sigx = dalloc(m.orb_allocs, nn, &err);
+    m.sigc = dalloc(m.orb_allocs, nn, &err);
+    m.g0w0 = nullptr;
+    m.D = dalloc(m.orb_allocs, nov, &err);
+    m.Om = dalloc(m.orb_allocs, nov, &err);
+    m.R = dalloc(m.orb_allocs, (size_t)nov * na, &err);
+    m.Xv = dalloc(m.orb_allocs, (size_t)nov * na, &err);
+    m.M = dalloc(m.orb_allocs, (size_t)nov * nov, &err);
+    m.ZT = dalloc(m.orb_allocs, (size_t)nov * nov, &err);
+    m.XpY = nullptr;
+    std::unique_ptr<MolBuf> d(new (std::nothrow) MolBuf());
+    if (!d) err = MOLGW_E_NOMEM;
+    if (!err) {
+      d->B = dalloc(d->ri_allocs, (size_t)na * nn, &err);
+      d->T1 = dalloc(d->ri_allocs, (size_t)na * nn, &err);
+      d->eps = dalloc(d->orb_allocs, nb, &err);
+      d->C = dalloc(d->orb_allocs, nn, &err);
+      d->hmo = dalloc(d->orb_allocs, nn, &err);
+      d->J = dalloc(d->orb_allocs, nn, &err);
+      d->sigx = dalloc(d->orb_allocs, nn, &err);
+      d->sigc = dalloc(d->orb_allocs, nn, &err);
+    }
+    if (err) {
+      if (d) { free_all(d->ri_allocs); free_all(d->orb_allocs); }
+      free_all(m.orb_allocs);
+      m.eps = nullptr;
+      m.alloc_no = 0;
+      return err;
+    }
+    m.dn = std::move(d);
+    m.alloc_no = key;
+  }
+  MolBuf& d = *m.dn;
+  m.no = n_occ_up;
+  m.nov = nov;
+  m.nov_up = nov_up;
+  // the spin-down channel: its own orbitals and B, the RI factors and the RPA of m
+  d.nb = nb; d.na = na; d.no = n_occ_dn; d.nov = nov;
+  d.L = m.L; d.R = m.R; d.Om = m.Om; d.D = m.D;
+  d.have_ri = d.have_orb = true;
+  int r = copy_in(c, m.eps, eps_up, nb);
+  if (!r) r = copy_in(c, m.C, C_up, nn);
+  if (!r) r = copy_in(c, d.eps, eps_dn, nb);
+  if (!r) r = copy_in(c, d.C, C_dn, nn);
+  if (r) return r;
+  Exec& ex = c->lanes[0].ex;
+  check_finite(ex, m.eps, nb);
+  check_finite(ex, m.C, (long long)nn);
+  check_finite(ex, d.eps, nb);
+  check_finite(ex, d.C, (long long)nn);
+  m.have_orb = true;
+  m.b_valid = m.jx_valid = m.rpa_valid = m.sigma_valid = false;
+  m.have_b = m.have_rpa = m.have_jx = m.have_sigma = m.have_g0w0 = false;
+  m.h_ready = false;
+  if (h_core) {
+    r = ensure_scratch(c, c->lanes[0], nb, na, nov);
+    if (r) return r;
+    r = copy_in(c, m.T1, h_core, nn);
+    if (r) return r;
+    h_ao_to_mo(ex, m, m.T1, c->lanes[0].scr);
+    h_ao_to_mo(ex, d, m.T1, c->lanes[0].scr);
+    m.h_ready = true;
+  }
+  return launch_status();
+}
+
 int molgw_b200_rpa(molgw_ctx c, int mol, double* omega, double* xpy) {
   if (!c) return MOLGW_E_ARG;
   DeviceGuard g(c->device);
@@ -830,6 +1004,10 @@ int molgw_b200_sigma(molgw_ctx c, int mol, double* sigma_x, double* sigma_c) {
   const size_t nn = (size_t)m.nb * m.nb;
   if (sigma_x) r = copy_out(c, sigma_x, m.sigx, nn, &sync);
   if (!r && sigma_c) r = copy_out(c, sigma_c, m.sigc, nn, &sync);
+  if (m.dn) {   // open shell: the spin-down blocks follow
+    if (!r && sigma_x) r = copy_out(c, sigma_x + nn, m.dn->sigx, nn, &sync);
+    if (!r && sigma_c) r = copy_out(c, sigma_c + nn, m.dn->sigc, nn, &sync);
+  }
   if (r) return r;
   return sync ? read_status(c) : MOLGW_OK;
 }
@@ -880,6 +1058,10 @@ int molgw_b200_qs_step(molgw_ctx c, int mol, double* eps_out, double* C_out) {
   bool sync = false;
   if (eps_out) r = copy_out(c, eps_out, m.eps, m.nb, &sync);
   if (!r && C_out) r = copy_out(c, C_out, m.C, (size_t)m.nb * m.nb, &sync);
+  if (m.dn) {   // open shell: the spin-down energies and orbitals follow
+    if (!r && eps_out) r = copy_out(c, eps_out + m.nb, m.dn->eps, m.nb, &sync);
+    if (!r && C_out) r = copy_out(c, C_out + (size_t)m.nb * m.nb, m.dn->C, (size_t)m.nb * m.nb, &sync);
+  }
   if (r) return r;
   return sync ? read_status(c) : MOLGW_OK;
 }
@@ -921,9 +1103,26 @@ int molgw_b200_fetch(molgw_ctx c, int mol, int item, double* out, size_t count) 
     default: return MOLGW_E_ARG;
   }
   if (!avail) return MOLGW_E_STATE;
-  if (count != n) return MOLGW_E_ARG;
+  // open shell: the per-orbital items are the spin-up block followed by the spin-down one
+  const double* src_dn = nullptr;
+  if (m.dn) {
+    const MolBuf& d = *m.dn;
+    switch (item) {
+      case MOLGW_ITEM_B: src_dn = d.B; break;
+      case MOLGW_ITEM_SIGMA_X: src_dn = d.sigx; break;
+      case MOLGW_ITEM_SIGMA_C: src_dn = d.sigc; break;
+      case MOLGW_ITEM_J: src_dn = d.J; break;
+      case MOLGW_ITEM_H_MO: src_dn = d.hmo; break;
+      case MOLGW_ITEM_EPS: src_dn = d.eps; break;
+      case MOLGW_ITEM_C: src_dn = d.C; break;
+      case MOLGW_ITEM_OMEGA: case MOLGW_ITEM_R: break;
+      default: return MOLGW_E_STATE;             // G0W0 items: closed shell only
+    }
+  }
+  if (count != (src_dn ? 2 * n : n)) return MOLGW_E_ARG;
   bool sync = false;
   int r = copy_out(c, out, src, n, &sync);
+  if (!r && src_dn) r = copy_out(c, out + n, src_dn, n, &sync);
   if (r) return r;
   return sync ? read_status(c) : MOLGW_OK;
 }
@@ -1068,22 +1267,32 @@ int molgw_b200_autotune(molgw_ctx c, int32_t* lanes_out) {
   std::vector<Flags> flags;
   for (int k : mols) {
     const MolBuf& m = c->mols[k];
-    const size_t nn = (size_t)m.nb * m.nb;
-    double* b = dalloc(tmp, m.nb + 2 * nn, &err);
+    const size_t nn = (size_t)m.nb * m.nb, per = m.nb + 2 * nn;
+    double* b = dalloc(tmp, m.dn ? 2 * per : per, &err);
     if (err) { free_all(tmp); return err; }
     snap.push_back(b);
     flags.push_back(get_flags(m));
-    cudaMemcpyAsync(b, m.eps, m.nb * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
-    cudaMemcpyAsync(b + m.nb, m.C, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
-    cudaMemcpyAsync(b + m.nb + nn, m.hmo, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    const MolBuf* chans[2] = {&m, m.dn.get()};
+    for (const MolBuf* x : chans) {   // open shell: both spin channels
+      if (!x) continue;
+      double* bx = (x == &m) ? b : b + per;
+      cudaMemcpyAsync(bx, x->eps, m.nb * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+      cudaMemcpyAsync(bx + m.nb, x->C, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+      cudaMemcpyAsync(bx + m.nb + nn, x->hmo, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    }
   }
   auto restore = [&]() {
     for (size_t q = 0; q < mols.size(); ++q) {
       MolBuf& m = c->mols[mols[q]];
-      const size_t nn = (size_t)m.nb * m.nb;
-      cudaMemcpyAsync(m.eps, snap[q], m.nb * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
-      cudaMemcpyAsync(m.C, snap[q] + m.nb, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
-      cudaMemcpyAsync(m.hmo, snap[q] + m.nb + nn, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+      const size_t nn = (size_t)m.nb * m.nb, per = m.nb + 2 * nn;
+      MolBuf* chans[2] = {&m, m.dn.get()};
+      for (MolBuf* x : chans) {
+        if (!x) continue;
+        const double* bx = (x == &m) ? snap[q] : snap[q] + per;
+        cudaMemcpyAsync(x->eps, bx, m.nb * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+        cudaMemcpyAsync(x->C, bx + m.nb, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+        cudaMemcpyAsync(x->hmo, bx + m.nb + nn, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+      }
       put_flags(m, flags[q]);
     }
   };
@@ -1157,7 +1366,7 @@ int molgw_b200_destroy(molgw_ctx c) {
   {
     DeviceGuard g(c->device);
     s = read_status(c);
-    for (auto& m : c->mols) { free_all(m.ri_allocs); free_all(m.orb_allocs); }
+    for (auto& m : c->mols) { drop_open(m); free_all(m.ri_allocs); free_all(m.orb_allocs); }
     for (auto& t : c->tcb) free_all(t.ri_allocs);
     graph_drop(c);
     for (auto& l : c->lanes) lane_free(l);

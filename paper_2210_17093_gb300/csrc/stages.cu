@@ -30,6 +30,24 @@ __global__ void k_gather_xv(const double* B, const double* eps, int nb, int no, 
   }
 }
 
+// Open shell: rows t0 .. t0 + no*nv - 1 of Xv = sqrt(2) D^1/2 B_ia^T (n_tot x n_aux,
+// column-major) and of D for one spin channel (the spin sum of the closed-shell
+// factor 2 is written out over the two channels).
+__global__ void k_gather_xv_spin(const double* B, const double* eps, int nb, int no, int na, long long t0,
+                                 long long ntot, double* Xv, double* D) {
+  const int nv = nb - no;
+  const long long nov = (long long)no * nv;
+  const long long total = nov * na;
+  for (long long idx = gtid(); idx < total; idx += gstride()) {
+    const long long t = idx % nov;
+    const int P = (int)(idx / nov);
+    const int i = (int)(t / nv), a = no + (int)(t % nv);
+    const double Dt = eps[a] - eps[i];
+    if (P == 0) D[t0 + t] = Dt;
+    Xv[t0 + t + (long long)P * ntot] = sqrt(2.0 * Dt) * B[(long long)P * nb * nb + (long long)i * nb + a];
+  }
+}
+
 __global__ void k_add_diag_sq(double* M, const double* D, long long n) {
   for (long long t = gtid(); t < n; t += gstride()) M[t + t * n] += D[t] * D[t];
 }
@@ -89,13 +107,22 @@ __global__ void k_rho(const double* B, int nb, int no, int na, double* rho) {
   }
 }
 
-// J[pq] = 2 sum_P B[P][pq] rho_P
-__global__ void k_hartree(const double* B, const double* rho, int nb, int na, double* J) {
+// rho_P += sum_{i < no} B[P][i][i] (the other spin channel of an open shell)
+__global__ void k_rho_add(const double* B, int nb, int no, int na, double* rho) {
+  for (long long P = gtid(); P < na; P += gstride()) {
+    double s = 0.0;
+    for (int i = 0; i < no; ++i) s += B[P * nb * nb + (long long)i * nb + i];
+    rho[P] += s;
+  }
+}
+
+// J[pq] = f sum_P B[P][pq] rho_P (f = 2 for a closed shell, 1 with both spins in rho)
+__global__ void k_hartree(const double* B, const double* rho, int nb, int na, double f, double* J) {
   const long long nn = (long long)nb * nb;
   for (long long pq = gtid(); pq < nn; pq += gstride()) {
     double s = 0.0;
     for (int P = 0; P < na; ++P) s += B[(long long)P * nn + pq] * rho[P];
-    J[pq] = 2.0 * s;
+    J[pq] = f * s;
   }
 }
 
@@ -349,13 +376,18 @@ void stage_ri_mo_transform(Exec& ex, MolBuf& m) {
 }
 
 // Hartree J and exchange Sigma_x from B (Eqs. J, K in the MO basis).
-void stage_j_sigx(Exec& ex, MolBuf& m, Scratch& s) {
+void stage_j_sigx(Exec& ex, MolBuf& m, Scratch& s, const MolBuf* other) {
   const int nb = m.nb, na = m.na, no = m.no;
   {
-    KScope ks(ex, MOLGW_K_MISC, 3);
+    KScope ks(ex, MOLGW_K_MISC, other ? 4 : 3);
     k_rho<<<grid_for(na), 256, 0, ex.st>>>(m.B, nb, no, na, s.rho);
-    k_hartree<<<grid_for((long long)nb * nb), 256, 0, ex.st>>>(m.B, s.rho, nb, na, m.J);
-    k_gather_bocc<<<grid_for((long long)nb * na * no), 256, 0, ex.st>>>(m.B, nb, no, na, m.T1);
+    if (other) k_rho_add<<<grid_for(na), 256, 0, ex.st>>>(other->B, nb, other->no, na, s.rho);
+    k_hartree<<<grid_for((long long)nb * nb), 256, 0, ex.st>>>(m.B, s.rho, nb, na, other ? 1.0 : 2.0, m.J);
+    if (no > 0) k_gather_bocc<<<grid_for((long long)nb * na * no), 256, 0, ex.st>>>(m.B, nb, no, na, m.T1);
+  }
+  if (no == 0) {   // an empty spin channel has no exchange
+    cudaMemsetAsync(m.sigx, 0, sizeof(double) * nb * nb, ex.st);
+    return;
   }
   const long long K = (long long)na * no;
   GemmF64 g;
@@ -370,6 +402,19 @@ void stage_j_sigx(Exec& ex, MolBuf& m, Scratch& s) {
 }
 
 void gather_xv(Exec& ex, MolBuf& m) {
+  if (m.dn) {
+    // open shell: spin-up transitions, then spin-down ones
+    const MolBuf& d = *m.dn;
+    const long long nov_dn = m.nov - m.nov_up;
+    KScope ks(ex, MOLGW_K_MISC, 2);
+    if (m.nov_up > 0)
+      k_gather_xv_spin<<<grid_for(m.nov_up * m.na), 256, 0, ex.st>>>(m.B, m.eps, m.nb, m.no, m.na, 0, m.nov, m.Xv,
+                                                                     m.D);
+    if (nov_dn > 0)
+      k_gather_xv_spin<<<grid_for(nov_dn * m.na), 256, 0, ex.st>>>(d.B, d.eps, m.nb, d.no, m.na, m.nov_up, m.nov,
+                                                                   m.Xv, m.D);
+    return;
+  }
   KScope ks(ex, MOLGW_K_MISC);
   k_gather_xv<<<grid_for(m.nov * m.na), 256, 0, ex.st>>>(m.B, m.eps, m.nb, m.no, m.na, m.Xv, m.D);
 }

@@ -1,5 +1,7 @@
 // Per-molecule device buffers and the stage drivers of one RI-qsGW pass.
 #pragma once
+#include <memory>
+
 #include "common.cuh"
 #include "fx.cuh"
 #include "tc.cuh"
@@ -29,6 +31,11 @@ struct MolBuf {
   double* g0w0 = nullptr;                      // G0W0: [eps_QP | Z | Sigma_c,pp(eps_p)], 3 nb
   bool have_g0w0 = false;
   std::vector<void*> ri_allocs, orb_allocs;
+  // Open shell (molgw_b200_set_orbitals_open): this MolBuf is the spin-up channel and
+  // holds the RPA of both spins (nov = nov_up + n_ov of spin down transitions, up
+  // first); dn is the spin-down channel, whose R, Om and D point into this one.
+  std::unique_ptr<MolBuf> dn;
+  long long nov_up = 0;
 };
 
 // Split operands of the tensor-core path (hi/lo pairs, K-major, padded).  L is
@@ -87,7 +94,9 @@ void dev_copy(Exec& ex, const double* a, double* b, long long n);
 void check_finite(Exec& ex, const double* a, long long n);
 void fill_upper(Exec& ex, double* M, long long n);
 void stage_ri_mo_transform(Exec& ex, MolBuf& m);
-void stage_j_sigx(Exec& ex, MolBuf& m, Scratch& s);
+// J and Sigma_x of molecule m; with `other` (the other spin channel of an open
+// shell) the density of both channels enters J, without the closed-shell factor 2.
+void stage_j_sigx(Exec& ex, MolBuf& m, Scratch& s, const MolBuf* other = nullptr);
 void stage_rpa_build(Exec& ex, MolBuf& m);
 void stage_rpa_eigensolve(Exec& ex, MolBuf& m, EigWork& w, Scratch& s, bool full_xpy);
 void stage_sigma(Exec& ex, MolBuf& m, Scratch& s, double eta);

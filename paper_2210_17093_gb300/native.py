@@ -39,7 +39,7 @@ EXPORTS = ["molgw_b200_create", "molgw_b200_set_ri", "molgw_b200_set_orbitals", 
            "molgw_b200_launch_count", "molgw_b200_set_timing", "molgw_b200_destroy",
            "molgw_b200_status_string", "molgw_b200_eigh_noalloc", "molgw_b200_graph_replays",
            "molgw_b200_tc_gemm", "molgw_b200_autotune", "molgw_b200_lanes", "molgw_b200_g0w0",
-           "molgw_b200_g0w0_window", "molgw_b200_inject_fault"]
+           "molgw_b200_g0w0_window", "molgw_b200_inject_fault", "molgw_b200_set_orbitals_open"]
 NOALLOC_NMAX = 256
 
 
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "molgw_b200_create": ([ctypes.POINTER(Opts), ctypes.POINTER(vp)], ip),
         "molgw_b200_set_ri": ([vp, ip, ip, ip, dp], ip),
         "molgw_b200_set_orbitals": ([vp, ip, ip, dp, dp, dp], ip),
+        "molgw_b200_set_orbitals_open": ([vp, ip, ip, ip, dp, dp, dp, dp, dp], ip),
         "molgw_b200_rpa": ([vp, ip, dp, dp], ip),
         "molgw_b200_sigma": ([vp, ip, dp, dp], ip),
         "molgw_b200_qs_step": ([vp, ip, dp, dp], ip),
@@ -158,6 +159,7 @@ class Context:
         _check(self._lib.molgw_b200_create(ctypes.byref(o), ctypes.byref(h)), "molgw_b200_create")
         self._h = h
         self.sizes = {}
+        self.open_nov = {}    # open-shell molecules: transitions of both spins
 
     def _hh(self):
         if self._h is None:
@@ -168,6 +170,7 @@ class Context:
         _check(self._lib.molgw_b200_set_ri(self._hh(), mol, n_basis, n_aux,
                                            _ptr(L, n_aux * n_basis * n_basis)), "set_ri")
         self.sizes[mol] = [n_basis, n_aux, None]
+        self.open_nov.pop(mol, None)
 
     def set_orbitals(self, mol: int, n_occ: int, eps, C, h_core=None):
         nb = self.sizes[mol][0] if mol in self.sizes else None
@@ -175,10 +178,28 @@ class Context:
         _check(self._lib.molgw_b200_set_orbitals(self._hh(), mol, n_occ, _ptr(eps, nb), _ptr(C, nn),
                                                  _ptr(h_core, nn)), "set_orbitals")
         self.sizes[mol][2] = n_occ
+        self.open_nov.pop(mol, None)
+
+    def set_orbitals_open(self, mol: int, n_occ_up: int, n_occ_dn: int, eps_up, eps_dn, C_up, C_dn,
+                          h_core=None):
+        """Open shell: one set of orbitals per spin (molgw_b200_set_orbitals_open).  Later
+        per-orbital outputs are the spin-up block followed by the spin-down block."""
+        nb = self.sizes[mol][0] if mol in self.sizes else None
+        nn = None if nb is None else nb * nb
+        _check(self._lib.molgw_b200_set_orbitals_open(self._hh(), mol, n_occ_up, n_occ_dn, _ptr(eps_up, nb),
+                                                      _ptr(eps_dn, nb), _ptr(C_up, nn), _ptr(C_dn, nn),
+                                                      _ptr(h_core, nn)), "set_orbitals_open")
+        self.sizes[mol][2] = n_occ_up
+        self.open_nov[mol] = n_occ_up * (nb - n_occ_up) + n_occ_dn * (nb - n_occ_dn)
 
     def n_ov(self, mol: int):
+        if mol in self.open_nov:
+            return self.open_nov[mol]
         nb, _, no = self.sizes.get(mol, (None, None, None))
         return None if no is None else no * (nb - no)
+
+    def _spins(self, mol: int) -> int:
+        return 2 if mol in self.open_nov else 1
 
     def rpa(self, mol: int, omega=None, xpy=None):
         n = self.n_ov(mol) if mol >= 0 else None
@@ -186,13 +207,14 @@ class Context:
                "rpa")
 
     def sigma(self, mol: int, sigma_x=None, sigma_c=None):
-        nn = self.sizes[mol][0] ** 2 if mol in self.sizes else None
+        nn = self._spins(mol) * self.sizes[mol][0] ** 2 if mol in self.sizes else None
         _check(self._lib.molgw_b200_sigma(self._hh(), mol, _ptr(sigma_x, nn), _ptr(sigma_c, nn)), "sigma")
 
     def qs_step(self, mol: int, eps_out=None, C_out=None):
         nb = self.sizes[mol][0] if mol in self.sizes else None
-        _check(self._lib.molgw_b200_qs_step(self._hh(), mol, _ptr(eps_out, nb),
-                                            _ptr(C_out, None if nb is None else nb * nb)), "qs_step")
+        k = self._spins(mol)
+        _check(self._lib.molgw_b200_qs_step(self._hh(), mol, _ptr(eps_out, None if nb is None else k * nb),
+                                            _ptr(C_out, None if nb is None else k * nb * nb)), "qs_step")
 
     def g0w0(self, mol: int, eps_qp=None, z=None, sigma_c_diag=None):
         nb = self.sizes[mol][0] if mol in self.sizes else None
