@@ -145,3 +145,24 @@ def test_open_shell_argument_and_state_errors():
         ctx.set_orbitals(0, 5, to_dev(m["eps"]), to_dev(m["C"]))
         e = np.empty(nb)
         ctx.qs_step(0, e)
+
+
+def test_open_shell_graph_replay_and_autotune():
+    """Three steps replayed from a captured graph equal three eager steps; autotuning a
+    context that holds an open-shell molecule puts both spin channels back."""
+    nb, na = 36, 80
+    L, epss, Cs, nos = open_molecule(nb, 7, 6, na, 48)
+    out = []
+    for flags, tune in ((0, False), (4, False), (0, True)):
+        with lib_context(flags=flags) as ctx:
+            load_open(ctx, 0, L, epss, Cs, nos)
+            if tune:
+                ctx.autotune()
+            for _ in range(3):
+                ctx.qs_step(-1)
+            ctx.sync()
+            e = np.empty((2, nb))
+            ctx.fetch(0, "eps", e)
+            out.append(e)
+    assert np.array_equal(out[0], out[1])
+    assert np.max(np.abs(out[2] - out[0])) < 1e-8
