@@ -70,7 +70,7 @@ def test_equal_channels_match_the_closed_shell_gpu_path():
         ctx.set_orbitals(0, no, to_dev(m["eps"]), to_dev(m["C"]))
         e_closed = np.empty(nb)
         ctx.qs_step(0, e_closed)
-        load_open(ctx, 1 - 1, m["L"], (m["eps"], m["eps"]), (m["C"], m["C"]), (no, no))
+        load_open(ctx, 0, m["L"], (m["eps"], m["eps"]), (m["C"], m["C"]), (no, no))
         e_open = np.empty((2, nb))
         ctx.qs_step(0, e_open)
     assert np.max(np.abs(e_open[0] - e_closed)) < 1e-9
