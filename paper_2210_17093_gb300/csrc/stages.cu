@@ -641,11 +641,23 @@ int stage_g0w0(Exec& ex, MolBuf& m, Scratch& s, double eta, int p0, int p1) {
   for (int b = 0; b < nblk; ++b) {
     const int m0 = b * mb, cnt = std::min(mb, nb - m0);
     const long long K = (long long)cnt * nov;
+    // Wb[pl][mm][s] = sum_P B[P][m0 + mm][p0 + pl] R[P][s]: batched over the states of a
+    // narrow window (rows m, so that the tiles fill), else over the m of the block
+    // (rows p); the same sums in the same order either way
     GemmF64 g;
-    g.M = np; g.N = nov; g.K = na; g.batch = cnt;
-    g.A = m.B + (long long)m0 * nb + p0; g.sa_m = 1; g.sa_k = nn; g.sa_b = nb;
+    g.N = nov; g.K = na;
+    g.A = m.B + (long long)m0 * nb + p0; g.sa_k = nn;
     g.B = m.R; g.sb_k = nov; g.sb_n = 1; g.sb_b = 0;
-    g.C = s.wblk; g.sc_m = K; g.sc_n = 1; g.sc_b = nov;
+    g.C = s.wblk; g.sc_n = 1;
+    if (np < 32) {
+      g.M = cnt; g.batch = np;
+      g.sa_m = nb; g.sa_b = 1;
+      g.sc_m = nov; g.sc_b = K;
+    } else {
+      g.M = np; g.batch = cnt;
+      g.sa_m = 1; g.sa_b = nb;
+      g.sc_m = K; g.sc_b = nov;
+    }
     g.kclass = MOLGW_K_SIGMA;
     gemm_f64(ex, g);
     KScope ks(ex, MOLGW_K_SIGMA);
