@@ -12,8 +12,13 @@
  *                         1/2 Re[Sigma_pq(eps_p) + Sigma_pq(eps_q)]        Eqs. (Sigma.c.GW), (Sigma.c.qsGW.real)
  *   (f) qs_update         H = h + J + Sigma_x + Sigma_c, H U = U eps', C' = C U   Eqs. (H), (GEP), (J)
  *
+ * Beside it: qsMP2 (MOLGW_FLAG_QSMP2, Eqs. (Sigma.c.MP2), (Sigma.c.qsMP2.real)),
+ * one-shot G0W0 (molgw_b200_g0w0, Sec. II.C) and open shells
+ * (molgw_b200_set_orbitals_open, the sigma-resolved equations of Sec. II).
+ *
  * Conventions (all entry points)
- *   - Closed shell, real orbitals, orthonormal AO basis (S = I).  Sizes:
+ *   - Closed shell unless molgw_b200_set_orbitals_open, real orbitals, orthonormal
+ *     AO basis (S = I).  Sizes:
  *     nb = n_basis, no = n_occ, nv = nb - no, n_ov = no*nv, na = n_aux.
  *     Transition index t = i*nv + (a - no), occupied-major.
  *   - Every array argument is a plain pointer to float64 data that may live in
