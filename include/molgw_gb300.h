@@ -145,8 +145,9 @@ int molgw_b200_set_ri(molgw_ctx ctx, int mol, int n_basis, int n_aux, const doub
 int molgw_b200_set_orbitals(molgw_ctx ctx, int mol, int n_occ, const double* eps,
                             const double* C, const double* h_core);
 
-/* Open shell (float64 only): the orbitals of molecule `mol` per spin -- n_occ_up,
- * n_occ_dn (0 <= n_occ < n_basis, at least one electron), eps_up/eps_dn[n_basis]
+/* Open shell (float64, or BF16X10 with the fixed-point contractions): the orbitals
+ * of molecule `mol` per spin -- n_occ_up, n_occ_dn (0 <= n_occ < n_basis, at least
+ * one electron), eps_up/eps_dn[n_basis]
  * ascending, C_up/C_dn[mu][p] orthonormal columns -- for the sigma-resolved
  * equations of Sec. II (Eqs. GEP, H, J, D, K with sigma; Casida.A/B with the spin
  * sum written out: one RPA over the transitions of both spins, spin up first, M =
@@ -156,9 +157,9 @@ int molgw_b200_set_orbitals(molgw_ctx ctx, int mol, int n_occ, const double* eps
  * solution.  Afterwards every per-orbital output and fetch item (B, Sigma_x,
  * Sigma_c, J, h_MO, eps, C) is the spin-up block followed by the spin-down block
  * (twice the closed-shell size); Omega and R span the transitions of both spins.
- * MOLGW_E_ARG unless the context is MOLGW_PREC_FP64 without MOLGW_FLAG_QSMP2 and
- * MOLGW_FLAG_FULL_XPY; molgw_b200_g0w0 and the G0W0 items return MOLGW_E_STATE for
- * an open-shell molecule.  set_ri or set_orbitals make the molecule closed again. */
+ * MOLGW_E_ARG unless the context is MOLGW_PREC_FP64 or MOLGW_PREC_BF16X10, without
+ * MOLGW_FLAG_QSMP2 and MOLGW_FLAG_FULL_XPY; molgw_b200_g0w0 and the G0W0 items
+ * return MOLGW_E_STATE for an open-shell molecule.  set_ri or set_orbitals make the molecule closed again. */
 int molgw_b200_set_orbitals_open(molgw_ctx ctx, int mol, int n_occ_up, int n_occ_dn, const double* eps_up,
                                  const double* eps_dn, const double* C_up, const double* C_dn,
                                  const double* h_core);

@@ -340,9 +340,10 @@ struct Range {
   Range& operator=(const Range&) = delete;
 };
 
-// Open shell (float64): both spin channels through (a), J, Sigma_x and h; one RPA over
-// the transitions of both spins (up first); (d)+(e) and (f) per channel, the
-// spin-down channel reading R and Omega of the spin-up MolBuf.
+// Open shell (float64, or BF16X10 with the contractions on the fixed-point engine):
+// both spin channels through (a), J, Sigma_x and h; one RPA over the transitions of
+// both spins (up first); (d)+(e) and (f) per channel, the spin-down channel reading
+// R and Omega of the spin-up MolBuf.
 int run_pass_open(molgw_ctx c, Lane& l, int mol, char upto) {
   MolBuf& m = c->mols[mol];
   MolBuf& d = *m.dn;
@@ -350,10 +351,18 @@ int run_pass_open(molgw_ctx c, Lane& l, int mol, char upto) {
   int r = lane_fit(c, l, m);
   if (r) return r;
   Exec& ex = l.ex;
+  const bool fx = use_fx(c), fx_ab = fx && use_tc_ab(c);
+  if (fx) fx_bufs_carve(l.fxo, m.nb, m.na, m.nov, fx_mblock(m.nb, m.na, m.nov), l.tco_base);
   if (!m.b_valid) {
     Range rg("(a) ri_mo_transform, both spins");
-    stage_ri_mo_transform(ex, m);
-    stage_ri_mo_transform(ex, d);
+    if (fx_ab) {
+      r = stage_ri_mo_transform_fx(ex, m, c->tcb[mol].Lfx, l.tco_base);
+      if (!r) r = stage_ri_mo_transform_fx(ex, d, c->tcb[mol].Lfx, l.tco_base);
+      if (r) return r;
+    } else {
+      stage_ri_mo_transform(ex, m);
+      stage_ri_mo_transform(ex, d);
+    }
     m.b_valid = m.have_b = true;
   }
   if (!m.h_ready) {
@@ -365,16 +374,19 @@ int run_pass_open(molgw_ctx c, Lane& l, int mol, char upto) {
     m.jx_valid = m.have_jx = true;
     m.h_ready = true;
   }
-  if (upto == 'b') {
-    Range rg("(b) rpa_build");
-    stage_rpa_build(ex, m);
-    m.rpa_valid = false;
-    return launch_status();
-  }
-  if (!m.rpa_valid) {
+  if (upto == 'b' || !m.rpa_valid) {
     {
       Range rg("(b) rpa_build");
-      stage_rpa_build(ex, m);
+      if (fx_ab) {
+        r = stage_rpa_build_fx(ex, m, l.tco_base);
+        if (r) return r;
+      } else {
+        stage_rpa_build(ex, m);
+      }
+    }
+    if (upto == 'b') {
+      m.rpa_valid = false;
+      return launch_status();
     }
     Range rg("(c) rpa_eigensolve");
     stage_rpa_eigensolve(ex, m, l.eig, l.scr, false);
@@ -387,8 +399,14 @@ int run_pass_open(molgw_ctx c, Lane& l, int mol, char upto) {
       stage_j_sigx(ex, d, l.scr, &m);
       m.jx_valid = m.have_jx = true;
     }
-    stage_sigma(ex, m, l.scr, c->opts.eta);
-    stage_sigma(ex, d, l.scr, c->opts.eta);
+    if (fx) {
+      r = stage_sigma_fx(ex, m, l.fxo, l.scr, c->opts.eta);
+      if (!r) r = stage_sigma_fx(ex, d, l.fxo, l.scr, c->opts.eta);
+      if (r) return r;
+    } else {
+      stage_sigma(ex, m, l.scr, c->opts.eta);
+      stage_sigma(ex, d, l.scr, c->opts.eta);
+    }
     m.sigma_valid = m.have_sigma = true;
   }
   if (upto == 'f') {
@@ -879,7 +897,8 @@ int molgw_b200_set_orbitals_open(molgw_ctx c, int mol, int n_occ_up, int n_occ_d
                                  const double* eps_dn, const double* C_up, const double* C_dn,
                                  const double* h_core) {
   if (!mol_ok(c, mol) || !eps_up || !eps_dn || !C_up || !C_dn) return MOLGW_E_ARG;
-  if (c->opts.precision != MOLGW_PREC_FP64 || (c->opts.flags & (MOLGW_FLAG_QSMP2 | MOLGW_FLAG_FULL_XPY)))
+  if ((c->opts.precision != MOLGW_PREC_FP64 && c->opts.precision != MOLGW_PREC_BF16X10) ||
+      (c->opts.flags & (MOLGW_FLAG_QSMP2 | MOLGW_FLAG_FULL_XPY)))
     return MOLGW_E_ARG;
   DeviceGuard g(c->device);
   MolBuf& m = c->mols[mol];

@@ -128,7 +128,7 @@ def test_open_shell_argument_and_state_errors():
     from paper_2210_17093_gb300 import MolgwError
     nb, na = 24, 72
     L, epss, Cs, nos = open_molecule(nb, 5, 4, na, 47)
-    with lib_context(precision="bf16x10") as ctx:
+    with lib_context(precision="bf16x3") as ctx:
         with pytest.raises(MolgwError):
             load_open(ctx, 0, L, epss, Cs, nos)
     with lib_context() as ctx:
@@ -166,3 +166,19 @@ def test_open_shell_graph_replay_and_autotune():
             out.append(e)
     assert np.array_equal(out[0], out[1])
     assert np.max(np.abs(out[2] - out[0])) < 1e-8
+
+
+@pytest.mark.parametrize("flags", [0, 16, 48])
+@pytest.mark.parametrize("nb,nos,na,seed", [(24, (5, 4), 72, 40), (71, (13, 11), 150, 41)])
+def test_open_shell_fixed_point_within_1mev(flags, nb, nos, na, seed):
+    """BF16X10: (d)+(e) per spin on the fixed-point engine; with MOLGW_FLAG_TC_AB (16)
+    also (a) per spin and (b); with MOLGW_FLAG_EIG_TC (32) the eigensolver's trailing
+    updates on the 7-digit engine."""
+    L, epss, Cs, nos = open_molecule(nb, nos[0], nos[1], na, seed)
+    r = qsgw.qsgw_pass_open(L, epss, Cs, nos, ETA)
+    with lib_context(precision="bf16x10", flags=flags) as ctx:
+        load_open(ctx, 0, L, epss, Cs, nos)
+        eps = np.empty((2, nb))
+        ctx.qs_step(0, eps)
+    for k in (0, 1):
+        assert np.max(np.abs(eps[k] - r["spin"][k]["eps_new"])) < 3.675e-5
