@@ -257,6 +257,22 @@ def test_iterations_keep_orthonormal_orbitals():
         assert np.all(np.diff(r["eps_new"]) >= 0)
 
 
+def test_core_hamiltonian_fixed_in_ao_basis():
+    """Eq. (H) with S = I: h is one fixed operator on the AO basis, so C h_MO C^T is the same
+    before and after every iteration, and H = h + J + Sigma_x + Sigma_c, carried to the AO
+    basis by the input orbitals, is diagonal in the updated ones: C'^T H_AO C' = diag(eps')."""
+    m = tiny(92, 8, 3, 10)
+    its = qsgw.qsgw_iterations(m["L"], m["eps"], m["C"], 3, ETA, 2)
+    C = m["C"]
+    h_ao = C @ its[0]["h_mo"] @ C.T
+    for r in its:
+        H_ao = C @ (r["h_mo"] + r["J"] + r["sigma_x"] + r["sigma_c"]) @ C.T
+        Cn = r["C_new"]
+        np.testing.assert_allclose(Cn.T @ H_ao @ Cn, np.diag(r["eps_new"]), atol=1e-13)
+        np.testing.assert_allclose(Cn @ r["h_mo_new"] @ Cn.T, h_ao, atol=1e-13)
+        C = Cn
+
+
 def test_golden_regression():
     """The oracle still reproduces the stored small-workload values (tests/golden)."""
     import json
