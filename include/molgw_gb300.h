@@ -313,6 +313,21 @@ int molgw_b200_autotune(molgw_ctx ctx, int32_t* lanes_out);
 /* Lane count the next mol = -1 call uses. */
 int32_t molgw_b200_lanes(molgw_ctx ctx);
 
+/* The lane plan of a batch (mol = -1), computed on the host with no context and no
+ * device: molecule k of n_mols goes to lane lane_of[k] and is issued there in position
+ * slot[k] (slot may be NULL).  A pass's relative cost is n_ov^3 (eigensolve) plus
+ * 2 nb^2 n_ov na per spin channel (residues); with MOLGW_FLAG_QSMP2 in flags it is
+ * 4 nb^2 n_ov na + 2 nb^3 n_ov.  Molecules are taken in order of decreasing cost (equal
+ * costs by index), each to the lane with the least cost so far (equal: the lowest
+ * lane), over max(1, min(lanes, n_mols)) lanes; lanes = 0 means the default of 8, and
+ * at most 16 are used.  A context whose opts.lanes equals `lanes` (and which was not
+ * autotuned) runs the same plan.  n_basis, n_aux, n_occ_up: [n_mols]; n_occ_dn: NULL
+ * for closed shells (n_occ_up is then n_occ), else [n_mols] with -1 for a closed shell.
+ * Returns the number of lanes used, or MOLGW_E_ARG for sizes that set_ri or
+ * set_orbitals(_open) would refuse (and for open shells with MOLGW_FLAG_QSMP2). */
+int molgw_b200_plan_batch(int n_mols, const int32_t* n_basis, const int32_t* n_aux, const int32_t* n_occ_up,
+                          const int32_t* n_occ_dn, uint32_t flags, int lanes, int32_t* lane_of, int32_t* slot);
+
 /* Library extension (the paper has no counterpart): number of qs_step calls
  * served by replaying a captured graph (MOLGW_FLAG_GRAPH); -1 once a capture
  * failed and the context went back to issuing the launches one by one. */

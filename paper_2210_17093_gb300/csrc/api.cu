@@ -541,40 +541,55 @@ bool steady(const MolBuf& m) {
   return ready(m) && m.h_ready && !m.b_valid && !m.jx_valid && !m.rpa_valid && !m.sigma_valid;
 }
 
-// Relative cost of one pass: the n_ov^3 eigensolve and the residue contraction.
-double pass_cost(const MolBuf& m, bool mp2) {
-  const double n = (double)m.nov;
-  if (mp2) return 2.0 * 2.0 * m.nb * (double)m.nb * n * m.na + 2.0 * m.nb * (double)m.nb * m.nb * n;
-  return n * n * n + 2.0 * m.nb * (double)m.nb * n * m.na;
+// Relative cost of one pass: the n_ov^3 eigensolve and the residue contraction (one per
+// spin channel); for qsMP2 the direct and exchange factors and the Sigma contraction.
+double pass_cost_of(long long nb, long long na, long long nov, bool open, bool mp2) {
+  const double n = (double)nov, b = (double)nb, a = (double)na;
+  if (mp2) return 2.0 * 2.0 * b * b * n * a + 2.0 * b * b * b * n;
+  return n * n * n + (open ? 2.0 : 1.0) * 2.0 * b * b * n * a;
+}
+
+double pass_cost(const MolBuf& m, bool mp2) { return pass_cost_of(m.nb, m.na, m.nov, m.dn != nullptr, mp2); }
+
+// Longest-processing-time-first: items in order of decreasing cost (equal costs by
+// index), each to the lane with the least load so far (equal loads: the lowest lane).
+// Returns the items of each of the max(1, min(lanes, items)) lanes in issue order.
+std::vector<std::vector<int>> lpt_assign(const std::vector<double>& cost, int lanes) {
+  const int n = (int)cost.size();
+  const int nl = std::max(1, std::min(lanes, n));
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<std::vector<int>> out(nl);
+  std::vector<double> load(nl, 0.0);
+  for (int k : order) {
+    int best = 0;
+    for (int j = 1; j < nl; ++j)
+      if (load[j] < load[best]) best = j;
+    out[best].push_back(k);
+    load[best] += cost[k];
+  }
+  return out;
 }
 
 struct Plan {
   std::vector<std::vector<int>> lane_mols;   // molecules of each lane, in issue order
 };
 
-// Longest-processing-time-first assignment of molecules to at most `lanes` lanes.
 int lanes_wanted(molgw_ctx c) {
   if (c->opts.lanes > 0) return std::min(c->opts.lanes, kMaxLanes);
   return c->tuned_lanes > 0 ? c->tuned_lanes : kDefaultLanes;
 }
 
+// The molecules spread over at most `lanes` (0: lanes_wanted) lanes by lpt_assign.
 Plan plan_batch(molgw_ctx c, const std::vector<int>& mols, int lanes = 0) {
-  int want = lanes > 0 ? lanes : lanes_wanted(c);
-  want = std::max(1, std::min(std::min(want, kMaxLanes), (int)mols.size()));
-  std::vector<int> order(mols);
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int b) {
-                     return pass_cost(c->mols[a], use_mp2(c)) > pass_cost(c->mols[b], use_mp2(c));
-                   });
+  const int want = std::min(lanes > 0 ? lanes : lanes_wanted(c), kMaxLanes);
+  std::vector<double> cost;
+  for (int k : mols) cost.push_back(pass_cost(c->mols[k], use_mp2(c)));
   Plan p;
-  p.lane_mols.resize(want);
-  std::vector<double> load(want, 0.0);
-  for (int k : order) {
-    int best = 0;
-    for (int j = 1; j < want; ++j)
-      if (load[j] < load[best]) best = j;
-    p.lane_mols[best].push_back(k);
-    load[best] += pass_cost(c->mols[k], use_mp2(c));
+  for (const auto& items : lpt_assign(cost, want)) {
+    p.lane_mols.emplace_back();
+    for (int i : items) p.lane_mols.back().push_back(mols[i]);
   }
   return p;
 }
@@ -1364,6 +1379,29 @@ int molgw_b200_autotune(molgw_ctx c, int32_t* lanes_out) {
 }
 
 int32_t molgw_b200_lanes(molgw_ctx c) { return c ? lanes_wanted(c) : 0; }
+
+int molgw_b200_plan_batch(int n_mols, const int32_t* n_basis, const int32_t* n_aux, const int32_t* n_occ_up,
+                          const int32_t* n_occ_dn, uint32_t flags, int lanes, int32_t* lane_of, int32_t* slot) {
+  if (n_mols < 1 || !n_basis || !n_aux || !n_occ_up || !lane_of || lanes < 0) return MOLGW_E_ARG;
+  const bool mp2 = (flags & MOLGW_FLAG_QSMP2) != 0;
+  std::vector<double> cost(n_mols);
+  for (int k = 0; k < n_mols; ++k) {
+    const long long nb = n_basis[k], na = n_aux[k], nu = n_occ_up[k];
+    const long long nd = n_occ_dn ? n_occ_dn[k] : -1;
+    const bool open = nd >= 0;
+    if (nb < 2 || na < 1 || nu < 0 || nu >= nb) return MOLGW_E_ARG;
+    if (open ? (nd >= nb || nu + nd < 1 || mp2) : nu < 1) return MOLGW_E_ARG;
+    const long long nov = nu * (nb - nu) + (open ? nd * (nb - nd) : 0);
+    cost[k] = pass_cost_of(nb, na, nov, open, mp2);
+  }
+  const auto plan = lpt_assign(cost, std::min(lanes > 0 ? lanes : kDefaultLanes, kMaxLanes));
+  for (int j = 0; j < (int)plan.size(); ++j)
+    for (int i = 0; i < (int)plan[j].size(); ++i) {
+      lane_of[plan[j][i]] = j;
+      if (slot) slot[plan[j][i]] = i;
+    }
+  return (int)plan.size();
+}
 
 int64_t molgw_b200_graph_replays(molgw_ctx c) {
   if (!c) return 0;

@@ -39,7 +39,8 @@ EXPORTS = ["molgw_b200_create", "molgw_b200_set_ri", "molgw_b200_set_orbitals", 
            "molgw_b200_launch_count", "molgw_b200_set_timing", "molgw_b200_destroy",
            "molgw_b200_status_string", "molgw_b200_eigh_noalloc", "molgw_b200_graph_replays",
            "molgw_b200_tc_gemm", "molgw_b200_autotune", "molgw_b200_lanes", "molgw_b200_g0w0",
-           "molgw_b200_g0w0_window", "molgw_b200_inject_fault", "molgw_b200_set_orbitals_open"]
+           "molgw_b200_g0w0_window", "molgw_b200_inject_fault", "molgw_b200_set_orbitals_open",
+           "molgw_b200_plan_batch"]
 NOALLOC_NMAX = 256
 
 
@@ -94,6 +95,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "molgw_b200_destroy": ([vp], ip),
         "molgw_b200_status_string": ([ip], ctypes.c_char_p),
         "molgw_b200_eigh_noalloc": ([ip, dp, dp, dp, vp], ip),
+        "molgw_b200_plan_batch": ([ip, vp, vp, vp, vp, ctypes.c_uint32, ip, vp, vp], ip),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -108,6 +110,26 @@ def status_string(code: int) -> str:
         return load().molgw_b200_status_string(code).decode()
     except Exception:  # noqa: BLE001 - only used to decorate an error message
         return "?"
+
+
+def plan_batch(n_basis, n_aux, n_occ, n_occ_dn=None, flags: int = 0, lanes: int = 0):
+    """Lane plan of a batch without a device (molgw_b200_plan_batch): returns
+    (lane_of, slot), int32 arrays over the molecules.  ``n_occ_dn`` None = all closed
+    shells, else per molecule with -1 for a closed shell."""
+    cols = [np.ascontiguousarray(x, dtype=np.int32) for x in (n_basis, n_aux, n_occ)]
+    n = cols[0].size
+    if any(c.size != n for c in cols):
+        raise ValueError("n_basis, n_aux and n_occ must have the same length")
+    dn = None if n_occ_dn is None else np.ascontiguousarray(n_occ_dn, dtype=np.int32)
+    if dn is not None and dn.size != n:
+        raise ValueError("n_occ_dn must have one entry per molecule")
+    lane_of, slot = np.empty(n, np.int32), np.empty(n, np.int32)
+    r = load().molgw_b200_plan_batch(n, cols[0].ctypes.data, cols[1].ctypes.data, cols[2].ctypes.data,
+                                     None if dn is None else dn.ctypes.data, flags, lanes,
+                                     lane_of.ctypes.data, slot.ctypes.data)
+    if r < 0:
+        raise MolgwError(r, "plan_batch")
+    return lane_of, slot
 
 
 def _ptr(a, n: int | None = None):
