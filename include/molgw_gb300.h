@@ -204,7 +204,7 @@ int molgw_b200_g0w0(molgw_ctx ctx, int mol, double* eps_qp, double* z, double* s
  * window of states whose self-energy is computed): the residues w^s_pm are formed
  * for those rows p alone, so their cost scales with p_end - p_begin.  Outputs have
  * p_end - p_begin entries; in the fetch items (length n_basis) only the window is
- * updated.  0 <= p_begin < p_end <= n_basis (else MOLGW_E_ARG); with mol = -1 the
+ * updated (entries that no window has computed since set_orbitals are NaN).  0 <= p_begin < p_end <= n_basis (else MOLGW_E_ARG); with mol = -1 the
  * window is clipped to each molecule's n_basis. */
 int molgw_b200_g0w0_window(molgw_ctx ctx, int mol, int p_begin, int p_end, double* eps_qp, double* z,
                            double* sigma_c_diag);

@@ -892,6 +892,8 @@ int molgw_b200_set_orbitals(molgw_ctx c, int mol, int n_occ, const double* eps, 
   Exec& ex = c->lanes[0].ex;
   check_finite(ex, m.eps, nb);
   check_finite(ex, m.C, (long long)nb * nb);
+  // all-ones bytes are a NaN: G0W0 entries that no window has computed for these orbitals
+  cudaMemsetAsync(m.g0w0, 0xFF, 3 * (size_t)nb * sizeof(double), c->st);
   m.have_orb = true;
   m.b_valid = m.jx_valid = m.rpa_valid = m.sigma_valid = false;
   m.have_b = m.have_rpa = m.have_jx = m.have_sigma = m.have_g0w0 = false;

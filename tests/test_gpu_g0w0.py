@@ -119,6 +119,23 @@ def test_g0w0_state_window():
     np.testing.assert_allclose(s, r["sigma_c_diag"][lo:hi], rtol=0, atol=1e-10 * np.max(np.abs(r["sigma_c_diag"])))
 
 
+def test_g0w0_entries_outside_the_window_are_nan():
+    nb, no, na = 40, 8, 96
+    m = sy.molecule(nb, no, na, 3)
+    with lib_context() as ctx:
+        load_mol(ctx, 0, m)
+        e = np.empty(4)
+        ctx.g0w0_window(0, no - 2, no + 2, e)
+        full, z = np.empty(nb), np.empty(nb)
+        ctx.fetch(0, "eps_qp", full)
+        ctx.fetch(0, "Z", z)
+    inside = np.zeros(nb, bool)
+    inside[no - 2:no + 2] = True
+    assert np.array_equal(full[inside], e)
+    assert np.all(np.isfinite(z[inside]))
+    assert np.all(np.isnan(full[~inside])) and np.all(np.isnan(z[~inside]))
+
+
 def test_g0w0_window_arguments():
     from paper_2210_17093_gb300 import MolgwError
     m = sy.molecule(24, 5, 72, 0)
