@@ -50,3 +50,20 @@ def test_create_rejects_bad_opts_without_touching_the_device(lib):
     assert lib.molgw_b200_create(ctypes.byref(o), ctypes.byref(h)) == -1
     assert h.value is None
     assert lib.molgw_b200_destroy(None) == 0
+
+
+def test_no_cpu_fallback(lib):
+    """Without a usable CUDA device the product path raises; a missing library raises on load."""
+    import torch
+    from paper_2210_17093_gb300 import Context, MolgwError, native
+    with pytest.raises(RuntimeError, match="not built"):
+        saved, native._lib = native._lib, None
+        try:
+            native.load(os.path.join(ROOT, "no_such_library.so"))
+        finally:
+            native._lib = saved
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: covered by the gpu tests")
+    with pytest.raises(MolgwError) as e:
+        Context()
+    assert e.value.code == -4          # MOLGW_E_CUDA
