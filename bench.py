@@ -132,20 +132,26 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.seek(0)
-        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 9]
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            try:
-                sm.append(float(r[1]))
-                smax = float(r[2])
-            except ValueError:
-                continue
-            for k, nm in enumerate(names):
-                if r[5 + k].strip().lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return summarise_clocks(self.f.read())
+
+
+def summarise_clocks(text):
+    """Median SM clock, maximum SM clock and the throttle reasons seen in the CSV rows of
+    ClockSampler.Q (noheader, nounits); rows that do not parse are skipped."""
+    rows = [r for r in csv.reader(io.StringIO(text)) if len(r) >= 9]
+    sm, smax, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        try:
+            sm.append(float(r[1]))
+            smax = float(r[2])
+        except ValueError:
+            continue
+        for k, nm in enumerate(names):
+            if r[5 + k].strip().lower() == "active":
+                reasons.add(nm)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+            "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def molecule_seed(wl, rank):
