@@ -247,14 +247,15 @@ def jacobi_eigh(A: np.ndarray, tol: float = 1e-15, max_sweeps: int = 100):
     """Cyclic Jacobi eigensolver for a small real symmetric matrix.
 
     Each rotation zeroes A_pq with the classical angle choice
-    (theta = (A_qq - A_pp) / (2 A_pq), t = sign(theta) / (|theta| + sqrt(theta^2 + 1))).
+    (theta = (A_qq - A_pp) / (2 A_pq), t = sign(theta) / (|theta| + sqrt(theta^2 + 1)),
+    which is 1 / (2 theta) to working precision once theta^2 would overflow).
     Returns eigenvalues ascending and eigenvectors as columns.
     """
     A = np.array(A, dtype=np.float64, copy=True)
     n = A.shape[0]
     V = np.eye(n)
     for _ in range(max_sweeps):
-        off = math.sqrt(np.sum(A * A) - np.sum(np.diag(A) ** 2))
+        off = math.sqrt(np.sum((A - np.diag(np.diag(A))) ** 2))
         if off <= tol * max(1.0, math.sqrt(np.sum(A * A))):
             break
         for p in range(n - 1):
@@ -263,7 +264,10 @@ def jacobi_eigh(A: np.ndarray, tol: float = 1e-15, max_sweeps: int = 100):
                 if apq == 0.0:
                     continue
                 theta = (A[q, q] - A[p, p]) / (2.0 * apq)
-                t = math.copysign(1.0, theta) / (abs(theta) + math.sqrt(theta * theta + 1.0))
+                if abs(theta) > 1e150:
+                    t = 0.5 / theta
+                else:
+                    t = math.copysign(1.0, theta) / (abs(theta) + math.sqrt(theta * theta + 1.0))
                 c = 1.0 / math.sqrt(t * t + 1.0)
                 s = t * c
                 Ap, Aq = A[:, p].copy(), A[:, q].copy()
