@@ -99,6 +99,26 @@ def casida_M(A: np.ndarray, Bc: np.ndarray, D: np.ndarray) -> np.ndarray:
     return sq[:, None] * (A + Bc) * sq[None, :]
 
 
+def casida_M_apply(B: np.ndarray, eps: np.ndarray, n_occ: int):
+    """The product x -> M x of the symmetric reduction of Eq. (Casida.AB.XY) without
+    forming M: M x = D^2 x + 4 D^(1/2) B_ia^T (B_ia (D^(1/2) x)), with K = B_ia^T B_ia of
+    Eq. (Casida.A/B) applied as two products over the auxiliary index (for workloads
+    whose n_ov x n_ov matrix is too large to form on the host).  Returns (apply, D)."""
+    nb = eps.shape[0]
+    i, a = transitions(nb, n_occ)
+    D = eps[a] - eps[i]
+    Bia = np.ascontiguousarray(B[:, i, a])        # [na, n_ov]
+    sq = np.sqrt(D)
+
+    def apply(x):
+        x = np.asarray(x, dtype=np.float64)
+        y = sq[:, None] * x if x.ndim == 2 else sq * x
+        k = Bia.T @ (Bia @ y)
+        return (D * D)[:, None] * x + 4.0 * (sq[:, None] * k) if x.ndim == 2 else D * D * x + 4.0 * sq * k
+
+    return apply, D
+
+
 def rpa_eigensolve(M: np.ndarray, D: np.ndarray):
     """Omega_s ascending and (X+Y)^s from the eigenpairs of M.
 
@@ -133,11 +153,22 @@ def gw_residues(B: np.ndarray, XpY: np.ndarray, n_occ: int):
 
     R_Ps = sum_t B^P_t (X+Y)_ts (t = ia); returns (R [na, n_ov], w [n_ov, nb, nb]).
     """
-    nb = B.shape[1]
-    i, a = transitions(nb, n_occ)
-    R = B[:, i, a] @ XpY
+    R = residue_weights(B, XpY, n_occ)
     w = np.einsum("Ppq,Ps->spq", B, R, optimize=True)
     return R, w
+
+
+def residue_weights(B: np.ndarray, XpY: np.ndarray, n_occ: int) -> np.ndarray:
+    """R_Ps = sum_t B^P_t (X+Y)_ts over the transitions t = ia: the auxiliary side of
+    Eq. (w.residue), so that w^s_pq = sum_P B^P_pq R_Ps.  [na, n_ov]."""
+    nb = B.shape[1]
+    i, a = transitions(nb, n_occ)
+    return B[:, i, a] @ XpY
+
+
+def residues_of_state(B: np.ndarray, R: np.ndarray, m: int) -> np.ndarray:
+    """w^s_pm for one orbital m, every (p, s): sum_P B^P_pm R_Ps (Eq. w.residue). [p, s]."""
+    return B[:, :, m].T @ R
 
 
 # ----------------------------------------------------------------------------
@@ -178,6 +209,21 @@ def sigma_c_rows(w: np.ndarray, eps: np.ndarray, Omega: np.ndarray, n_occ: int,
         shift = Omega if m < n_occ else -Omega        # -eps_i + Omega_s | -eps_a - Omega_s
         x = eps[:, None] - eps[m] + shift[None, :]    # [p, s]
         wm = w[:, :, m].T                             # [p, s] = w^s_pm
+        S += (wm * g_real(x, eta)) @ wm.T
+    return S
+
+
+def sigma_c_rows_from_R(B: np.ndarray, R: np.ndarray, eps: np.ndarray, Omega: np.ndarray,
+                        n_occ: int, eta: float) -> np.ndarray:
+    """``sigma_c_rows`` with the residues of each orbital m formed inside the loop over
+    m (``residues_of_state``), so that w [n_ov, nb, nb] is never held whole (it is
+    33 GB at n_basis = 400).  The same sums in the same order as ``sigma_c_rows``."""
+    nb = eps.shape[0]
+    S = np.zeros((nb, nb))
+    for m in range(nb):
+        shift = Omega if m < n_occ else -Omega
+        x = eps[:, None] - eps[m] + shift[None, :]
+        wm = residues_of_state(B, R, m)
         S += (wm * g_real(x, eta)) @ wm.T
     return S
 
@@ -341,13 +387,17 @@ def qs_update(h_mo: np.ndarray, J: np.ndarray, Sx: np.ndarray, Sc: np.ndarray,
 # One qsGW iteration
 # ----------------------------------------------------------------------------
 def qsgw_pass(L: np.ndarray, eps: np.ndarray, C: np.ndarray, n_occ: int,
-              eta: float, h_mo: np.ndarray | None = None, correlation: bool = True) -> dict:
+              eta: float, h_mo: np.ndarray | None = None, correlation: bool = True,
+              keep_w: bool = True) -> dict:
     """One RI-qsGW iteration: Eqs. (AO.to.MO) -> (Casida) -> (w.residue) ->
     (Sigma.c.GW, Sigma.c.qsGW.real, K) -> (H, GEP).
 
     ``h_mo`` is the one-body Hamiltonian in the basis of the current orbitals; if
     None it is derived from the input read as an HF solution (reading R5).
     ``correlation=False`` sets Sigma_c = 0 (the exchange-only limit).
+    ``keep_w=False`` forms the residues of one orbital m at a time inside the sum
+    of Eq. (Sigma.c.GW) and returns w = None (for workloads whose w does not fit
+    in host memory); the values are the same.
     Returns every intermediate and the updated (eps', C', h_MO').
     """
     B = ri_mo_transform(L, C)
@@ -355,11 +405,17 @@ def qsgw_pass(L: np.ndarray, eps: np.ndarray, C: np.ndarray, n_occ: int,
         h_mo = hf_core_mo(B, eps, n_occ)
     A, Bc, D = casida_AB(B, eps, n_occ)
     M = casida_M(A, Bc, D)
+    del A, Bc
     Omega, XpY, Z = rpa_eigensolve(M, D)
-    R, w = gw_residues(B, XpY, n_occ)
+    if keep_w:
+        R, w = gw_residues(B, XpY, n_occ)
+    else:
+        R, w = residue_weights(B, XpY, n_occ), None
     Sx = sigma_x(B, n_occ)
-    if correlation:
+    if correlation and keep_w:
         Sc = sigma_c_qs(sigma_c_rows(w, eps, Omega, n_occ, eta))
+    elif correlation:
+        Sc = sigma_c_qs(sigma_c_rows_from_R(B, R, eps, Omega, n_occ, eta))
     else:
         Sc = np.zeros_like(Sx)
     J = hartree(B, n_occ)

@@ -61,6 +61,61 @@ def test_two_level_closed_form(params):
     np.testing.assert_allclose(r["eps_new"], [tr / 2 - disc, tr / 2 + disc], rtol=1e-13, atol=1e-15)
 
 
+@pytest.mark.parametrize("params", [dict(), dict(e0=-3.0, e1=1.5, b=0.9)])
+def test_two_level_closed_form_streamed_residues(params):
+    """The same closed form through the path that forms the residues of one orbital m
+    at a time (keep_w=False, used for the large stored workloads)."""
+    L, eps, C = two_level(**params)
+    b00, b, b11 = L[0, 0, 0], L[0, 0, 1], L[0, 1, 1]
+    delta = eps[1] - eps[0]
+    eta = 1e-3
+    r = qsgw.qsgw_pass(L, eps, C, 1, eta, keep_w=False)
+    assert r["w"] is None
+    Om = math.sqrt(delta * delta + 4.0 * delta * b * b)
+    w = np.array([[b00, b], [b, b11]]) * b * math.sqrt(2.0 * delta / Om)
+    g = lambda x: x / (x * x + eta * eta)
+    S = np.zeros((2, 2))
+    for p in range(2):
+        for q in range(2):
+            S[p, q] = w[p, 0] * w[q, 0] * g(eps[p] - eps[0] + Om) + w[p, 1] * w[q, 1] * g(eps[p] - eps[1] - Om)
+    np.testing.assert_allclose(r["sigma_c"], 0.5 * (S + S.T), rtol=1e-12, atol=1e-16)
+
+
+@pytest.mark.parametrize("seed,nb,no,na", [(91, 6, 2, 5), (92, 9, 4, 20), (93, 7, 1, 3)])
+def test_streamed_residues_match_index_loops(seed, nb, no, na):
+    """Sigma_c with per-orbital residues equals four nested loops over (p, q, m, s) of
+    Eq. (Sigma.c.GW) on the full residues, and the residues of one orbital are the
+    slice w[:, :, m] of Eq. (w.residue)."""
+    m = tiny(seed, nb, no, na)
+    full = qsgw.qsgw_pass(m["L"], m["eps"], m["C"], no, ETA)
+    lean = qsgw.qsgw_pass(m["L"], m["eps"], m["C"], no, ETA, keep_w=False)
+    S_loop = brute.sigma_c_loops(full["w"], m["eps"], full["Omega"], no, ETA)
+    np.testing.assert_allclose(lean["sigma_c"], 0.5 * (S_loop + S_loop.T),
+                               atol=1e-12 * max(1.0, np.abs(S_loop).max()))
+    for k in range(nb):
+        np.testing.assert_allclose(qsgw.residues_of_state(full["B"], lean["R"], k), full["w"][:, :, k].T,
+                                   atol=1e-14)
+    np.testing.assert_allclose(lean["eps_new"], full["eps_new"], atol=1e-12)
+
+
+@pytest.mark.parametrize("seed,nb,no,na", [(95, 9, 4, 20), (96, 12, 3, 7)])
+def test_casida_operator_equals_the_formed_matrix(seed, nb, no, na):
+    """The matrix-free product M x (used for the largest workload) equals the formed
+    M of Eq. (Casida.AB.XY) times x, whose eigenvalues the brute-force Casida pin fixes."""
+    m = tiny(seed, nb, no, na)
+    B = qsgw.ri_mo_transform(m["L"], m["C"])
+    A, Bc, D = qsgw.casida_AB(B, m["eps"], no)
+    M = qsgw.casida_M(A, Bc, D)
+    apply, D2 = qsgw.casida_M_apply(B, m["eps"], no)
+    np.testing.assert_array_equal(D2, D)
+    x = np.random.default_rng(seed).standard_normal((D.shape[0], 3))
+    np.testing.assert_allclose(apply(x), M @ x, rtol=1e-12, atol=1e-13 * np.abs(M).max())
+    np.testing.assert_allclose(apply(x[:, 0]), M @ x[:, 0], rtol=1e-12, atol=1e-13 * np.abs(M).max())
+    lam = np.linalg.eigvalsh(np.column_stack([apply(e) for e in np.eye(D.shape[0])]))
+    assert np.sum(lam) == pytest.approx(np.trace(M), rel=1e-12)
+    np.testing.assert_allclose(np.sqrt(lam), qsgw.rpa_eigensolve(M, D)[0], rtol=1e-12)
+
+
 # --------------------------------------------------------------------------
 # P2: brute-force non-Hermitian Casida over spin orbitals
 # --------------------------------------------------------------------------
