@@ -220,6 +220,17 @@ int molgw_b200_sync(molgw_ctx ctx);
  * is made and no kernel is stopped.  MOLGW_E_ARG for any other code. */
 int molgw_b200_inject_fault(molgw_ctx ctx, int code);
 
+/* Test hook for the bounded device waits: a grid barrier of the tridiagonalisation's
+ * persistent panel kernel gives up after `grid_spins` polls (default 2^24, about 1 s)
+ * with MOLGW_E_TIMEOUT, raising an abort flag on which every CTA of the launch leaves;
+ * the float64 bisection of an eigenvalue stops after `bisect_rounds` rounds (default
+ * and maximum 128) with MOLGW_E_NOCONV.  A negative value restores the default.  With
+ * lowered bounds the results of the pass are not meaningful; the latched code reaches
+ * the caller as for any device-found error, and once the defaults are back the
+ * context computes as before (every launch clears its barrier block).  No fault is
+ * made and no wait is endless.  MOLGW_E_ARG for a NULL context. */
+int molgw_b200_set_wait_limits(molgw_ctx ctx, long long grid_spins, int bisect_rounds);
+
 /* Copy an intermediate of the last pass of molecule `mol` into out[count]
  * (count must equal the item's size).  Items: */
 enum molgw_item {
@@ -259,12 +270,14 @@ int molgw_b200_eigh(molgw_ctx ctx, int n, const double* A, double* w, double* Z)
  * after the host program has claimed its memory).  The paper has no counterpart:
  * it is a service of this library.
  *   n <= MOLGW_NOALLOC_NMAX; A[n][n] symmetric, w[n], Z[n][n] (may be NULL) are
- *   DEVICE pointers on the current device (else MOLGW_E_ARG); results as for
- *   molgw_b200_eigh.  stream: the cudaStream_t to run on (NULL = legacy default).
- *   All workspace is one fixed device array of 5.07 MB inside the library, held
- *   by every GPU that loads it until the process exits; no call allocates or
- *   frees.  The first call on a device looks up that array's address (once per
- *   device, with the device current), so make it before any stream capture.
+ *   DEVICE (or managed) pointers of the current device (host memory, or memory of
+ *   another device: MOLGW_E_ARG); results as for molgw_b200_eigh.  stream: the
+ *   cudaStream_t to run on (NULL = legacy default).
+ *   All workspace is one fixed device array of 634,042 doubles (5.07 MB) inside
+ *   the library, held by every GPU that loads it until the process exits; no call
+ *   allocates or frees.  The first call on a device (and the first after its
+ *   context was replaced, e.g. by cudaDeviceReset) looks up that array's address
+ *   with the device current, so make it before any stream capture.
  *   The call synchronises `stream` and returns the device status.
  *   Every call shares the one array: calls that overlap on the GPU (other
  *   streams, other host threads) race and must be serialised by the caller. */

@@ -51,6 +51,29 @@ def test_noalloc_matches_eigh_on_consecutive_calls():
             assert np.max(np.abs(A @ Z_na - Z_na * w_na[None, :])) <= 1e-11 * scale
 
 
+def test_noalloc_eigenvalues_only_and_default_stream():
+    """Z = NULL (eigenvalues only) and stream = NULL (the legacy default stream) give
+    the eigenvalues of molgw_b200_eigh, twice in a row."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_17093_gb300 import Context, native
+
+    lib = native.load()
+    with Context(stream=torch.cuda.current_stream()) as ctx:
+        for n, seed, spread in [(130, 5, 3.0), (256, 6, 2.0)]:
+            A = _sym(n, seed, spread)
+            Ad = torch.from_numpy(A).cuda()
+            w = torch.empty(n, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            rc = lib.molgw_b200_eigh_noalloc(n, ctypes.c_void_p(Ad.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+                                             None, None)
+            assert rc == 0, native.STATUS.get(rc, rc)
+            w_ref = np.empty(n)
+            ctx.eigh(np.ascontiguousarray(A), w_ref, None)
+            assert np.max(np.abs(w.cpu().numpy() - w_ref)) <= 1e-12 * np.abs(w_ref).max() * n ** 0.5
+
+
 def test_noalloc_rejects_bad_arguments():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
@@ -66,3 +89,10 @@ def test_noalloc_rejects_bad_arguments():
     h = np.zeros(4)
     assert lib.molgw_b200_eigh_noalloc(2, h.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(w.data_ptr()),
                                        None, None) == -1          # host input
+    hp = torch.zeros(4, dtype=torch.float64).pin_memory()        # pinned host memory is host memory
+    assert lib.molgw_b200_eigh_noalloc(2, ctypes.c_void_p(hp.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+                                       None, None) == -1
+    assert lib.molgw_b200_eigh_noalloc(2, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(hp.data_ptr()),
+                                       None, None) == -1          # host output
+    assert lib.molgw_b200_eigh_noalloc(0, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+                                       None, None) == -1          # empty
