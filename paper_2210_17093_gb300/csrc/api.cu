@@ -57,6 +57,8 @@ struct molgw_ctx_s {
   int tuned_lanes = 0;           // molgw_b200_autotune's choice (0: none)
   int g0w0_p0 = 0, g0w0_p1 = 0;  // state window of the G0W0 call in flight (clipped per molecule)
   GemmTuner tuner;               // float64 GEMM tile choices (molgw_b200_autotune)
+  long long grid_spins = kGridSpinLimit;   // molgw_b200_set_wait_limits
+  int bisect_rounds = kBisectRounds;
 };
 
 namespace {
@@ -177,6 +179,8 @@ int lane_get(molgw_ctx c, int k, Lane** out) {
     l.ex.status = c->d_status;
     l.ex.timer = &c->timer;
     l.ex.tuner = &c->tuner;
+    l.ex.grid_spins = c->grid_spins;
+    l.ex.bisect_rounds = c->bisect_rounds;
     c->lanes.push_back(l);
   }
   *out = &c->lanes[k];
@@ -1113,6 +1117,18 @@ int molgw_b200_inject_fault(molgw_ctx c, int code) {
   DeviceGuard g(c->device);
   k_inject_status<<<1, 1, 0, c->st>>>(c->d_status, code);
   return launch_status();
+}
+
+int molgw_b200_set_wait_limits(molgw_ctx c, long long grid_spins, int bisect_rounds) {
+  if (!c) return MOLGW_E_ARG;
+  c->grid_spins = grid_spins < 0 ? kGridSpinLimit : grid_spins;
+  c->bisect_rounds = bisect_rounds < 0 ? kBisectRounds : std::min(bisect_rounds, kBisectRounds);
+  for (Lane& l : c->lanes) {
+    l.ex.grid_spins = c->grid_spins;
+    l.ex.bisect_rounds = c->bisect_rounds;
+  }
+  ++c->gen;   // a captured graph holds the old bounds in its launch parameters
+  return MOLGW_OK;
 }
 
 int molgw_b200_fetch(molgw_ctx c, int mol, int item, double* out, size_t count) {

@@ -44,6 +44,11 @@ struct KTimer {
 
 struct GemmTuner;
 
+// Bounds of the device-side waits and iterations (defaults; molgw_b200_set_wait_limits
+// lowers them for the failure-path tests).  A grid barrier polls about 1 s at most.
+constexpr long long kGridSpinLimit = 1LL << 24;
+constexpr int kBisectRounds = 128;
+
 struct Exec {
   cudaStream_t st = nullptr;
   GemmTuner* tuner = nullptr;  // tile choices of the float64 GEMM (per context), or none
@@ -52,6 +57,8 @@ struct Exec {
   bool capturing = false;  // inside stream capture: no events, no allocation
   int coop_cap = 0;        // CTAs a cooperative launch may use (0: the whole device);
                            // concurrent lanes split the device between them
+  long long grid_spins = kGridSpinLimit;  // polls of a grid barrier before MOLGW_E_TIMEOUT
+  int bisect_rounds = kBisectRounds;      // float64 bisection rounds before MOLGW_E_NOCONV
 };
 
 // Scoped marker: records a start/stop event pair around the kernels launched in

@@ -149,7 +149,7 @@ __device__ __forceinline__ void multisect(T& lo, T& hi, int cnt_l, T x_l, int k,
 // used).  The float64 phase then multisects to 2 eps |lambda| + 4 eps ||T||.
 __global__ void __launch_bounds__(32) k_bisect(const double* d, const double* e2, const float* d32,
                                                 const float* e232, const double* g, int n, double* lam,
-                                                int* status) {
+                                                int* status, int max_rounds) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = gt >> 2, l = gt & 3;
   const int lane = threadIdx.x & 31;
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(32) k_bisect(const double* d, const double* e2
   // the result is the bracket's midpoint once it is 2 eps |lambda| + atol wide.
   bool ok = false;
   double xn = 0.5 * (lo + hi), dn = hi - lo;
-  for (int it = 0; it < 128; ++it) {
+  for (int it = 0; it < max_rounds; ++it) {
     const double tol = 2.0 * eps * fmax(fabs(lo), fabs(hi)) + atol;
     if (hi - lo <= tol) { ok = true; break; }
     const bool newton = xn > lo && xn < hi;
@@ -375,7 +375,8 @@ void tridiag_eigvals(Exec& ex, EigWork& w, int n) {
   KScope ks(ex, MOLGW_K_BISECT, 3);
   k_gersh<<<1, 256, 0, ex.st>>>(w.d, w.e, n, g);
   k_e2<<<ceil_div(n, 256), 256, 0, ex.st>>>(w.d, w.e, e2, d32, e232, n);
-  k_bisect<<<ceil_div(4LL * n, 32), 32, 0, ex.st>>>(w.d, e2, d32, e232, g, n, w.lam, ex.status);
+  k_bisect<<<ceil_div(4LL * n, 32), 32, 0, ex.st>>>(w.d, e2, d32, e232, g, n, w.lam, ex.status,
+                                                     ex.bisect_rounds);
 }
 
 void tridiag_eigvecs(Exec& ex, EigWork& w, int n, double* ZT, long long ldz) {

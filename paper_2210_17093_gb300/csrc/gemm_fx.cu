@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(NT, 1) fx_gemm_kernel(const __grid_constant__ 
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full[STAGES], empty[STAGES], accf[2], acce[2];
+  __shared__ uint64_t full[STAGES], empty[STAGES], accf[2], acce[2], drain;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(NT, 1) fx_gemm_kernel(const __grid_constant__ 
       mbar_init(&accf[b], 1);
       mbar_init(&acce[b], EPI_THREADS);
     }
+    mbar_init(&drain, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -249,6 +250,21 @@ __global__ void __launch_bounds__(NT, 1) fx_gemm_kernel(const __grid_constant__ 
         mma_commit(&empty[s]);
       }
       if (ok) mma_commit(&accf[buf]);
+    }
+    if (!ok && i > 0) {
+      // error path: the MMAs already issued finish before TMEM is released (bounded
+      // wait that the abort flag does not cut short)
+      mma_commit(&drain);
+      const uint32_t a = smem_u32(&drain);
+      for (long long it = 0; it < SPIN_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(0u)
+            : "memory");
+        if (done) break;
+      }
     }
   } else if (warp >= 4) {
     const int q = warp & 3, h = (warp - 4) >> 2;            // TMEM lane quarter, column half

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256, 1)
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full[3], empty[3], done;
+  __shared__ uint64_t full[3], empty[3], done, drain;
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int m0 = bm * BM, n0 = bn * BN;
@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(256, 1)
       mbar_init(&empty[s], 1);
     }
     mbar_init(&done, 1);
+    mbar_init(&drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 2) {
@@ -164,7 +165,8 @@ __global__ void __launch_bounds__(256, 1)
     const uint32_t ty = (PREC == TC_TF32X3) ? 2u : 1u;
     const uint32_t idesc = (1u << 4) | (ty << 7) | (ty << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
     bool ok = true;
-    for (int i = 0; i < nk; ++i) {
+    int i = 0;
+    for (; i < nk; ++i) {
       const int s = i % STAGES;
       if (!mbar_wait(&full[s], (i / STAGES) & 1)) {
         set_status(p.status, MOLGW_E_TIMEOUT);
@@ -187,7 +189,14 @@ __global__ void __launch_bounds__(256, 1)
       }
       mma_commit(&empty[s]);
     }
-    if (ok) mma_commit(&done);
+    if (ok) {
+      mma_commit(&done);
+    } else if (i > 0) {
+      // error path: the MMAs already issued finish (bounded wait) before the CTA
+      // releases TMEM
+      mma_commit(&drain);
+      mbar_wait(&drain, 0);
+    }
   } else if (warp >= 4) {
     const int q = warp & 3;
     const bool ok = (nk > 0) ? mbar_wait(&done, 0) : true;

@@ -65,6 +65,7 @@ struct PanelParams {
   double* VW; double* WV;   // packed [V W] and [W V] of rows >= k1
   GridBar* bar;
   int* status;
+  long long spin_limit;     // polls of a grid barrier before it gives up
 };
 
 __device__ __forceinline__ double ldg_cg(const double* p) { return __ldcg(p); }
@@ -78,10 +79,12 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
 // Grid-wide barrier for a cooperative launch.  Arrival is one fire-and-forget
 // release increment of a counter that only grows during the launch (zeroed before
 // it); barrier number e of the launch is passed when the counter reaches
-// e * gridDim.x, seen with acquire loads.  The wait is bounded: after ~1 s without
-// progress it latches MOLGW_E_TIMEOUT, raises the abort flag and returns false so
-// that every CTA leaves the kernel.
-__device__ bool grid_sync(GridBar* bar, int* status, unsigned int& epoch) {
+// e * gridDim.x, seen with acquire loads.  The wait is bounded: after spin_limit
+// polls (~1 s with the default) without progress it latches MOLGW_E_TIMEOUT, raises
+// the abort flag and returns false so that every CTA leaves the kernel.  A CTA that
+// arrives last passes; it leaves at its next barrier, where the abort flag stops
+// its wait.
+__device__ bool grid_sync(GridBar* bar, int* status, unsigned int& epoch, long long spin_limit) {
   __shared__ int ok;
   __syncthreads();
   ++epoch;
@@ -93,7 +96,7 @@ __device__ bool grid_sync(GridBar* bar, int* status, unsigned int& epoch) {
     long long spins = 0;
     while (ld_acquire(&bar->count) < target) {
       if (*(volatile int*)&bar->abort != 0) { ok = 0; break; }
-      if (++spins > (1LL << 24)) {
+      if (++spins > spin_limit) {
         set_status(status, MOLGW_E_TIMEOUT);
         atomicExch(&bar->abort, 1);
         ok = 0;
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
       }
       __syncthreads();
     }
-    if (!grid_sync(p.bar, p.status, epoch)) return;
+    if (!grid_sync(p.bar, p.status, epoch, p.spin_limit)) return;
     if (j == 0) {
       if (t == 0) s_rank[2] = (s_rank[0] == 0) ? s_rank[1] : (int)ld_acquire(&p.bar->n0) + s_rank[1];
       __syncthreads();
@@ -404,7 +407,7 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
         J = Jn;
       }
     }
-    if (!grid_sync(p.bar, p.status, epoch)) return;
+    if (!grid_sync(p.bar, p.status, epoch, p.spin_limit)) return;
 
     // ---------------- P3: W column ----------------
     const int n3 = ceil_div_d(n - i - 1, RC);
@@ -459,7 +462,7 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
       p.tau[i] = h.tau;
       A[(i + 1) + (long long)i * ld] = 1.0;
     }
-    if (!grid_sync(p.bar, p.status, epoch)) return;
+    if (!grid_sync(p.bar, p.status, epoch, p.spin_limit)) return;
   }
 
   // ---------------- end of panel: last W correction and packing ----------------
@@ -527,6 +530,7 @@ void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
   PanelParams p{};
   p.n = n; p.A = A; p.Wp = w.Wp; p.d = w.d; p.e = w.e; p.tau = w.tau; p.scal = w.scal;
   p.status = ex.status;
+  p.spin_limit = ex.grid_spins;
   const int nrbt = ceil_div(n, TB);
   double* base = w.part;
   p.p_ss = base;   base += ceil_div(n, RC) + 1;
