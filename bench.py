@@ -78,7 +78,9 @@ def workload_flops(nb, no, na):
     """
     n = no * (nb - no)
     return {
-        "sigma": 2.0 * nb * nb * na * n + 2.0 * nb ** 3 * n,      # w^s_pm per m block + S += (w g) w^T
+        # residues w^s_pm over the pairs m <= p (w^s_pm = w^s_mp: nb (nb + 1) / 2 pairs of
+        # n_aux x n_ov products), then S += (w g) w^T per m
+        "sigma": 1.0 * nb * (nb + 1) * na * n + 2.0 * nb ** 3 * n,
         # Householder reduction of M: symmetric matrix-vector products (2n^3/3) in the
         # panel kernel, rank-2k trailing updates of the lower triangle (2n^3/3) in the GEMM
         "tridiag_panel": 2.0 / 3.0 * n ** 3 + 2.0 * 64 * n * n,
@@ -89,6 +91,85 @@ def workload_flops(nb, no, na):
         "sigma_x": 2.0 * nb * nb * na * no,
         "qs_update": 4.0 / 3.0 * nb ** 3 + 6.0 * nb ** 3,
     }
+
+
+CLASSES = ["gemm_f64", "tridiag_panel", "tridiag_syr2k", "bisect", "twisted", "backtransform", "sigma",
+           "gemm_tc", "misc"]
+FLAG_TC_AB_BIT, FLAG_EIG_TC_BIT = 1 << 4, 1 << 5
+# float64 instruction rate (2 per clock per SM), for the kernels counted in operations
+FP64_PEAK_GOPS = 152 * 2 * 2.07e9 / 1e9
+BISECT_ROUNDS = 7        # float64 rounds per eigenvalue after the float32 bracket (typical)
+
+
+def pad64(k):
+    return -(-k // 64) * 64
+
+
+def stage_rooflines(nb, no, na, stages_ms, precision="fp64", flags=0):
+    """Achieved fraction of its own roofline for every kernel class timed over one
+    qsGW iteration: float64 classes against the float64 pipe (useful flops of
+    workload_flops), tensor-core classes against the measured BF16 burst peak
+    (executed digit products), the slicing kernel of (e) against the measured HBM
+    copy bandwidth, and the bisection and twisted-vector kernels against the float64
+    instruction rate (their operation counts are estimates, stated per class)."""
+    n = no * (nb - no)
+    f = workload_flops(nb, no, na)
+    peaks = measured_peaks()
+    fx = precision == "bf16x10"
+    tc_ab = fx and bool(flags & FLAG_TC_AB_BIT)
+    eig_tc = bool(flags & FLAG_EIG_TC_BIT)
+    out = {}
+
+    def put(k, work, unit, peak, bound, what, extra=None):
+        ms = stages_ms.get(k)
+        if not ms or ms <= 0:
+            return
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        ach = work / (ms / 1e3) / scale
+        d = {"ms": round(ms, 3), "bound": bound, "work": what, "achieved": round(ach, 4), "peak": round(peak, 4),
+             "unit": unit, "frac": round(ach / peak, 4)}
+        if extra:
+            d.update(extra)
+        out[k] = d
+
+    bf16 = peaks["bf16_tflops"]
+    panel = f["tridiag_panel"] + 2.0 / 3.0 * nb ** 3
+    put("tridiag_panel", panel, "TFLOP/s", FP64_PEAK_TFLOPS, "alu",
+        "2n^3/3 + 128n^2 (symmetric mat-vecs, column updates) for M and H")
+    syr2k = f["tridiag_syr2k"] + 2.0 / 3.0 * nb ** 3
+    bt = f["backtransform"] + 2.0 * nb ** 3
+    if eig_tc:
+        for k, useful in (("tridiag_syr2k", syr2k), ("backtransform", bt)):
+            ms = stages_ms.get(k)
+            put(k, 28.0 * useful, "TFLOP/s", bf16, "tensor",
+                "28 BF16 digit products per useful float64 multiply-add (7-digit fixed point)",
+                {"fp64_equivalent_tflops": round(useful / (ms / 1e3) / 1e12, 3) if ms else None})
+    else:
+        put("tridiag_syr2k", syr2k, "TFLOP/s", FP64_PEAK_TFLOPS, "alu", "2n^3/3 rank-2k updates of the lower triangle")
+        put("backtransform", bt, "TFLOP/s", FP64_PEAK_TFLOPS, "alu", "4 n_aux n^2 (Q^T Xv, R = Y^T Z_T) + C' = C U")
+    put("bisect", 4.0 * BISECT_ROUNDS * 5.0 * (n * n + nb * nb) / 1e0, "Gop/s", FP64_PEAK_GOPS, "alu",
+        f"estimated: 4 lanes x {BISECT_ROUNDS} float64 rounds x 5 operations per Sturm step, n steps per eigenvalue")
+    put("twisted", 12.0 * (n * n + nb * nb), "Gop/s", FP64_PEAK_GOPS, "alu (serial recurrences: latency)",
+        "estimated: 3 passes x 4 float64 operations per step, n steps per eigenvector")
+    if fx:
+        groups = -(-pad64(na) // 1024)
+        nbytes = nb * nb * n * (8 * groups + 2 * 4 * 2)
+        put("sigma", nbytes, "GB/s", peaks["hbm_gbs"], "hbm",
+            "k_fx_sigma_slices: w partials read (8 B per 1024-wide group), digits of w and g w written (2 x 4 x 2 B)")
+        ex = 10.0 * 2 * (nb * nb * n * pad64(na) + nb * nb * nb * pad64(n))
+        if tc_ab:
+            ex += 10.0 * 2 * (2 * na * nb * nb * pad64(nb) + 0.5 * n * n * pad64(na))
+        put("gemm_tc", ex, "TFLOP/s", bf16, "tensor",
+            "10 BF16 digit products per useful multiply-add: (d), (e)" + (", (a), (b)" if tc_ab else ""))
+    else:
+        put("sigma", f["sigma"], "TFLOP/s", FP64_PEAK_TFLOPS, "alu",
+            "residues over the pairs m <= p and the Sigma_c contraction, float64")
+    g64 = f["sigma_x"] + 2.0 * nb * nb * na + 6.0 * nb ** 3
+    if not tc_ab:
+        g64 += f["ri_mo_transform"] + f["rpa_build"]
+    put("gemm_f64", g64, "TFLOP/s", FP64_PEAK_TFLOPS, "alu",
+        ("" if tc_ab else "(a) 4 n_aux nb^3, (b) n_aux n^2, ") + "Sigma_x, J, the H and h_MO rotations")
+    return out
 
 
 def config_dict(wl, precision):
@@ -213,15 +294,34 @@ def oracle_steps(wl, steps, warmup, eta):
     return (time.perf_counter() - t0) / max(steps, 1)
 
 
+# CPU seconds of one oracle iteration per workload on 16 Neoverse-V2 cores (measured), and
+# the CPU time the reference arm allows itself
+ORACLE_S_PER_ITER = {"A": 0.05, "B": 9.3, "C": 420.0, "E": 2400.0}
+ORACLE_BUDGET_S = 240.0
+
+
+def oracle_step_counts(wl, steps, warmup):
+    """Steps and warm-up of the oracle arm: those requested when they fit the CPU budget,
+    else as many steps as fit after one warm-up (at least one)."""
+    key = next((k for k, v in WORKLOADS.items() if v == wl), "B")
+    t = ORACLE_S_PER_ITER.get(key, 10.0)
+    if (steps + warmup) * t <= ORACLE_BUDGET_S:
+        return steps, warmup
+    w = min(warmup, 1)
+    return max(1, min(steps, int(ORACLE_BUDGET_S / t) - w)), w
+
+
 def run_reference(args, wl):
     world, rank, local, dist = dist_setup()
     if rank != 0:
         return 0
-    steps, warmup = min(args.steps, 3), min(args.warmup, 1)
+    steps, warmup = oracle_step_counts(wl, args.steps, args.warmup)
     t = oracle_steps(wl, steps, warmup, sy.ETA)
     cores = os.cpu_count()
     sample = (f"{steps} oracle iteration(s) after {warmup} warm-up of the same workload "
-              f"(seed {wl['seed']}), NumPy float64 with multithreaded BLAS")
+              f"(seed {wl['seed']}), NumPy float64 with multithreaded BLAS"
+              + ("" if (steps, warmup) == (args.steps, args.warmup) else
+                 f"; {args.steps} steps after {args.warmup} requested, cut to keep the CPU run near 4 minutes"))
     line = {
         "impl": "reference", "metric": METRIC, "value": t, "unit": "s", "n_gpus": args.gpus,
         "steps": steps, "warmup": warmup, "ms_per_step": t * 1e3, "higher_is_better": False,
@@ -264,6 +364,126 @@ def run_reference_batch(args):
     }
     print(json.dumps(line))
     return 0
+
+
+GOLDEN_C = os.path.join(ROOT, "tests", "golden", "qsgw_nb400_no80_na1200_seed4.npz")
+HA_MEV = 27211.386
+
+
+def one_pass(m, precision, flags, local, st, fetch_b=False):
+    """One qsGW iteration of molecule m from its input orbitals through the C ABI, every
+    kernel class event-timed on the context stream.  Returns the pass time, the time
+    per class, and the pass's Omega, Sigma_x, Sigma_c and updated energies (and B on
+    the device when fetch_b).  Buffers are allocated inside the first pass (a few tens
+    of ms at these sizes, inside the time)."""
+    import torch
+    from paper_2210_17093_gb300 import Context
+    nb, no, na = m["n_basis"], m["n_occ"], m["n_aux"]
+    n = no * (nb - no)
+    dev = f"cuda:{local}"
+    out = {}
+    with Context(precision=precision, device=local, eta=sy.ETA, stream=st, flags=flags) as ctx:
+        L_d = torch.from_numpy(m["L"]).to(dev)
+        ctx.set_ri(0, nb, na, L_d)
+        ctx.set_orbitals(0, no, torch.from_numpy(m["eps"]).to(dev), torch.from_numpy(m["C"]).to(dev))
+        ctx.sync()
+        del L_d
+        torch.cuda.empty_cache()
+        ctx.set_timing(CLASSES)
+        ctx.kernel_stats(reset=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        ctx.qs_step(0)
+        e1.record(st)
+        torch.cuda.synchronize()
+        out["s"] = e0.elapsed_time(e1) / 1e3
+        stats = ctx.kernel_stats(reset=True)
+        out["stages_ms"] = {k: round(v[1], 2) for k, v in stats.items() if v[0]}
+        om, sx, sc, ep = np.empty(n), np.empty(nb * nb), np.empty(nb * nb), np.empty(nb)
+        ctx.fetch(0, "Omega", om)
+        ctx.fetch(0, "sigma_x", sx)
+        ctx.fetch(0, "sigma_c", sc)
+        ctx.fetch(0, "eps", ep)
+        out.update(Omega=om, sigma_x=sx.reshape(nb, nb), sigma_c=sc.reshape(nb, nb), eps_new=ep)
+        if fetch_b:
+            B = torch.empty(na * nb * nb, dtype=torch.float64, device=dev)
+            ctx.fetch(0, "B", B)
+            out["B"] = B
+    return out
+
+
+def vs_golden(r, g):
+    """Errors of one pass against the oracle's stored values (upper triangles of Sigma)."""
+    nb = r["eps_new"].shape[0]
+    iu = np.triu_indices(nb)
+    rel = lambda a, b: float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+    d_eps = float(np.max(np.abs(r["eps_new"] - g["eps_new"])))
+    return {"omega_max_abs_ha": float(np.max(np.abs(r["Omega"] - g["Omega"]))),
+            "qp_max_abs_ha": d_eps, "qp_max_abs_meV": d_eps * HA_MEV,
+            "sigma_x_rel": rel(r["sigma_x"][iu], g["sigma_x_upper"]),
+            "sigma_c_rel": rel(r["sigma_c"][iu], g["sigma_c_upper"])}
+
+
+def config_c_line(local, st):
+    """Workload 400/80/1200 (25,600 transitions), seed 4: one float64 pass and two
+    BF16X10 passes (TC_AB; and TC_AB + EIG_TC), each against the oracle's stored values."""
+    wl = WORKLOADS["C"]
+    m = sy.molecule(wl["nb"], wl["no"], wl["na"], wl["seed"])
+    g = dict(np.load(GOLDEN_C)) if os.path.exists(GOLDEN_C) else None
+    out = {"workload": "n_basis=400, n_occ=80, n_aux=1200, 25600 transitions, seed 4, one pass from the "
+                       "input orbitals (M 5.2 GB)",
+           "oracle_values": "tests/golden/qsgw_nb400_no80_na1200_seed4.npz (written by the CPU oracle)"
+           if g is not None else None}
+    runs = (("fp64", "fp64", 0), ("mixed", "bf16x10", FLAG_TC_AB_BIT),
+            ("mixed_eig_tc", "bf16x10", FLAG_TC_AB_BIT | FLAG_EIG_TC_BIT))
+    t64 = None
+    for name, prec, flags in runs:
+        r = one_pass(m, prec, flags, local, st)
+        d = {"s_per_pass": round(r["s"], 3), "precision": prec, "flags": flags, "stages_ms": r["stages_ms"],
+             "roofline_stages": stage_rooflines(wl["nb"], wl["no"], wl["na"], r["stages_ms"], prec, flags)}
+        if t64 is None:
+            t64 = r["s"]
+        else:
+            d["speedup_vs_fp64"] = round(t64 / r["s"], 3)
+        if g is not None:
+            d["vs_oracle"] = vs_golden(r, g)
+            bar = 1e-8 if prec == "fp64" else 1.0 / HA_MEV
+            d["meets_bar"] = bool(d["vs_oracle"]["qp_max_abs_ha"] <= bar and d["vs_oracle"]["omega_max_abs_ha"] <= bar
+                                  and d["vs_oracle"]["sigma_c_rel"] <= 1e-6 and d["vs_oracle"]["sigma_x_rel"] <= 1e-6)
+        out[name] = d
+    return out
+
+
+def config_e_line(local, st):
+    """Workload 600/120/1800 (57,600 transitions, M 26.5 GB), seed 7: one BF16X10 pass
+    (TC_AB + EIG_TC) with per-stage times and fractions, and checks that hold at any size."""
+    import torch
+    wl = WORKLOADS["E"]
+    nb, no, na = wl["nb"], wl["no"], wl["na"]
+    m = sy.molecule(nb, no, na, wl["seed"])
+    flags = FLAG_TC_AB_BIT | FLAG_EIG_TC_BIT
+    r = one_pass(m, "bf16x10", flags, local, st, fetch_b=True)
+    n = no * (nb - no)
+    eps = torch.from_numpy(m["eps"]).to(r["B"].device)
+    D = (eps[no:][None, :] - eps[:no][:, None]).reshape(-1)            # t = i nv + (a - no)
+    Bia = r["B"].view(na, nb, nb)[:, :no, no:].reshape(na, n)
+    tr_m = float((D * D).sum() + 4.0 * (D * (Bia * Bia).sum(0)).sum())
+    del Bia, r["B"]
+    torch.cuda.empty_cache()
+    om = r["Omega"]
+    sum_om2 = float(np.sum(om * om))
+    return {"workload": "n_basis=600, n_occ=120, n_aux=1800, 57600 transitions (M 26.5 GB), seed 7, one pass "
+                        "from the input orbitals; BF16X10 with TC_AB and EIG_TC",
+            "s_per_pass": round(r["s"], 3), "stages_ms": r["stages_ms"],
+            "roofline_stages": stage_rooflines(nb, no, na, r["stages_ms"], "bf16x10", flags),
+            "checks": {"sum_omega2_vs_trace_M_rel": abs(sum_om2 - tr_m) / tr_m,
+                       "omega_min": float(om.min()), "min_D": float(D.min().item()),
+                       "omega_min_ge_min_D": bool(om.min() >= float(D.min().item())),
+                       "sigma_x_asym": float(np.max(np.abs(r["sigma_x"] - r["sigma_x"].T))),
+                       "sigma_c_asym": float(np.max(np.abs(r["sigma_c"] - r["sigma_c"].T))),
+                       "finite": bool(np.all(np.isfinite(om)) and np.all(np.isfinite(r["eps_new"])))}}
 
 
 def run_ours(args, wl):
@@ -380,7 +600,9 @@ def run_ours(args, wl):
                "speedup_vs_fp64": (t_max / args.steps) / (t_v / args.steps),
                "qp_error_vs_fp64_meV": err * 27211.386,
                "meets_1meV": bool(err * 27211.386 <= 1.0),
-               "stages_ms": {k: round(v[1], 3) for k, v in vbreak.items() if v[0]}}
+               "stages_ms": {k: round(v[1], 3) for k, v in vbreak.items() if v[0]},
+               "roofline_stages": stage_rooflines(nb, no, na, {k: v[1] for k, v in vbreak.items() if v[0]},
+                                                  precision, flags)}
         tc_ms = vbreak.get("gemm_tc", (0, 0.0))[1]
         sg_ms = vbreak.get("sigma", (0, 0.0))[1]
         if precision == "bf16x10" and sg_ms > 0:
@@ -544,6 +766,23 @@ def run_ours(args, wl):
         return {"method": "open-shell qsGW, float64: one RPA over the transitions of both spins",
                 "n_occ_up_down": [no, no - 1], "n_transitions": n_open, "ms_per_step": t}
 
+    extras = {}
+    if world == 1 and not args.no_extra_configs:
+        for key, fn in (("config_C", lambda: config_c_line(local, st)), ("config_E", lambda: config_e_line(local, st))):
+            try:
+                extras[key] = fn()
+            except Exception as exc:          # a failed extra workload must not hide the main line
+                extras[key] = {"error": f"{type(exc).__name__}: {exc}"}
+            torch.cuda.empty_cache()
+        try:
+            import copy
+            bargs = copy.copy(args)
+            bargs.steps, bargs.warmup, bargs.no_cpu_baseline = 3, 3, True
+            bargs.dominant = "tridiag_panel"
+            extras["batch_D"] = run_batch(bargs, setup=(world, rank, local, dist), emit=False)
+        except Exception as exc:
+            extras["batch_D"] = {"error": f"{type(exc).__name__}: {exc}"}
+        torch.cuda.empty_cache()
     qsmp2 = None if args.no_mp2 else qsmp2_lines()
     g0w0 = None if args.no_variants else g0w0_lines()
     open_shell = None if args.no_variants else open_shell_line()
@@ -588,6 +827,8 @@ def run_ours(args, wl):
             "launches": nl, "event_ms": kms,
         },
         "stages_ms": {k: round(v[1], 3) for k, v in breakdown.items() if v[0]},
+        "roofline_stages": stage_rooflines(nb, no, na, {k: v[1] for k, v in breakdown.items() if v[0]},
+                                           args.precision, 0),
         "mixed": mixed,
         "mixed_eig_tc": mixed_eig,
         "fp64_eig_tc": fp64_eig,
@@ -605,16 +846,62 @@ def run_ours(args, wl):
             "value": t_cpu, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"1 oracle iteration of the same workload (seed {wl['seed']}), NumPy float64, "
                       f"BLAS threads = host cores"}
-    print(json.dumps(line))
+    line.update(extras)
+    line["headline"] = headline(line)
+    print(json.dumps(line, separators=(",", ":")))
     return 0
 
 
-def run_batch(args):
+def headline(line):
+    """The figures of the line in a few hundred characters, last on the line so that a
+    reader of its tail sees them: s per iteration per path and workload, speed-ups,
+    errors against the oracle, per-stage roofline fractions."""
+    r3 = lambda x: None if x is None else float(f"{x:.4g}")
+    h = {"B_fp64_s": r3(line["value"]), "B_panel_frac": r3(line["roofline"]["frac"])}
+    for k in ("mixed", "mixed_eig_tc", "fp64_eig_tc"):
+        v = line.get(k)
+        if v:
+            h[f"B_{k}_s"] = r3(v["ms_per_step"] / 1e3)
+            h[f"B_{k}_x"] = r3(v["speedup_vs_fp64"])
+            h[f"B_{k}_qp_meV"] = r3(v["qp_error_vs_fp64_meV"])
+    h["B_stage_frac"] = {k: r3(v["frac"]) for k, v in line.get("roofline_stages", {}).items()}
+    c = line.get("config_C") or {}
+    for k in ("fp64", "mixed", "mixed_eig_tc"):
+        v = c.get(k)
+        if isinstance(v, dict):
+            h[f"C_{k}_s"] = r3(v["s_per_pass"])
+            if "speedup_vs_fp64" in v:
+                h[f"C_{k}_x"] = r3(v["speedup_vs_fp64"])
+            if "vs_oracle" in v:
+                h[f"C_{k}_qp_meV"] = r3(v["vs_oracle"]["qp_max_abs_meV"])
+                h[f"C_{k}_ok"] = v["meets_bar"]
+    if "error" in c:
+        h["C_error"] = c["error"][:80]
+    e = line.get("config_E") or {}
+    if "s_per_pass" in e:
+        h["E_s"] = r3(e["s_per_pass"])
+        h["E_stage_frac"] = {k: r3(v["frac"]) for k, v in e["roofline_stages"].items()}
+        h["E_checks_ok"] = bool(e["checks"]["omega_min_ge_min_D"] and e["checks"]["finite"]
+                                and e["checks"]["sum_omega2_vs_trace_M_rel"] < 1e-6)
+    elif "error" in e:
+        h["E_error"] = e["error"][:80]
+    d = line.get("batch_D") or {}
+    if "value" in d:
+        h["D_s"] = r3(d["value"])
+        h["D_launches_per_step"] = int(d["gpu_launches"] / max(d["steps"], 1))
+    elif "error" in d:
+        h["D_error"] = d["error"][:80]
+    return h
+
+
+def run_batch(args, setup=None, emit=True):
     """Workload D: 64 molecules (n_basis ~ U{40..160}, seeds 100-163 + 64 x rank) as one
-    qs_step(-1) per step on concurrent lanes, replayed from a captured graph."""
+    qs_step(-1) per step on concurrent lanes, replayed from a captured graph.  With
+    emit=False the line is returned instead of printed (setup: the caller's
+    (world, rank, local, dist))."""
     import torch
 
-    world, rank, local, dist = dist_setup()
+    world, rank, local, dist = setup if setup is not None else dist_setup()
     from paper_2210_17093_gb300 import FLAG_EIG_TC, FLAG_GRAPH, FLAG_TC_AB, Context
 
     torch.cuda.set_device(local)
@@ -677,7 +964,7 @@ def run_batch(args):
             ctx.fetch(k, "eps", o)
         t_e2e = max_over_ranks(dist, time.perf_counter() - t0)
     if rank != 0:
-        return 0
+        return 0 if emit else None
     nl, kms = kstats[dominant]
     dom_flops = flops.get(dominant)
     achieved = dom_flops / (kms / 1e3) / 1e12 if (dom_flops and kms > 0) else None
@@ -721,6 +1008,8 @@ def run_batch(args):
             "value": t_cpu, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"one oracle iteration of molecules {seeds[0]}..{seeds[3]} (n_basis "
                       f"{', '.join(str(m['n_basis']) for m in sample)}), time x {len(mols)}/{len(sample)}"}
+    if not emit:
+        return line
     print(json.dumps(line))
     return 0
 
@@ -745,6 +1034,8 @@ def main():
     ap.add_argument("--batch-no-eig-tc", action="store_true",
                     help="workload D: keep the eigensolvers' trailing updates in float64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="skip the 400/80/1200 and 600/120/1800 passes and the batch object (N=1 only)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
