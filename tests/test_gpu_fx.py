@@ -211,10 +211,12 @@ def test_eig_tc_eigh_matches_float64():
     for flags, (w, Z) in out.items():
         assert np.max(np.abs(w - ref)) < 1e-12 * nrm, flags
         Zc = Z.reshape(n, n)
-        # eigenvectors are columns or rows of Z depending on layout: test both ways
-        R1 = np.abs(A @ Zc.T - Zc.T * w[None, :]).max()
-        R2 = np.abs(A @ Zc - Zc * w[None, :]).max()
-        assert min(R1, R2) < 1e-10 * nrm, flags
+        # the layout the header states: Z[i][k] = component i of eigenvector k (columns),
+        # each column's largest-magnitude entry positive
+        assert np.abs(A @ Zc - Zc * w[None, :]).max() < 1e-10 * nrm, flags
+        assert np.abs(Zc.T @ Zc - np.eye(n)).max() < 1e-12 * n, flags
+        big = np.abs(Zc).argmax(axis=0)
+        assert np.all(Zc[big, np.arange(n)] > 0), flags
 
 
 @pytest.mark.parametrize("prec,tol_ha", [("fp64", 1e-8), ("bf16x10", 1.0 * MEV)])
