@@ -12,7 +12,7 @@ RI-qsGW pass of the 400/80/1200 workload (25,600 transitions), seed 4, eta = 1e-
 Ha -- Omega_s, the updated energies eps', Sigma_x and the Hermitised Sigma_c
 (upper triangles, both matrices are symmetric) and min D_t.  The residues are
 formed one orbital at a time (``keep_w=False``): whole, w would take 33 GB.  It
-takes about 20 minutes on 8 cores and ~35 GB of host memory.
+takes about 15 minutes on 8 x86 cores and ~35 GB of host memory.
 Run from the repository root:
     python tests/golden/make_golden.py          # the 24/5/72 files
     python tests/golden/make_golden.py C        # the 400/80/1200 file
