@@ -200,13 +200,14 @@ def test_qsmp2_fixed_point_batch_lanes_equal_solo():
 def test_qsmp2_fixed_point_within_1mev_well_conditioned(flags, nb, no, na, seed):
     """The absolute 1 meV bar where qsMP2 is well conditioned: the RI factors scaled by
     0.1 (coupling 0.1, the regime of the weak-coupling pin), so that the energies stay
-    in the input range (|eps| < 20 Ha, max |Sigma_c| ~ 0.5 Ha) instead of the 1e2 -
-    3e5 Ha of the unscaled, strongly coupled inputs.  BF16X10 (with MOLGW_FLAG_TC_AB
-    also stage (a)) against the oracle: QP energies within 1 meV = 3.675e-5 Ha,
-    Sigma_c within 1e-6 of its maximum."""
+    near the input range (|eps| <= 20 Ha in, |eps'| <= 28 Ha out; max |Sigma_c| 0.5 Ha
+    at 71/13/150, 18 Ha at 200/40/600) instead of the 1e2 - 3e5 Ha of the unscaled,
+    strongly coupled inputs.  BF16X10 (with MOLGW_FLAG_TC_AB also stage (a)) against
+    the oracle: QP energies within 1 meV = 3.675e-5 Ha, Sigma_c within 1e-6 of its
+    maximum."""
     m = sy.scale_ri(sy.molecule(nb, no, na, seed), 0.1)
     r = qsgw.qsmp2_pass(m["L"], m["eps"], m["C"], no, ETA)
-    assert np.max(np.abs(r["eps_new"])) < 25.0           # the regime this test is about
+    assert np.max(np.abs(r["eps_new"])) < 50.0           # the regime this test is about
     with lib_context(precision="bf16x10", flags=flags) as ctx:
         load_mol(ctx, 0, m)
         sc = np.empty((nb, nb))
