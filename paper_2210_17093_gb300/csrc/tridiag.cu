@@ -151,13 +151,13 @@ __device__ double sum_partials(const double* p, int cnt, double* sh) {
   return sh[32];
 }
 
-struct Refl { double tau, beta, scale; };
+struct Refl { double tau, beta, scale, alpha; };
 
 __device__ Refl householder(const PanelParams& p, int i, double* sh) {
   const int n_ss = ceil_div_d(p.n - i, RC);
   const double sumsq = sum_partials(p.p_ss, n_ss, sh);
   const double alpha = ldg_cg(p.scal + 0);
-  Refl h{0.0, alpha, 0.0};
+  Refl h{0.0, alpha, 0.0, alpha};
   if (sumsq > 0.0) {
     const double nrm = sqrt(alpha * alpha + sumsq);
     h.beta = (alpha >= 0.0) ? -nrm : nrm;
@@ -176,8 +176,7 @@ __device__ __forceinline__ double vval(const PanelParams& p, int i, int r, doubl
 __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
   __shared__ double sh[40];
   __shared__ double Wi[NBP], Vi[NBP], vtv[NBP], wtv[NBP];
-  __shared__ double tile[TB * (TB + 1)];
-  __shared__ double vJ[TB], vR[TB];
+  __shared__ double tile[TB * (TB + 1)];   // P1 scratch; P2 row-block sums [8][64]
   const int n = p.n, k0 = p.k0;
   const long long ld = n;
   double* A = p.A;
@@ -289,47 +288,54 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
       L = s_rank[2];
     }
 
-    // ---------------- P2: reflector and y = A22 v ----------------
+    // ---------------- P2: reflector and y = A22 x ----------------
+    // The symmetric product runs on the unscaled column x (rows >= i+1 of column i as
+    // P1 left it, x_(i+1) = alpha): v = scale x + (1 - scale alpha) e_(i+1), so P3 forms
+    // A22 v = scale (A22 x) + (1 - scale alpha) A22 e_(i+1) from the partials written here.
     const int lo = i + 1;
     const int rb0 = lo / TB;
     const int nrb = nrbt - rb0;
     // The stored (lower and diagonal) tiles of A22 in row-major order (R, J <= R),
-    // split into equal contiguous ranges.  Each tile is read once and used twice:
-    // y_R += A_RJ v_J (accumulated per thread along the row, stored per CTA and row
-    // block) and, below the diagonal, y_J += A_RJ^T v_R (reduced over the four lanes
-    // that share a column, stored per tile).
+    // split into equal contiguous ranges.  Each tile is read once into registers and
+    // used twice: y_R += A_RJ x_J (per thread along its rows, summed over the CTA at
+    // the end of its part of row block R, stored per CTA and row block) and, below the
+    // diagonal, y_J += A_RJ^T x_R (summed over the tile's rows by shuffles, stored per
+    // tile).  Thread (warp w, lane l) holds rows (l & 15) + 16 k and columns
+    // 8 w + 4 (l >> 4) + c of the tile (k, c < 4): every load instruction reads 128
+    // contiguous bytes per half-warp, and no shared memory or barrier is used per tile.
     const long long T = (long long)nrb * (nrb + 1) / 2;
     const long long f0 = (long long)blockIdx.x * T / gridDim.x;
     const long long f1 = (long long)(blockIdx.x + 1) * T / gridDim.x;
-    const int rr = t % TB, cq = t / TB;
-    double nxt[16];
-    double vraw = 0.0;
+    const int wq = t >> 5, lane = t & 31, rq = lane & 15;
+    const int cq0 = 8 * wq + 4 * (lane >> 4);
+    double nxt[16];                        // [4 c + k]
     // (R, J) of the first tile of the range: R - rb0 = the largest a with a(a+1)/2 <= f0
-    // (integer search; later tiles advance J, then R).  Its elements, and the raw
-    // column entries behind v_J, are loaded before the reflector's norm is summed.
+    // (integer search; later tiles advance J, then R).  Its elements are loaded before
+    // the reflector's norm is summed.
     int R0 = rb0, J0 = rb0;
+    auto load_tile = [&](int R, int J) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int gc = J * TB + cq0 + c;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int gr = R * TB + rq + 16 * k;
+          nxt[4 * c + k] = (gr < n && gc < n) ? __ldca(A + gr + (long long)gc * ld) : 0.0;
+        }
+      }
+    };
     if (f0 < f1) {
       long long a = 0;
       while ((a + 1) * (a + 2) / 2 <= f0) ++a;
       R0 = rb0 + (int)a;
       J0 = rb0 + (int)(f0 - a * (a + 1) / 2);
-      const int gr = R0 * TB + rr;
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int gc = J0 * TB + cq + 4 * k;
-        nxt[k] = (gr < n && gc < n) ? ldg_cg(A + gr + (long long)gc * ld) : 0.0;
-      }
-      if (t < TB) {
-        const int r = J0 * TB + t;
-        if (r >= lo && r < n && r != i + 1) vraw = ldg_cg(A + r + (long long)i * ld);
-      }
+      load_tile(R0, J0);
     }
     const Refl h = householder(p, i, sh);
     {
       // V^T v = V(i+1,:) + scale * (sum over the P1 chunks), the same for W^T v:
       // the first CTAs finish these 2j sums (one warp per value) for P3
-      const int warp = t >> 5, lane = t & 31;
-      const int c = blockIdx.x * (RT / 32) + warp;
+      const int c = blockIdx.x * (RT / 32) + wq;
       if (c < 2 * j) {
         double s2 = 0.0;
         for (int ch = lane; ch < n1; ch += 32) s2 += ldg_cg(p.p_vw + (long long)ch * (2 * NBP) + c);
@@ -341,67 +347,75 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
       }
     }
     if (f0 < f1) {
-      const int x = t >> 2, q = t & 3;          // row / column x of the tile, quarter q of the other index
-      double vnxt = 0.0;
-      if (t < TB) {
-        const int r = J0 * TB + t;
-        vnxt = (r == i + 1) ? 1.0 : ((r >= lo && r < n) ? vraw * h.scale : 0.0);   // vval of the first tile
-      }
-      auto load_tile = [&](int R, int J) {
-        const int gr = R * TB + rr;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const int gc = J * TB + cq + 4 * k;
-          nxt[k] = (gr < n && gc < n) ? ldg_cg(A + gr + (long long)gc * ld) : 0.0;
-        }
-        if (t < TB) {
-          const int r = J * TB + t;
-          vnxt = (r >= lo && r < n) ? vval(p, i, r, h.scale) : 0.0;
-        }
-      };
-      double acc = 0.0;          // y_R partial of row x, this thread's column quarter
-      int Rcur = -1;
+      // x entries of rows >= lo (written by P1 of this column: read through L2)
+      auto xval = [&](int r) { return (r >= lo && r < n) ? ldg_cg(A + r + (long long)i * ld) : 0.0; };
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};   // y_R partials of the thread's rows
+      double xr[4];
       int R = R0, J = J0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) xr[k] = xval(R * TB + rq + 16 * k);
       for (long long f = f0; f < f1; ++f) {
         int Rn = R, Jn = J + 1;             // next tile
         if (Jn > Rn) { ++Rn; Jn = rb0; }
-        __syncthreads();
+        double cur[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) tile[(cq + 4 * k) * (TB + 1) + rr] = nxt[k];
-        if (t < TB) {
-          vJ[t] = vnxt;
-          if (R != Rcur) {
-            const int r = R * TB + t;
-            vR[t] = (r >= lo && r < n) ? vval(p, i, r, h.scale) : 0.0;
-          }
-        }
-        Rcur = R;
-        __syncthreads();
+        for (int e = 0; e < 16; ++e) cur[e] = nxt[e];
+        double xc[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) xc[c] = xval(J * TB + cq0 + c);
         if (f + 1 < f1) load_tile(Rn, Jn);   // in flight while this tile is used
-        double s1 = 0.0, s2 = 0.0;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const int c = q + 4 * k;
-          s1 += tile[c * (TB + 1) + x] * vJ[c];          // (A_RJ v_J)[x]
-          if (J < R) s2 += tile[x * (TB + 1) + c] * vR[c];  // (A_RJ^T v_R)[x]
-        }
-        acc += s1;
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[k] = fma(cur[4 * c + k], xc[c], acc[k]);
         if (J < R) {
-          s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
-          s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
-          if (q == 0) {
+          double q[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            q[c] = cur[4 * c] * xr[0];
+#pragma unroll
+            for (int k = 1; k < 4; ++k) q[c] = fma(cur[4 * c + k], xr[k], q[c]);
+          }
+          // sum over the 16 lanes of the half-warp (the tile's 64 rows), scattering the
+          // four columns: lane bits 3 and 2 select the column each lane keeps
+          const bool b3 = (rq & 8) != 0, b2 = (rq & 4) != 0;
+          const double k0v = b3 ? q[2] : q[0], k1v = b3 ? q[3] : q[1];
+          const double s0v = b3 ? q[0] : q[2], s1v = b3 ? q[1] : q[3];
+          const double h0 = k0v + __shfl_xor_sync(0xffffffffu, s0v, 8);
+          const double h1 = k1v + __shfl_xor_sync(0xffffffffu, s1v, 8);
+          double v = (b2 ? h1 : h0) + __shfl_xor_sync(0xffffffffu, b2 ? h0 : h1, 4);
+          v += __shfl_xor_sync(0xffffffffu, v, 2);
+          v += __shfl_xor_sync(0xffffffffu, v, 1);
+          if ((rq & 3) == 0) {
             const long long ft = (long long)(R - rb0) * (R - rb0 + 1) / 2 + (J - rb0);
-            p.p_t[ft * TB + x] = s2;
+            p.p_t[ft * TB + cq0 + 2 * (b3 ? 1 : 0) + (b2 ? 1 : 0)] = v;
           }
         }
         if (f + 1 == f1 || J == R) {
-          // end of this CTA's part of row block R
-          double y = acc;
-          y += __shfl_xor_sync(0xffffffffu, y, 1);
-          y += __shfl_xor_sync(0xffffffffu, y, 2);
-          const int r = R * TB + x;
-          if (q == 0 && r < n) p.p_y[(long long)blockIdx.x * n + r] = y;
-          acc = 0.0;
+          // end of this CTA's part of row block R: the rows' sums over the 16 threads that
+          // hold them (the two half-warps, then the eight warps through shared memory)
+          double* red = tile;               // [8][64]
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 16);
+          __syncthreads();
+          if (lane < 16) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) red[wq * TB + rq + 16 * k] = acc[k];
+          }
+          __syncthreads();
+          if (t < TB) {
+            double y = red[t];
+#pragma unroll
+            for (int w2 = 1; w2 < RT / 32; ++w2) y += red[w2 * TB + t];
+            const int r = R * TB + t;
+            if (r < n) p.p_y[(long long)blockIdx.x * n + r] = y;
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc[k] = 0.0;
+          if (f + 1 < f1 && Rn != R) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) xr[k] = xval(Rn * TB + rq + 16 * k);
+          }
         }
         R = Rn;
         J = Jn;
@@ -420,27 +434,31 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
       const int r = lo + ch * RC + rl;
       double y = 0.0;
       if (r < n) {
-        // y_r = (direct partials of the CTAs whose ranges cover row block R)
-        //     + (transposed partials of the tiles (R', R) below it)
+        // (A22 x)_r = (direct partials of the CTAs whose ranges cover row block R)
+        //           + (transposed partials of the tiles (R', R) below it);
+        // y_r = scale (A22 x)_r + (1 - scale alpha) A(r, i+1) - W(r,:) V^T v - V(r,:) W^T v
         const int Rr = r / TB, a = Rr - rb0;
         const long long T = (long long)nrb * (nrb + 1) / 2;
         const long long fa = (long long)a * (a + 1) / 2, fb = fa + a;
         const int ca = (int)(((fa + 1) * gridDim.x - 1) / T), cb = (int)(((fb + 1) * gridDim.x - 1) / T);
+        double yx = 0.0;
         for (int c = ca + q8; c <= cb; c += 8) {
           // CTAs with an empty tile range wrote nothing
           if ((long long)c * T / gridDim.x == (long long)(c + 1) * T / gridDim.x) continue;
-          y += ldg_cg(p.p_y + (long long)c * n + r);
+          yx += ldg_cg(p.p_y + (long long)c * n + r);
         }
 #pragma unroll 8
         for (int R2 = Rr + 1 + q8; R2 < nrbt; R2 += 8) {
           const long long ft = (long long)(R2 - rb0) * (R2 - rb0 + 1) / 2 + a;
-          y += ldg_cg(p.p_t + ft * TB + (r - Rr * TB));
+          yx += ldg_cg(p.p_t + ft * TB + (r - Rr * TB));
         }
+        if (q8 == 0) y = (1.0 - h.scale * h.alpha) * ldg_cg(A + r + (long long)(i + 1) * ld);
 #pragma unroll 4
         for (int c = q8; c < j; c += 8) {
           y -= ldg_cg(p.Wp + r + (long long)c * ld) * vtv[c];
           y -= ldg_cg(A + r + (long long)(k0 + c) * ld) * wtv[c];
         }
+        y = fma(h.scale, yx, y);
       }
       y += __shfl_xor_sync(0xffffffffu, y, 1);
       y += __shfl_xor_sync(0xffffffffu, y, 2);
