@@ -27,6 +27,8 @@ struct Lane {
   size_t pk_fail = 0;         // packed-residue request that did not fit (not retried)
   void* eigfx = nullptr;      // MOLGW_FLAG_EIG_TC: fixed-point operands of the trailing updates
   long long eigfx_rows = 0, eigfx_cols = 0;
+  void* eigsv = nullptr;      // MOLGW_FLAG_EIG_TC, lane 0: tile images of the panel mat-vec
+  long long eigsv_n = 0;
 };
 
 constexpr int kMaxLanes = 16;
@@ -192,6 +194,7 @@ void lane_free(Lane& l) {
   if (l.scr.pk_base) cudaFree(l.scr.pk_base);
   if (l.tco_base) cudaFree(l.tco_base);
   if (l.eigfx) cudaFree(l.eigfx);
+  if (l.eigsv) cudaFree(l.eigsv);
   eig_work_free(l.eig);
   if (l.done) cudaEventDestroy(l.done);
   if (l.own_stream) cudaStreamDestroy(l.st);
@@ -217,6 +220,8 @@ int ensure_eigfx(molgw_ctx c, Lane& l) {
   if (!use_eig_tc(c)) {
     l.eig.fx = nullptr;
     l.eig.fx_rows = 0;
+    l.eig.sv = nullptr;
+    l.eig.sv_n = 0;
     return MOLGW_OK;
   }
   const long long rows = l.eig_n, cols = l.eig_cols;
@@ -238,6 +243,26 @@ int ensure_eigfx(molgw_ctx c, Lane& l) {
   l.eig.fx = l.eigfx;
   l.eig.fx_rows = l.eigfx_rows;
   l.eig.fx_cols = l.eigfx_cols;
+  // the tensor-core mat-vec of the panel kernel runs on the context stream only (lane 0):
+  // its persistent launch holds one CTA per SM and TMEM, which concurrent lanes would share
+  if (&l == &c->lanes[0]) {
+    if (rows > l.eigsv_n) {
+      if (l.ex.capturing) return MOLGW_E_STATE;
+      cudaStreamSynchronize(l.st);
+      ++c->gen;
+      if (l.eigsv) cudaFree(l.eigsv);
+      l.eigsv = nullptr;
+      l.eigsv_n = 0;
+      if (cudaMalloc(&l.eigsv, eig_sv_bytes(rows)) != cudaSuccess) {
+        cudaGetLastError();
+        l.eigsv = nullptr;
+        return MOLGW_E_NOMEM;
+      }
+      l.eigsv_n = rows;
+    }
+    l.eig.sv = l.eigsv;
+    l.eig.sv_n = l.eigsv_n;
+  }
   return MOLGW_OK;
 }
 

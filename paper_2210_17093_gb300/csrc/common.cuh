@@ -156,7 +156,21 @@ struct EigWork {
   void* fx = nullptr;
   long long fx_rows = 0;       // matrices up to fx_rows (n)
   long long fx_cols = 0;       // back-transformations of up to fx_cols columns
+  // with MOLGW_FLAG_EIG_TC on the context's own stream: 7-digit images of the lower
+  // 64 x 64 tiles of the trailing matrix (eig_sv_bytes(sv_n) bytes) for the panel
+  // kernel's tensor-core mat-vec, their scales, and the panel's column-maximum
+  // partials; else nullptr
+  void* sv = nullptr;
+  long long sv_n = 0;
 };
+// Bytes of the tensor-core mat-vec arena for matrices up to n: one 57,344-byte image
+// (7 digit planes of 64 x 64 BF16) and one scale per lower tile, then ceil(n/32) + 2
+// column-maximum partials.
+constexpr long long kSvTileBytes = 7LL * 64 * 64 * 2;
+inline long long eig_sv_tiles(long long n) { const long long b = (n + 63) / 64; return b * (b + 1) / 2; }
+inline size_t eig_sv_bytes(long long n) {
+  return (size_t)(eig_sv_tiles(n) * (kSvTileBytes + 8) + ((n + 31) / 32 + 2) * 8 + 256);
+}
 // Workspace sizes in doubles for matrices up to n and back-transformations of
 // up to ncols (>= 64) columns at a time.
 constexpr int kMaxPanelGrid = 320;   // CTAs of the tridiagonalisation panel kernel, at most

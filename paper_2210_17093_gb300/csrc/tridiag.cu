@@ -66,6 +66,11 @@ struct PanelParams {
   GridBar* bar;
   int* status;
   long long spin_limit;     // polls of a grid barrier before it gives up
+  // tensor-core mat-vec (k_panel<true>): tile images and scales of the panel's trailing
+  // region (tile index relative to block k0 / 64), P1's column-maximum partials
+  const uint8_t* sv_img;
+  const double* sv_scl;
+  double* sv_mx;
 };
 
 __device__ __forceinline__ double ldg_cg(const double* p) { return __ldcg(p); }
@@ -84,11 +89,11 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
 // the abort flag and returns false so that every CTA leaves the kernel.  A CTA that
 // arrives last passes; it leaves at its next barrier, where the abort flag stops
 // its wait.
-__device__ bool grid_sync(GridBar* bar, int* status, unsigned int& epoch, long long spin_limit) {
+__device__ bool grid_sync(GridBar* bar, int* status, unsigned int& epoch, long long spin_limit, int leader = 0) {
   __shared__ int ok;
   __syncthreads();
   ++epoch;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == leader) {
     ok = 1;
     const unsigned int target = epoch * gridDim.x;
     __threadfence();
@@ -153,6 +158,24 @@ __device__ double sum_partials(const double* p, int cnt, double* sh) {
 
 struct Refl { double tau, beta, scale, alpha; };
 
+// Largest of `cnt` partials, the same value in every thread of every CTA.
+__device__ double max_partials(const double* p, int cnt, double* sh) {
+  double v = 0.0;
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) v = fmax(v, ldg_cg(p + k));
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+    sh[33] = m;
+  }
+  __syncthreads();
+  return sh[33];
+}
+
 __device__ Refl householder(const PanelParams& p, int i, double* sh) {
   const int n_ss = ceil_div_d(p.n - i, RC);
   const double sumsq = sum_partials(p.p_ss, n_ss, sh);
@@ -173,10 +196,182 @@ __device__ __forceinline__ double vval(const PanelParams& p, int i, int r, doubl
   return ldg_cg(p.A + r + (long long)i * p.n) * scale;
 }
 
-__global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
+// ---------------------------------------------------------------------------
+// Tensor-core symmetric mat-vec (MOLGW_FLAG_EIG_TC).  Before a panel, every stored
+// 64 x 64 tile of the trailing matrix is written as a 7-digit fixed-point image
+// (fx.cuh: x ~ u sum_d s_d 2^(-8d), one power-of-two scale u per tile): digit plane d
+// holds row c (tile column) = the 64 tile rows of column c, 128 bytes with the 128-byte
+// swizzle, i.e. the shared-memory image a K-major operand indexed (column, row) and an
+// MN-major operand indexed (row, column) both read.  In P2 the panel kernel copies
+// tile images with the bulk-copy engine, writes the 7 digits of the two 64-blocks of x
+// it needs (one scale per column: its maximum), and per tile issues, for each pair of
+// digit planes (2g, 2g+1) of the tile and K step, M=128 N=8 K=16 MMAs: A_RJ x_J with the
+// two planes as an MN-major A operand (64-element atoms 8 KB apart) and (below the
+// diagonal) A_RJ^T x_R as a K-major one (the planes' rows contiguous), the 7 digits of x
+// as the 8 columns of B.  (Each tcgen05.mma costs the same ~65 SM cycles whatever its
+// shape at these sizes, so two planes per instruction halve the mat-vec's issue time.)
+// TMEM lanes 0-63 then hold digit 2g's sums, lanes 64-127 digit 2g+1's: every column one
+// digit pair's sum over 64 elements, an integer below 2^21, exact in float32.  The
+// epilogue adds the pairs with i + j <= 6 into levels exactly (odd-digit warps hand their
+// partial levels to the even-digit warps through shared memory), combines the levels in
+// 64-bit integers (as the fixed-point GEMM does) and rounds once to float64.
+// The arithmetic is float64-accurate in the normwise sense (values represented to
+// 2^-54 of their tile's or column's largest), not float64 arithmetic.
+constexpr int SV_PLANE = TB * TB * 2;                 // 8 KB: one digit plane of a tile image
+constexpr int SV_TILE = 7 * SV_PLANE;                 // 57,344 B
+constexpr int SV_XIMG = 8 * 128;                      // a 64-block of x: 7 digit rows + a zero row
+constexpr int SV_STAGES = 3;
+constexpr int SV_STAGE = SV_TILE + 2 * SV_XIMG;
+// 1024 for the stage alignment, 8 KB so that the last digit pair's second half (a plane
+// past the 7th, read and discarded) stays inside the allocation
+constexpr int SV_SMEM = SV_STAGES * SV_STAGE + 1024 + SV_PLANE;
+constexpr int SV_TMEM = 128;                          // 2 buffers x (32 + 32) columns
+constexpr long long SV_SPIN = 1LL << 26;
+static_assert(SV_TILE == kSvTileBytes, "tile image size");
+static_assert(SV_STAGE % 1024 == 0, "stages stay 1024-byte aligned");
+
+// byte offset of 16-bit element e of row `row` of a 128-byte-row image, 128-byte swizzle
+__device__ __forceinline__ int sv_sw(int row, int e) {
+  return row * 128 + ((((e * 2) >> 4) ^ (row & 7)) << 4) + ((e * 2) & 15);
+}
+__device__ __forceinline__ uint32_t sv_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// matrix descriptor: 128-byte swizzle, leading / stride byte offsets
+__device__ __forceinline__ uint64_t sv_desc(const void* p, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((sv_u32(p) & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+__device__ __forceinline__ void sv_mbar_init(uint64_t* b, uint32_t cnt) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sv_u32(b)), "r"(cnt) : "memory");
+}
+__device__ __forceinline__ bool sv_mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t done;
+  asm volatile("{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}"
+               : "=r"(done) : "r"(sv_u32(b)), "r"(parity) : "memory");
+  return done != 0;
+}
+// bounded wait; gives up early when *abort is raised (checked every 256 polls)
+__device__ __forceinline__ bool sv_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
+  for (long long it = 0; it < SV_SPIN; ++it) {
+    if (sv_mbar_try(b, parity)) return true;
+    if ((it & 255) == 255 && *abort) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void sv_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+               "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void sv_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sv_u32(b)) : "memory");
+}
+__device__ __forceinline__ void sv_ld32(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+// The 7 digits of x / u (u = 2^(e-7), |x| < 2^e) as fx_digits<7>(x, 2^48 / u) writes them,
+// with integer instructions only: T = rint(x 2^(55-e)) from the bit pattern (the scaling
+// by a power of two is exact, the rounding is to nearest, ties to even), then the
+// balanced base-256 digits.
+__device__ __forceinline__ void sv_digits7(double x, int e, __nv_bfloat16* out) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  long long T = 0;
+  if (ex != 0) {                                        // zero and subnormals (far below u) give 0
+    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+    const int sh = (ex - 1023) - 52 + 55 - e;          // value = m 2^(ex-1075), times 2^(55-e)
+    unsigned long long t;
+    if (sh >= 0) {
+      t = m << sh;                                      // sh <= 2 since |x| < 2^e
+    } else if (sh > -64) {
+      const int r = -sh;
+      t = m >> r;
+      const unsigned long long rem = m & ((1ULL << r) - 1), half = 1ULL << (r - 1);
+      if (rem > half || (rem == half && (t & 1ULL))) ++t;
+    } else {
+      t = 0;
+    }
+    T = (bits >> 63) ? -(long long)t : (long long)t;
+  }
+#pragma unroll
+  for (int i = 6; i > 0; --i) {
+    const int d = (int)(((T + 128) & 255) - 128);
+    out[i] = __float2bfloat16_rn((float)d);
+    T = (T - d) >> 8;
+  }
+  out[0] = __float2bfloat16_rn((float)T);
+}
+
+// Tile images of the lower tiles (R, J), rbp <= J <= R < nrbt, of A (column-major, ld = n;
+// diagonal tiles full), tile index f = (R - rbp)(R - rbp + 1)/2 + (J - rbp): one CTA per tile.
+__global__ void __launch_bounds__(256) k_sv_digits(const double* __restrict__ A, int n, int rbp, uint8_t* img,
+                                                   double* scl) {
+  __shared__ double red[8];
+  const long long f = blockIdx.x;
+  long long a = (long long)((sqrt(8.0 * (double)f + 1.0) - 1.0) * 0.5);
+  while (a * (a + 1) / 2 > f) --a;
+  while ((a + 1) * (a + 2) / 2 <= f) ++a;
+  const int R = rbp + (int)a, J = rbp + (int)(f - a * (a + 1) / 2);
+  const int t = threadIdx.x, r = t & 63, c0 = t >> 6;
+  const int gr = R * TB + r;
+  double v[16];
+  double mx = 0.0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int gc = J * TB + c0 + 4 * k;
+    v[k] = (gr < n && gc < n) ? A[gr + (long long)gc * n] : 0.0;
+    mx = fmax(mx, fabs(v[k]));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((t & 31) == 0) red[t >> 5] = mx;
+  __syncthreads();
+  if (t < 32) {
+    double m = (t < 8) ? red[t] : 0.0;
+    for (int o = 4; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (t == 0) red[0] = m;
+  }
+  __syncthreads();
+  const double u = fx_unit(red[0]);
+  const double scale = 0x1p48 / u;
+  uint8_t* base = img + f * (long long)SV_TILE;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    __nv_bfloat16 d[7];
+    fx_digits<7>(v[k], scale, d);
+    const int off = sv_sw(c0 + 4 * k, r);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) *(__nv_bfloat16*)(base + q * SV_PLANE + off) = d[q];
+  }
+  if (t == 0) scl[f] = u;
+}
+
+template <bool TC>
+__global__ void __launch_bounds__(RT, TC ? 1 : 2) k_panel(PanelParams p) {
+  // the thread that arrives at the grid barriers: with the tensor-core mat-vec one of an
+  // idle warp (warp 3), not the bulk-copy producer, whose fences would also wait for its
+  // copies' bookkeeping
+  constexpr int kLeader = TC ? 96 : 0;
   __shared__ double sh[40];
   __shared__ double Wi[NBP], Vi[NBP], vtv[NBP], wtv[NBP];
-  __shared__ double tile[TB * (TB + 1)];   // P1 scratch; P2 row-block sums [8][64]
+  __shared__ double tile_s[TC ? 1 : TB * (TB + 1)];   // P1 scratch; P2 row-block sums [8][64]
+  // tensor-core mat-vec: a ring of stages (tile image, x_J and x_R digits) in dynamic
+  // shared memory, whose first stage doubles as P1's scratch (the phases never overlap)
+  extern __shared__ uint8_t sv_raw[];
+  __shared__ uint64_t sv_full[SV_STAGES], sv_empty[SV_STAGES], sv_accf[2], sv_acce[2], sv_drain;
+  __shared__ float sv_xchg[TC ? 2 * 2 * 32 * 16 : 1];   // odd-digit partial levels, [tile parity][pair][lane][16]
+  __shared__ uint32_t sv_tbase;
+  __shared__ int sv_abort;
+  uint8_t* sv_stages = TC ? (uint8_t*)(((uintptr_t)sv_raw + 1023) & ~(uintptr_t)1023) : nullptr;
+  double* tile = TC ? (double*)sv_stages : tile_s;
   const int n = p.n, k0 = p.k0;
   const long long ld = n;
   double* A = p.A;
@@ -197,6 +392,31 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
     s_rank[1] = (int)atomicAdd((slot == 0) ? &p.bar->n0 : &p.bar->n1, 1u);
   }
   int L = blockIdx.x;
+  if constexpr (TC) {
+    if (t == 0) {
+      for (int s = 0; s < SV_STAGES; ++s) {
+        sv_mbar_init(&sv_full[s], 2);    // the producer's expect-tx arrival and its x-digits arrival
+        sv_mbar_init(&sv_empty[s], 1);
+      }
+      for (int b = 0; b < 2; ++b) {
+        sv_mbar_init(&sv_accf[b], 1);
+        sv_mbar_init(&sv_acce[b], 4);    // one arrival per epilogue warp
+      }
+      sv_mbar_init(&sv_drain, 1);
+      sv_abort = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if ((t >> 5) == 2) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sv_u32(&sv_tbase)),
+                   "r"(SV_TMEM) : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  long long sv_it = 0;       // tiles this CTA has taken through the tensor-core mat-vec
+  bool aborted = false;
 
   for (int j = 0; j < p.nbp; ++j) {
     const int i = k0 + j;
@@ -226,11 +446,19 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
       double vs[NBP / 8], ws[NBP / 8];
       if (r < n && j > 0)
         wcorr = ldg_cg(p.Wp + r + (long long)(j - 1) * ld) + alpha_w * ldg_cg(A + r + (long long)(i - 1) * ld);
+      // k < ceil(j / 8) (the same in every lane): groups with no column below j cost
+      // no float64 instructions (the pipe spends one issue per warp instruction, however
+      // many lanes take part)
+      const int kj = (j + 7) >> 3;
 #pragma unroll
       for (int k = 0; k < NBP / 8; ++k) {
-        const int c = q8 + 8 * k;
         vs[k] = 0.0;
         ws[k] = 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < NBP / 8; ++k) {
+        if (k >= kj) break;
+        const int c = q8 + 8 * k;
         if (r < n && c < j) {
           vs[k] = ldg_cg(A + r + (long long)(k0 + c) * ld);
           ws[k] = (c == j - 1) ? wcorr : ldg_cg(p.Wp + r + (long long)c * ld);
@@ -280,8 +508,22 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
         if (c < 2 * j && hf == 0) p.p_vw[(long long)ch * (2 * NBP) + c] = d2;
       }
       __syncthreads();
+      if constexpr (TC) {
+        // largest |x_r| over the chunk's rows r >= i+1 (the scale of x's digits in P2)
+        double mx = (r < n && r >= i + 1 && q8 == 0) ? fabs(a) : 0.0;
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+        if ((t & 31) == 0) sh[t >> 5] = mx;
+        __syncthreads();
+        if (t == 0) {
+          double m = 0.0;
+          for (int w2 = 0; w2 < RT / 32; ++w2) m = fmax(m, sh[w2]);
+          p.sv_mx[ch] = m;
+        }
+        __syncthreads();
+      }
     }
-    if (!grid_sync(p.bar, p.status, epoch, p.spin_limit)) return;
+    if (!grid_sync(p.bar, p.status, epoch, p.spin_limit, kLeader)) { aborted = true; break; }
     if (j == 0) {
       if (t == 0) s_rank[2] = (s_rank[0] == 0) ? s_rank[1] : (int)ld_acquire(&p.bar->n0) + s_rank[1];
       __syncthreads();
@@ -329,9 +571,11 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
       while ((a + 1) * (a + 2) / 2 <= f0) ++a;
       R0 = rb0 + (int)a;
       J0 = rb0 + (int)(f0 - a * (a + 1) / 2);
-      load_tile(R0, J0);
+      if constexpr (!TC) load_tile(R0, J0);
     }
     const Refl h = householder(p, i, sh);
+    double xmax = 0.0;
+    if constexpr (TC) xmax = max_partials(p.sv_mx, ceil_div_d(n - i, RC), sh);
     {
       // V^T v = V(i+1,:) + scale * (sum over the P1 chunks), the same for W^T v:
       // the first CTAs finish these 2j sums (one warp per value) for P3
@@ -346,82 +590,339 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
         }
       }
     }
-    if (f0 < f1) {
-      // x entries of rows >= lo (written by P1 of this column: read through L2)
-      auto xval = [&](int r) { return (r >= lo && r < n) ? ldg_cg(A + r + (long long)i * ld) : 0.0; };
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};   // y_R partials of the thread's rows
-      double xr[4];
-      int R = R0, J = J0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) xr[k] = xval(R * TB + rq + 16 * k);
-      for (long long f = f0; f < f1; ++f) {
-        int Rn = R, Jn = J + 1;             // next tile
-        if (Jn > Rn) { ++Rn; Jn = rb0; }
-        double cur[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) cur[e] = nxt[e];
-        double xc[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) xc[c] = xval(J * TB + cq0 + c);
-        if (f + 1 < f1) load_tile(Rn, Jn);   // in flight while this tile is used
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[k] = fma(cur[4 * c + k], xc[c], acc[k]);
-        if (J < R) {
-          double q[4];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            q[c] = cur[4 * c] * xr[0];
-#pragma unroll
-            for (int k = 1; k < 4; ++k) q[c] = fma(cur[4 * c + k], xr[k], q[c]);
+    if constexpr (TC) {
+      // Roles: warp 0 feeds the stages (bulk copies of tile images, x digits written by
+      // the warp), one thread of warp 1 issues the MMAs, warps 4-7 drain the accumulators
+      // (TMEM lane quadrant = warp % 4; with M = 64, row m sits in lane 32 (m/16) + m%16).
+      volatile int* abort = &sv_abort;
+      const int rbp = k0 / TB;
+      const double ux = fx_unit(xmax);
+      int xe = 0;                     // ux = 2^(xe - 7)
+      frexp(ux, &xe);
+      xe += 6;
+      const long long nt = f1 - f0;
+      // P1's generic-proxy use of the first stage is complete before the copy engine
+      // writes the stages again
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (nt > 0 && wq == 0) {
+        int R = R0, J = J0;
+        long long issued = 0;
+        // Lanes take elements lane and lane + 32 of a 64-block.  x_J's values are loaded one
+        // tile ahead; x_R's digits are kept for the whole row block and written to every
+        // stage that needs them.
+        auto xval = [&](int B, int e2) {
+          const int r = B * TB + lane + 32 * e2;
+          return (r >= lo && r < n) ? ldg_cg(A + r + (long long)i * ld) : 0.0;
+        };
+        __nv_bfloat16 dr[2][7];
+        int r_cached = -1;
+        double xnJ[2] = {xval(J, 0), xval(J, 1)};
+        double xnR[2] = {xval(R, 0), xval(R, 1)};
+        for (long long q = 0; q < nt; ++q) {
+          const long long it = sv_it + q;
+          const int s = (int)(it % SV_STAGES);
+          int ok = 1;
+          if (lane == 0 && it >= SV_STAGES) ok = sv_wait(&sv_empty[s], (uint32_t)(((it / SV_STAGES) + 1) & 1), abort);
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok) {
+            if (lane == 0) { set_status(p.status, MOLGW_E_TIMEOUT); *abort = 1; atomicExch(&p.bar->abort, 1); }
+            break;
           }
-          // sum over the 16 lanes of the half-warp (the tile's 64 rows), scattering the
-          // four columns: lane bits 3 and 2 select the column each lane keeps
-          const bool b3 = (rq & 8) != 0, b2 = (rq & 4) != 0;
-          const double k0v = b3 ? q[2] : q[0], k1v = b3 ? q[3] : q[1];
-          const double s0v = b3 ? q[0] : q[2], s1v = b3 ? q[1] : q[3];
-          const double h0 = k0v + __shfl_xor_sync(0xffffffffu, s0v, 8);
-          const double h1 = k1v + __shfl_xor_sync(0xffffffffu, s1v, 8);
-          double v = (b2 ? h1 : h0) + __shfl_xor_sync(0xffffffffu, b2 ? h0 : h1, 4);
-          v += __shfl_xor_sync(0xffffffffu, v, 2);
-          v += __shfl_xor_sync(0xffffffffu, v, 1);
-          if ((rq & 3) == 0) {
-            const long long ft = (long long)(R - rb0) * (R - rb0 + 1) / 2 + (J - rb0);
-            p.p_t[ft * TB + cq0 + 2 * (b3 ? 1 : 0) + (b2 ? 1 : 0)] = v;
+          uint8_t* st = sv_stages + (size_t)s * SV_STAGE;
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sv_u32(&sv_full[s])),
+                         "r"(SV_TILE) : "memory");
+          if (lane < 7) {
+            // one copy per digit plane (8 KB each, concurrent), all completing on full[s]
+            const long long fp = (long long)(R - rbp) * (R - rbp + 1) / 2 + (J - rbp);
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             sv_u32(st + lane * SV_PLANE)),
+                         "l"(p.sv_img + fp * SV_TILE + lane * SV_PLANE), "r"(SV_PLANE), "r"(sv_u32(&sv_full[s]))
+                         : "memory");
+          }
+          ++issued;
+          const double xj[2] = {xnJ[0], xnJ[1]};
+          if (R != r_cached) {
+            // a new row block: the digits of x_R (its values were loaded ahead)
+#pragma unroll
+            for (int e2 = 0; e2 < 2; ++e2) sv_digits7(xnR[e2], xe, dr[e2]);
+            r_cached = R;
+          }
+          int Rn = R, Jn = J + 1;
+          if (Jn > Rn) { ++Rn; Jn = rb0; }
+          if (q + 1 < nt) {
+            xnJ[0] = xval(Jn, 0);
+            xnJ[1] = xval(Jn, 1);
+            if (Rn != R) {
+              xnR[0] = xval(Rn, 0);
+              xnR[1] = xval(Rn, 1);
+            }
+          }
+          uint8_t* xi = st + SV_TILE;
+#pragma unroll
+          for (int e2 = 0; e2 < 2; ++e2) {
+            const int e = lane + 32 * e2;
+            __nv_bfloat16 d[7];
+            sv_digits7(xj[e2], xe, d);
+#pragma unroll
+            for (int qd = 0; qd < 7; ++qd) *(__nv_bfloat16*)(xi + sv_sw(qd, e)) = d[qd];
+            *(__nv_bfloat16*)(xi + sv_sw(7, e)) = __float2bfloat16_rn(0.0f);
+            if (J < R) {
+#pragma unroll
+              for (int qd = 0; qd < 7; ++qd) *(__nv_bfloat16*)(xi + SV_XIMG + sv_sw(qd, e)) = dr[e2][qd];
+              *(__nv_bfloat16*)(xi + SV_XIMG + sv_sw(7, e)) = __float2bfloat16_rn(0.0f);
+            }
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sv_u32(&sv_full[s])) : "memory");
+          R = Rn;
+          J = Jn;
+        }
+        // on an error path copies may still be in flight: they land before the phase ends
+        if (lane == 0) {
+          for (long long q = (issued > SV_STAGES ? issued - SV_STAGES : 0); q < issued; ++q) {
+            const long long it = sv_it + q;
+            for (long long k = 0; k < SV_SPIN; ++k)
+              if (sv_mbar_try(&sv_full[it % SV_STAGES], (uint32_t)((it / SV_STAGES) & 1))) break;
           }
         }
-        if (f + 1 == f1 || J == R) {
-          // end of this CTA's part of row block R: the rows' sums over the 16 threads that
-          // hold them (the two half-warps, then the eight warps through shared memory)
-          double* red = tile;               // [8][64]
+        __syncwarp();
+      } else if (nt > 0 && wq == 1) {
+        if (lane == 0) {
+          // D F32 (bit 4), A and B BF16 (bits 7, 10), A MN-major (bit 15) for A_RJ x_J,
+          // N = 8 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24)
+          const uint32_t id_n = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 17) | (8u << 24);
+          const uint32_t id_t = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 17) | (8u << 24);
+          int R = R0, J = J0;
+          long long q = 0;
+          for (; q < nt; ++q) {
+            const long long it = sv_it + q;
+            const int s = (int)(it % SV_STAGES), b = (int)(it & 1);
+            if (!sv_wait(&sv_full[s], (uint32_t)((it / SV_STAGES) & 1), abort)) break;
+            if (it >= 2 && !sv_wait(&sv_acce[b], (uint32_t)(((it >> 1) + 1) & 1), abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint8_t* st = sv_stages + (size_t)s * SV_STAGE;
+            const uint32_t d0 = sv_tbase + (uint32_t)(b * 64);
+            // Digit pair g = planes (2g, 2g+1) (the 4th pair's second plane lies past the
+            // image and is discarded).  MN-major: the pair's 64-element atoms 8 KB apart
+            // (leading byte offset), 8-row K groups 1 KB apart; K-major: 128 rows of 128 B.
+            // Offsets move the start address (16-byte units: a pair 1024, a 16-row K step of
+            // the MN-major operand 128, a 32-byte K step of a K-major one 2).
+            const uint64_t a_mn = sv_desc(st, SV_PLANE, 1024), a_k = sv_desc(st, 16, 1024);
+            const uint64_t bxj = sv_desc(st + SV_TILE, 16, 1024), bxr = sv_desc(st + SV_TILE + SV_XIMG, 16, 1024);
+            const bool below = J < R;
 #pragma unroll
-          for (int k = 0; k < 4; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 16);
-          __syncthreads();
-          if (lane < 16) {
+            for (int ks = 0; ks < 4; ++ks) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) red[wq * TB + rq + 16 * k] = acc[k];
+              for (int g = 0; g < 4; ++g) {
+                sv_mma(d0 + 8 * g, a_mn + (uint64_t)(1024 * g + 128 * ks), bxj + (uint64_t)(2 * ks), id_n,
+                       ks > 0 ? 1u : 0u);
+                if (below)
+                  sv_mma(d0 + 32 + 8 * g, a_k + (uint64_t)(1024 * g + 2 * ks), bxr + (uint64_t)(2 * ks), id_t,
+                         ks > 0 ? 1u : 0u);
+              }
+            }
+            sv_commit(&sv_empty[s]);
+            sv_commit(&sv_accf[b]);
+            if (++J > R) { ++R; J = rb0; }
           }
-          __syncthreads();
-          if (t < TB) {
-            double y = red[t];
-#pragma unroll
-            for (int w2 = 1; w2 < RT / 32; ++w2) y += red[w2 * TB + t];
-            const int r = R * TB + t;
-            if (r < n) p.p_y[(long long)blockIdx.x * n + r] = y;
-          }
-#pragma unroll
-          for (int k = 0; k < 4; ++k) acc[k] = 0.0;
-          if (f + 1 < f1 && Rn != R) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) xr[k] = xval(Rn * TB + rq + 16 * k);
+          if (q < nt) {
+            set_status(p.status, MOLGW_E_TIMEOUT);
+            *abort = 1;
+            atomicExch(&p.bar->abort, 1);
+            if (q > 0) {
+              // the MMAs already issued finish before TMEM or the stages are given up
+              sv_commit(&sv_drain);
+              for (long long k = 0; k < SV_SPIN; ++k)
+                if (sv_mbar_try(&sv_drain, 0u)) break;
+            }
           }
         }
-        R = Rn;
-        J = Jn;
+        __syncwarp();
+      } else if (nt > 0 && wq >= 4) {
+        // TMEM lane quadrant qd: warps qd = 0, 1 hold the even digits of tile rows 32 qd + lane,
+        // warps qd = 2, 3 the odd digits of rows 32 (qd - 2) + lane
+        const int qd = wq - 4;
+        const bool odd = qd >= 2;
+        const int pair = qd & 1;
+        const int row = 32 * pair + lane;
+        int R = R0, J = J0;
+        double acc = 0.0;
+        // tile scales, loaded one tile ahead
+        double us_next = p.sv_scl[(long long)(R - rbp) * (R - rbp + 1) / 2 + (J - rbp)];
+        // partial level sums of this warp's digits: l = i + j <= 6, i = 2g (+1 if odd)
+        auto levels = [&](const uint32_t* S, float* P) {
+#pragma unroll
+          for (int l = 0; l < 7; ++l) P[l] = 0.0f;
+#pragma unroll
+          for (int g = 0; g < 4; ++g)
+#pragma unroll
+            for (int j = 0; j < 7; ++j) {
+              const int l = 2 * g + j + (odd ? 1 : 0);
+              if (l <= 6) P[l] += __uint_as_float(S[8 * g + j]);
+            }
+        };
+        // value = (2^-24 vh + 2^-48 vl) u_tile u_x: two conversions, one multiply, one FMA
+        auto finish = [&](const float* P, const float* Q, double us24) {
+          long long L[7];
+#pragma unroll
+          for (int l = 0; l < 7; ++l) L[l] = __float2int_rn(P[l] + Q[l]);   // integers below 2^23: exact
+          const long long vh = (L[0] << 24) + (L[1] << 16) + (L[2] << 8) + L[3];
+          const long long vl = (L[4] << 16) + (L[5] << 8) + L[6];
+          return fma((double)vl, us24 * 0x1p-24, (double)vh * us24);
+        };
+        for (long long q = 0; q < nt; ++q) {
+          const long long it = sv_it + q;
+          const int b = (int)(it & 1);
+          int got = 1;
+          if (lane == 0) got = sv_wait(&sv_accf[b], (uint32_t)((it >> 1) & 1), abort);
+          got = __shfl_sync(0xffffffffu, got, 0);
+          // the four epilogue warps agree (barrier 1 with an AND): a wait that ran out in one
+          // of them ends the loop in all, so that their named barriers stay matched
+          int all;
+          asm volatile("{\n .reg .pred pi, po;\n setp.ne.s32 pi, %1, 0;\n bar.red.and.pred po, 1, 128, pi;\n selp.s32 %0, 1, 0, po;\n}"
+                       : "=r"(all) : "r"(got) : "memory");
+          if (!all) {
+            if (lane == 0) { set_status(p.status, MOLGW_E_TIMEOUT); *abort = 1; atomicExch(&p.bar->abort, 1); }
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const bool below = J < R;
+          const uint32_t tq = sv_tbase + ((uint32_t)(32 * qd) << 16) + (uint32_t)(b * 64);
+          float Pn[7], Pt[7];
+          {
+            uint32_t S[32];
+            sv_ld32(tq, S);                      // A_RJ x_J: columns 0..31 of the buffer
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            levels(S, Pn);
+            if (below) {
+              sv_ld32(tq + 32, S);               // A_RJ^T x_R: columns 32..63
+              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+              levels(S, Pt);
+            }
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sv_u32(&sv_acce[b])) : "memory");
+          const double us = us_next * ux;
+          {
+            int Rn = R, Jn = J + 1;
+            if (Jn > Rn) { ++Rn; Jn = rb0; }
+            if (q + 1 < nt) us_next = p.sv_scl[(long long)(Rn - rbp) * (Rn - rbp + 1) / 2 + (Jn - rbp)];
+          }
+          float* xb = sv_xchg + ((q & 1) * 2 + pair) * 32 * 16 + lane * 16;
+          // the even-digit warps hand their partial levels over; the odd-digit warps (on the
+          // SM sub-partitions that neither the producer nor the MMA thread uses) finish
+          if (!odd) {
+#pragma unroll
+            for (int l = 0; l < 7; ++l) {
+              xb[l] = Pn[l];
+              xb[8 + l] = below ? Pt[l] : 0.0f;
+            }
+          }
+          asm volatile("bar.sync 1, 128;" ::: "memory");   // the four epilogue warps
+          if (odd) {
+            float Qn[7], Qt[7];
+#pragma unroll
+            for (int l = 0; l < 7; ++l) {
+              Qn[l] = xb[l];
+              Qt[l] = xb[8 + l];
+            }
+            acc += finish(Pn, Qn, us * 0x1p-24);
+            if (below) {
+              const long long ft = (long long)(R - rb0) * (R - rb0 + 1) / 2 + (J - rb0);
+              p.p_t[ft * TB + row] = finish(Pt, Qt, us * 0x1p-24);
+            }
+            if (q + 1 == nt || J == R) {
+              const int gr = R * TB + row;
+              if (gr < n) p.p_y[(long long)blockIdx.x * n + gr] = acc;
+              acc = 0.0;
+            }
+          }
+          if (++J > R) { ++R; J = rb0; }
+        }
+      }
+      sv_it += nt;
+    } else {
+      if (f0 < f1) {
+        // x entries of rows >= lo (written by P1 of this column: read through L2)
+        auto xval = [&](int r) { return (r >= lo && r < n) ? ldg_cg(A + r + (long long)i * ld) : 0.0; };
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};   // y_R partials of the thread's rows
+        double xr[4];
+        int R = R0, J = J0;
+  #pragma unroll
+        for (int k = 0; k < 4; ++k) xr[k] = xval(R * TB + rq + 16 * k);
+        for (long long f = f0; f < f1; ++f) {
+          int Rn = R, Jn = J + 1;             // next tile
+          if (Jn > Rn) { ++Rn; Jn = rb0; }
+          double cur[16];
+  #pragma unroll
+          for (int e = 0; e < 16; ++e) cur[e] = nxt[e];
+          double xc[4];
+  #pragma unroll
+          for (int c = 0; c < 4; ++c) xc[c] = xval(J * TB + cq0 + c);
+          if (f + 1 < f1) load_tile(Rn, Jn);   // in flight while this tile is used
+  #pragma unroll
+          for (int k = 0; k < 4; ++k)
+  #pragma unroll
+            for (int c = 0; c < 4; ++c) acc[k] = fma(cur[4 * c + k], xc[c], acc[k]);
+          if (J < R) {
+            double q[4];
+  #pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              q[c] = cur[4 * c] * xr[0];
+  #pragma unroll
+              for (int k = 1; k < 4; ++k) q[c] = fma(cur[4 * c + k], xr[k], q[c]);
+            }
+            // sum over the 16 lanes of the half-warp (the tile's 64 rows), scattering the
+            // four columns: lane bits 3 and 2 select the column each lane keeps
+            const bool b3 = (rq & 8) != 0, b2 = (rq & 4) != 0;
+            const double k0v = b3 ? q[2] : q[0], k1v = b3 ? q[3] : q[1];
+            const double s0v = b3 ? q[0] : q[2], s1v = b3 ? q[1] : q[3];
+            const double h0 = k0v + __shfl_xor_sync(0xffffffffu, s0v, 8);
+            const double h1 = k1v + __shfl_xor_sync(0xffffffffu, s1v, 8);
+            double v = (b2 ? h1 : h0) + __shfl_xor_sync(0xffffffffu, b2 ? h0 : h1, 4);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            if ((rq & 3) == 0) {
+              const long long ft = (long long)(R - rb0) * (R - rb0 + 1) / 2 + (J - rb0);
+              p.p_t[ft * TB + cq0 + 2 * (b3 ? 1 : 0) + (b2 ? 1 : 0)] = v;
+            }
+          }
+          if (f + 1 == f1 || J == R) {
+            // end of this CTA's part of row block R: the rows' sums over the 16 threads that
+            // hold them (the two half-warps, then the eight warps through shared memory)
+            double* red = tile;               // [8][64]
+  #pragma unroll
+            for (int k = 0; k < 4; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], 16);
+            __syncthreads();
+            if (lane < 16) {
+  #pragma unroll
+              for (int k = 0; k < 4; ++k) red[wq * TB + rq + 16 * k] = acc[k];
+            }
+            __syncthreads();
+            if (t < TB) {
+              double y = red[t];
+  #pragma unroll
+              for (int w2 = 1; w2 < RT / 32; ++w2) y += red[w2 * TB + t];
+              const int r = R * TB + t;
+              if (r < n) p.p_y[(long long)blockIdx.x * n + r] = y;
+            }
+  #pragma unroll
+            for (int k = 0; k < 4; ++k) acc[k] = 0.0;
+            if (f + 1 < f1 && Rn != R) {
+  #pragma unroll
+              for (int k = 0; k < 4; ++k) xr[k] = xval(Rn * TB + rq + 16 * k);
+            }
+          }
+          R = Rn;
+          J = Jn;
+        }
       }
     }
-    if (!grid_sync(p.bar, p.status, epoch, p.spin_limit)) return;
+    if (!grid_sync(p.bar, p.status, epoch, p.spin_limit, kLeader)) { aborted = true; break; }
 
     // ---------------- P3: W column ----------------
     const int n3 = ceil_div_d(n - i - 1, RC);
@@ -480,31 +981,42 @@ __global__ void __launch_bounds__(RT, 2) k_panel(PanelParams p) {
       p.tau[i] = h.tau;
       A[(i + 1) + (long long)i * ld] = 1.0;
     }
-    if (!grid_sync(p.bar, p.status, epoch, p.spin_limit)) return;
+    if (!grid_sync(p.bar, p.status, epoch, p.spin_limit, kLeader)) { aborted = true; break; }
   }
 
   // ---------------- end of panel: last W correction and packing ----------------
-  const int i = p.k1 - 1, j = p.nbp - 1;
-  const double s = sum_partials(p.p_wv, ceil_div_d(n - i - 1, RC), sh);
-  const double alpha_w = -0.5 * ldg_cg(p.tau + i) * s;
-  const long long m = n - p.k1;
-  const int n5 = ceil_div_d(n - i - 1, RT);
-  for (int ch = blockIdx.x; ch < n5; ch += gridDim.x) {
-    const int r = i + 1 + ch * RT + t;
-    if (r >= n) continue;
-    double* wc = p.Wp + r + (long long)j * ld;
-    const double wnew = ldg_cg(wc) + alpha_w * ldg_cg(A + r + (long long)i * ld);
-    *wc = wnew;
-    if (r >= p.k1) {
-      const long long rr = r - p.k1;
-      for (int c = 0; c < p.nbp; ++c) {
-        const double vv = ldg_cg(A + r + (long long)(k0 + c) * ld);
-        const double ww = (c == j) ? wnew : ldg_cg(p.Wp + r + (long long)c * ld);
-        p.VW[rr + (long long)c * m] = vv;
-        p.VW[rr + (long long)(p.nbp + c) * m] = ww;
-        p.WV[rr + (long long)c * m] = ww;
-        p.WV[rr + (long long)(p.nbp + c) * m] = vv;
+  if (!aborted) {
+    const int i = p.k1 - 1, j = p.nbp - 1;
+    const double s = sum_partials(p.p_wv, ceil_div_d(n - i - 1, RC), sh);
+    const double alpha_w = -0.5 * ldg_cg(p.tau + i) * s;
+    const long long m = n - p.k1;
+    const int n5 = ceil_div_d(n - i - 1, RT);
+    for (int ch = blockIdx.x; ch < n5; ch += gridDim.x) {
+      const int r = i + 1 + ch * RT + t;
+      if (r >= n) continue;
+      double* wc = p.Wp + r + (long long)j * ld;
+      const double wnew = ldg_cg(wc) + alpha_w * ldg_cg(A + r + (long long)i * ld);
+      *wc = wnew;
+      if (r >= p.k1) {
+        const long long rr = r - p.k1;
+        for (int c = 0; c < p.nbp; ++c) {
+          const double vv = ldg_cg(A + r + (long long)(k0 + c) * ld);
+          const double ww = (c == j) ? wnew : ldg_cg(p.Wp + r + (long long)c * ld);
+          p.VW[rr + (long long)c * m] = vv;
+          p.VW[rr + (long long)(p.nbp + c) * m] = ww;
+          p.WV[rr + (long long)c * m] = ww;
+          p.WV[rr + (long long)(p.nbp + c) * m] = vv;
+        }
       }
+    }
+  }
+  if constexpr (TC) {
+    // every role has finished (its MMAs and copies waited for) before TMEM is released
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((t >> 5) == 2) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sv_tbase), "r"(SV_TMEM) : "memory");
     }
   }
 }
@@ -526,6 +1038,8 @@ __global__ void k_clean(double* A, int n) {
 
 int g_coop_blocks_per_sm = -1;   // the panel grid never exceeds kMaxPanelGrid (p_y has that many rows)
 int g_num_sms = 0;
+int g_sv_blocks_per_sm = -1;     // k_panel<true>: co-resident CTAs per SM with its stage ring (0: unusable)
+constexpr int kSvMinRows = 1024; // trailing matrices from this size use the tensor-core mat-vec
 
 }  // namespace
 
@@ -535,9 +1049,16 @@ int tridiag_coop_capacity() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_panel, RT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_panel<false>, RT, 0);
     g_coop_blocks_per_sm = std::max(1, std::min(occ, 2));
     g_coop_blocks_per_sm = std::min(g_coop_blocks_per_sm, kMaxPanelGrid / std::max(g_num_sms, 1));
+    int occ_sv = 0;
+    if (cudaFuncSetAttribute(k_panel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SV_SMEM) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_sv, k_panel<true>, RT, SV_SMEM) == cudaSuccess)
+      g_sv_blocks_per_sm = std::min(occ_sv, 1);
+    else
+      g_sv_blocks_per_sm = 0;
+    cudaGetLastError();
   }
   return g_num_sms * g_coop_blocks_per_sm;
 }
@@ -564,6 +1085,15 @@ void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
   // persistent panels of all lanes fit on the device at the same time.
   int cap = g_num_sms * g_coop_blocks_per_sm;
   if (ex.coop_cap > 0) cap = std::max(2 * NBP / (RT / 32), std::min(cap, ex.coop_cap));
+  // Tensor-core mat-vec (MOLGW_FLAG_EIG_TC, the context's own stream): tile images and
+  // scales in w.sv, then the column-maximum partials.
+  const bool sv_ok = w.sv && ex.coop_cap == 0 && n <= w.sv_n && g_sv_blocks_per_sm > 0;
+  if (sv_ok) {
+    const long long cap_tiles = eig_sv_tiles(w.sv_n);
+    p.sv_img = (const uint8_t*)w.sv;
+    p.sv_scl = (const double*)((uint8_t*)w.sv + cap_tiles * kSvTileBytes);
+    p.sv_mx = (double*)p.sv_scl + cap_tiles;
+  }
   const int ncols = n - 1;
   for (int k0 = 0; k0 < ncols; k0 += NBP) {
     const int nbp = std::min(NBP, ncols - k0);
@@ -571,13 +1101,24 @@ void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
     p.k0 = k0; p.nbp = nbp; p.k1 = k1;
     const int nrb = nrbt - (k0 + 1) / TB;
     const long long tiles = (long long)nrb * (nrb + 1) / 2;
-    const int grid = (int)std::max<long long>(2 * NBP / (RT / 32),
-                                               std::min<long long>(cap, std::max<long long>(tiles, ceil_div(n - k0, RC))));
-    {
+    if (sv_ok && n - k0 >= kSvMinRows) {
+      KScope ks(ex, MOLGW_K_TRIDIAG_PANEL, 2);
+      const int rbp = k0 / TB;
+      const long long tiles_p = (long long)(nrbt - rbp) * (nrbt - rbp + 1) / 2;
+      k_sv_digits<<<(unsigned)tiles_p, 256, 0, ex.st>>>(A, n, rbp, (uint8_t*)p.sv_img, (double*)p.sv_scl);
+      const int cap_sv = g_num_sms * g_sv_blocks_per_sm;
+      const int grid = (int)std::max<long long>(2 * NBP / (RT / 32),
+                                                 std::min<long long>(cap_sv, std::max<long long>(tiles, ceil_div(n - k0, RC))));
+      cudaMemsetAsync(p.bar, 0, sizeof(GridBar), ex.st);
+      void* args[] = {&p};
+      cudaLaunchCooperativeKernel((const void*)k_panel<true>, dim3(grid), dim3(RT), args, SV_SMEM, ex.st);
+    } else {
+      const int grid = (int)std::max<long long>(2 * NBP / (RT / 32),
+                                                 std::min<long long>(cap, std::max<long long>(tiles, ceil_div(n - k0, RC))));
       KScope ks(ex, MOLGW_K_TRIDIAG_PANEL, 1);
       cudaMemsetAsync(p.bar, 0, sizeof(GridBar), ex.st);
       void* args[] = {&p};
-      cudaLaunchCooperativeKernel((const void*)k_panel, dim3(grid), dim3(RT), args, 0, ex.st);
+      cudaLaunchCooperativeKernel((const void*)k_panel<false>, dim3(grid), dim3(RT), args, 0, ex.st);
     }
     const int m = n - k1;
     if (m > 0 && w.fx && m <= w.fx_rows && m >= 128) {

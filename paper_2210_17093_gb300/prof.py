@@ -1,8 +1,9 @@
 """Small drivers to profile the library's kernels (e.g. under ncu).
 
-    python -m paper_2210_17093_gb300.prof eigh N [REPS]
+    python -m paper_2210_17093_gb300.prof eigh N [REPS [FLAGS]]
         float64 symmetric eigensolve of a random N x N matrix (tridiagonalisation,
-        bisection, twisted vectors, full back-transformation) through molgw_b200_eigh;
+        bisection, twisted vectors, full back-transformation) through molgw_b200_eigh
+        (FLAGS: e.g. 32 for MOLGW_FLAG_EIG_TC);
     python -m paper_2210_17093_gb300.prof qsgw NB NO NA PRECISION [REPS [FLAGS]]
         qsGW iterations of one synthetic molecule (seed 1) at the given precision
         (FLAGS: extra MOLGW_FLAG_* bits, e.g. 32 for MOLGW_FLAG_EIG_TC);
@@ -28,7 +29,7 @@ def _stats(ctx):
     return {k: round(v[1], 2) for k, v in ctx.kernel_stats(reset=True).items() if v[0]}
 
 
-def eigh(n: int, reps: int = 1) -> None:
+def eigh(n: int, reps: int = 1, flags: int = 0) -> None:
     import torch
 
     from . import Context, FLAG_KTIMING
@@ -37,7 +38,7 @@ def eigh(n: int, reps: int = 1) -> None:
     A = (A + A.T).contiguous()
     w = torch.empty(n, dtype=torch.float64, device="cuda")
     Z = torch.empty(n * n, dtype=torch.float64, device="cuda")
-    with Context(stream=torch.cuda.current_stream(), flags=FLAG_KTIMING) as ctx:
+    with Context(stream=torch.cuda.current_stream(), flags=FLAG_KTIMING | flags) as ctx:
         for r in range(reps):
             ctx.kernel_stats(reset=True)
             torch.cuda.synchronize()
@@ -144,7 +145,7 @@ def trace(nb: int, no: int, na: int, precision: str, flags: int, seed: int) -> N
 if __name__ == "__main__":
     a = sys.argv[1:]
     if a and a[0] == "eigh":
-        eigh(int(a[1]), int(a[2]) if len(a) > 2 else 1)
+        eigh(int(a[1]), int(a[2]) if len(a) > 2 else 1, int(a[3]) if len(a) > 3 else 0)
     elif a and a[0] == "batch":
         batch(a[1], int(a[2]), int(a[3]) if len(a) > 3 else 2)
     elif a and a[0] == "trace":
