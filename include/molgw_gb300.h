@@ -93,11 +93,13 @@ enum molgw_flags {
                                     buffers and the set of molecules stay the same                  */
   MOLGW_FLAG_USE_STREAM = 1u << 3, /* run on opts.stream even when it is NULL (the legacy default stream) */
   MOLGW_FLAG_TC_AB = 1u << 4,      /* with a split precision: stages (a) and (b) on the tensor cores too */
-  MOLGW_FLAG_EIG_TC = 1u << 5,     /* the trailing SYR2K update of the tridiagonalisation on the
-                                      tensor cores: 7 fixed-point BF16 digits per value (56 bits,
-                                      values within 4x of their group maximum exact), exact sums,
-                                      one float64 rounding -- float64 accuracy in the normwise
-                                      sense, not float64 arithmetic; any precision            */
+  MOLGW_FLAG_EIG_TC = 1u << 5,     /* the trailing SYR2K update of the tridiagonalisation and the
+                                      back-transformation on the tensor cores: 7 fixed-point BF16
+                                      digits per value (56 bits, values within 4x of their group
+                                      maximum exact), exact sums, one float64 rounding; and the
+                                      panel's mat-vec in fixed point (molgw_b200_set_panel_matvec)
+                                      -- float64 accuracy in the normwise sense, not float64
+                                      arithmetic; any precision                               */
   MOLGW_FLAG_QSMP2 = 1u << 6       /* qsMP2 instead of qsGW: Sigma_c is the second-order self-energy
                                       of Eq. (Sigma.c.MP2), made static and Hermitian by
                                       Eq. (Sigma.c.qsMP2.real).  Its second-order exchange factor
@@ -230,6 +232,22 @@ int molgw_b200_inject_fault(molgw_ctx ctx, int code);
  * context computes as before (every launch clears its barrier block).  No fault is
  * made and no wait is endless.  MOLGW_E_ARG for a NULL context. */
 int molgw_b200_set_wait_limits(molgw_ctx ctx, long long grid_spins, int bisect_rounds);
+
+/* The symmetric matrix-vector product y = A22 v of the tridiagonalisation's panel
+ * kernel (Sec. II.E's diagonalisation of the Casida matrix; LAPACK dlatrd's level-2
+ * step) with MOLGW_FLAG_EIG_TC, on the context stream:
+ *   MOLGW_MATVEC_AUTO  the default: the integer one;
+ *   MOLGW_MATVEC_FP64  float64 arithmetic (as without MOLGW_FLAG_EIG_TC);
+ *   MOLGW_MATVEC_TC    tensor cores: tile images of 7 BF16 digits (56-bit fixed point per
+ *                      64 x 64 tile), exact digit-pair sums, from trailing order 1024;
+ *   MOLGW_MATVEC_INT   32 x 32 -> 64-bit integer multiply-adds on 53-bit fixed-point images
+ *                      (one grid per 64 x 64 tile of A22, one for v), exact products and
+ *                      sums, one rounding per row, from trailing order 256.
+ * The fixed-point forms are float64-accurate in the normwise sense (every value to 2^-54
+ * of its group's largest), not float64 arithmetic.  Lanes of a batch (mol = -1 over
+ * several molecules) always use float64.  MOLGW_E_ARG for a NULL context or another kind. */
+enum molgw_matvec { MOLGW_MATVEC_AUTO = 0, MOLGW_MATVEC_FP64 = 1, MOLGW_MATVEC_TC = 2, MOLGW_MATVEC_INT = 3 };
+int molgw_b200_set_panel_matvec(molgw_ctx ctx, int kind);
 
 /* Copy an intermediate of the last pass of molecule `mol` into out[count]
  * (count must equal the item's size).  Items: */

@@ -61,6 +61,7 @@ struct molgw_ctx_s {
   GemmTuner tuner;               // float64 GEMM tile choices (molgw_b200_autotune)
   long long grid_spins = kGridSpinLimit;   // molgw_b200_set_wait_limits
   int bisect_rounds = kBisectRounds;
+  int panel_matvec = MOLGW_MATVEC_AUTO;    // molgw_b200_set_panel_matvec
 };
 
 namespace {
@@ -183,6 +184,7 @@ int lane_get(molgw_ctx c, int k, Lane** out) {
     l.ex.tuner = &c->tuner;
     l.ex.grid_spins = c->grid_spins;
     l.ex.bisect_rounds = c->bisect_rounds;
+    l.ex.panel_matvec = c->panel_matvec;
     c->lanes.push_back(l);
   }
   *out = &c->lanes[k];
@@ -1153,6 +1155,14 @@ int molgw_b200_set_wait_limits(molgw_ctx c, long long grid_spins, int bisect_rou
     l.ex.bisect_rounds = c->bisect_rounds;
   }
   ++c->gen;   // a captured graph holds the old bounds in its launch parameters
+  return MOLGW_OK;
+}
+
+int molgw_b200_set_panel_matvec(molgw_ctx c, int kind) {
+  if (!c || kind < MOLGW_MATVEC_AUTO || kind > MOLGW_MATVEC_INT) return MOLGW_E_ARG;
+  c->panel_matvec = kind;
+  for (Lane& l : c->lanes) l.ex.panel_matvec = kind;
+  ++c->gen;   // a captured graph holds the old choice in its launches
   return MOLGW_OK;
 }
 

@@ -59,6 +59,7 @@ struct Exec {
                            // concurrent lanes split the device between them
   long long grid_spins = kGridSpinLimit;  // polls of a grid barrier before MOLGW_E_TIMEOUT
   int bisect_rounds = kBisectRounds;      // float64 bisection rounds before MOLGW_E_NOCONV
+  int panel_matvec = MOLGW_MATVEC_AUTO;   // mat-vec of the panel kernel with an image arena
 };
 
 // Scoped marker: records a start/stop event pair around the kernels launched in
@@ -156,21 +157,20 @@ struct EigWork {
   void* fx = nullptr;
   long long fx_rows = 0;       // matrices up to fx_rows (n)
   long long fx_cols = 0;       // back-transformations of up to fx_cols columns
-  // with MOLGW_FLAG_EIG_TC on the context's own stream: 7-digit images of the lower
-  // 64 x 64 tiles of the trailing matrix (eig_sv_bytes(sv_n) bytes) for the panel
-  // kernel's tensor-core mat-vec, their scales, and the panel's column-maximum
-  // partials; else nullptr
+  // with MOLGW_FLAG_EIG_TC on the context's own stream: images of the lower 64 x 64
+  // tiles of the trailing matrix (eig_sv_bytes(sv_n) bytes) for the panel kernel's
+  // fixed-point mat-vec (7-digit BF16 for the tensor cores or 53-bit integers), their
+  // scales, the panel's column-maximum partials and the row blocks' scales; else
+  // nullptr
   void* sv = nullptr;
   long long sv_n = 0;
 };
-// Bytes of the tensor-core mat-vec arena for matrices up to n: one 57,344-byte image
-// (7 digit planes of 64 x 64 BF16) and one scale per lower tile, then ceil(n/32) + 2
-// column-maximum partials.
+// Bytes of the fixed-point mat-vec arena for matrices up to n: one 57,344-byte image
+// (7 digit planes of 64 x 64 BF16; the integer image takes 32,768) and one scale (or
+// exponent) per lower tile, then ceil(n/32) + 2 column-maximum partials, then the
+// largest |a| of the integer image.
 constexpr long long kSvTileBytes = 7LL * 64 * 64 * 2;
 inline long long eig_sv_tiles(long long n) { const long long b = (n + 63) / 64; return b * (b + 1) / 2; }
-inline size_t eig_sv_bytes(long long n) {
-  return (size_t)(eig_sv_tiles(n) * (kSvTileBytes + 8) + ((n + 31) / 32 + 2) * 8 + 256);
-}
 // Workspace sizes in doubles for matrices up to n and back-transformations of
 // up to ncols (>= 64) columns at a time.
 constexpr int kMaxPanelGrid = 320;   // CTAs of the tridiagonalisation panel kernel, at most
@@ -181,6 +181,9 @@ constexpr size_t eig_part_doubles(size_t n) {
 }
 constexpr size_t eig_gk_doubles(size_t n, size_t ncols) {
   return (16 * 64 * ncols > 8 * (n / 64 + 1) * 64 * 64) ? 16 * 64 * ncols : 8 * (n / 64 + 1) * 64 * 64;
+}
+inline size_t eig_sv_bytes(long long n) {
+  return (size_t)(eig_sv_tiles(n) * (kSvTileBytes + 8) + ((n + 31) / 32 + 2) * 8 + 8 + 256);
 }
 constexpr size_t eig_work_doubles(size_t n, size_t ncols) {
   return 4 * n + n * 64 + eig_part_doubles(n) + 64 + n * n + 2 * (n / 64 + 1) * 64 * 64 + 2 * 64 * ncols +

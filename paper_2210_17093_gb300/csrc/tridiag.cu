@@ -71,9 +71,25 @@ struct PanelParams {
   const uint8_t* sv_img;
   const double* sv_scl;
   double* sv_mx;
+  // integer mat-vec (k_panel<kPanelInt>): the trailing region's lower tiles as 53-bit
+  // fixed point (tile index relative to block k0 / 64) and each row block's exponent
+  const long long* ix_img;
+  const int* ix_texp;       // e_T per tile (as ix_img)
+  const unsigned long long* ix_gmax;   // bit pattern of the largest |a| of all tiles
 };
 
 __device__ __forceinline__ double ldg_cg(const double* p) { return __ldcg(p); }
+
+// (R, J) of lower tile f counted row by row from block rbp: R - rbp = the largest a with
+// a(a+1)/2 <= f (a float32 square root as the estimate, exact integer fix-ups)
+__device__ __forceinline__ void tile_of(long long f, int rbp, int& R, int& J) {
+  long long a = (long long)((sqrtf(8.0f * (float)f + 1.0f) - 1.0f) * 0.5f);
+  if (a < 0) a = 0;
+  while (a > 0 && a * (a + 1) / 2 > f) --a;
+  while ((a + 1) * (a + 2) / 2 <= f) ++a;
+  R = rbp + (int)a;
+  J = rbp + (int)(f - a * (a + 1) / 2);
+}
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
   unsigned int v;
@@ -115,85 +131,220 @@ __device__ bool grid_sync(GridBar* bar, int* status, unsigned int& epoch, long l
   return ok != 0;
 }
 
-__device__ __forceinline__ double blk_reduce_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+// Reductions of the panel kernel.  On GB300 a float64 warp instruction occupies the SM's
+// float64 pipe for the same ~19 cycles however many of its lanes are active, so a sum
+// over the CTA is formed by one warp: every thread's value goes to shared memory
+// (sh[kShBuf + t], RT doubles), warp 0 adds eight of them per lane and finishes with five
+// shuffle steps.  sh[0..39] hold scalars; every helper starts with a __syncthreads (which
+// also publishes the caller's earlier shared-memory writes) and returns after another.
+constexpr int kShBuf = 40;
+
+// Sum of the values v of all threads in a fixed order; valid in every thread.
+__device__ double cta_sum(double v, double* sh) {
+  const int t = threadIdx.x;
   __syncthreads();
-  if (lane == 0) sh[wid] = v;
+  sh[kShBuf + t] = v;
   __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x < 32) {
-    s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+  if (t < 32) {
+    double s = sh[kShBuf + t];
+#pragma unroll
+    for (int k = 1; k < RT / 32; ++k) s += sh[kShBuf + t + 32 * k];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (t == 0) sh[32] = s;
   }
-  return s;  // valid in thread 0
+  __syncthreads();
+  return sh[32];
 }
 
-// Sum over a chunk's rows of values held by the lanes with (thread & 7) == 0 (four per
-// warp, the rest zero): two shuffle steps per warp, eight warp sums in thread 0, where
-// the result is valid.  Two __syncthreads, like blk_reduce_sum.
+// Sum over a chunk's rows of values held by the lanes with (thread & 7) == 0 (the rest
+// zero): the 32 row values go to shared memory and warp 0 adds them.  Valid in thread 0;
+// its first __syncthreads publishes the caller's shared-memory writes.
 __device__ __forceinline__ double chunk_rows_sum(double v, double* sh) {
-  v += __shfl_xor_sync(0xffffffffu, v, 8);
-  v += __shfl_xor_sync(0xffffffffu, v, 16);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int t = threadIdx.x;
   __syncthreads();
-  if (lane == 0) sh[wid] = v;
+  if ((t & 7) == 0) sh[kShBuf + (t >> 3)] = v;
   __syncthreads();
   double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+  if (t < 32) {
+    s = sh[kShBuf + t];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
   return s;
 }
 
 // Sum of `cnt` partials, the same value and order in every thread of every CTA.
 __device__ double sum_partials(const double* p, int cnt, double* sh) {
-  double v = 0.0;
-  for (int k = threadIdx.x; k < cnt; k += blockDim.x) v += ldg_cg(p + k);
-  double s = blk_reduce_sum(v, sh);
-  __syncthreads();
-  if (threadIdx.x == 0) sh[32] = s;
-  __syncthreads();
-  return sh[32];
+  const int t = threadIdx.x;
+  double v = (t < cnt) ? ldg_cg(p + t) : 0.0;
+  for (int k = t + RT; k < cnt; k += RT) v += ldg_cg(p + k);
+  return cta_sum(v, sh);
 }
 
 struct Refl { double tau, beta, scale, alpha; };
 
-// Largest of `cnt` partials, the same value in every thread of every CTA.
-__device__ double max_partials(const double* p, int cnt, double* sh) {
-  double v = 0.0;
-  for (int k = threadIdx.x; k < cnt; k += blockDim.x) v = fmax(v, ldg_cg(p + k));
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
-    sh[33] = m;
+// Sum of `cnt` partials ps[] and the largest of the non-negative pm[] (compared as
+// 64-bit integers: the bit patterns of non-negative doubles are ordered like their
+// values), both the same in every thread of every CTA.
+__device__ double sum_max_partials(const double* ps, const double* pm, int cnt, double* sh, double& mx) {
+  const int t = threadIdx.x;
+  double v = (t < cnt) ? ldg_cg(ps + t) : 0.0;
+  long long m = (t < cnt) ? __double_as_longlong(ldg_cg(pm + t)) : 0;
+  for (int k = t + RT; k < cnt; k += RT) {
+    v += ldg_cg(ps + k);
+    m = max(m, __double_as_longlong(ldg_cg(pm + k)));
   }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   __syncthreads();
-  return sh[33];
+  if ((t & 31) == 0) reinterpret_cast<long long*>(sh)[16 + (t >> 5)] = m;
+  const double s = cta_sum(v, sh);   // its __syncthreads publish the warp maxima
+  long long mm = 0;
+#pragma unroll
+  for (int w = 0; w < RT / 32; ++w) mm = max(mm, reinterpret_cast<long long*>(sh)[16 + w]);
+  mx = __longlong_as_double(mm);
+  return s;
 }
 
-__device__ Refl householder(const PanelParams& p, int i, double* sh) {
-  const int n_ss = ceil_div_d(p.n - i, RC);
-  const double sumsq = sum_partials(p.p_ss, n_ss, sh);
-  const double alpha = ldg_cg(p.scal + 0);
-  Refl h{0.0, alpha, 0.0, alpha};
-  if (sumsq > 0.0) {
-    const double nrm = sqrt(alpha * alpha + sumsq);
-    h.beta = (alpha >= 0.0) ? -nrm : nrm;
-    h.tau = (h.beta - alpha) / h.beta;
-    h.scale = 1.0 / (alpha - h.beta);
+// The reflector of column i from P1's partial sums of squares (LAPACK dlarfg
+// convention), computed by thread 0 and shared; with xmax, also the largest |x_r| from
+// P1's chunk maxima (the fixed-point mat-vecs' scale of x).
+__device__ Refl householder(const PanelParams& p, int n_ss, double* sh, double* xmax = nullptr) {
+  const double sumsq = xmax ? sum_max_partials(p.p_ss, p.sv_mx, n_ss, sh, *xmax) : sum_partials(p.p_ss, n_ss, sh);
+  if (threadIdx.x == 0) {
+    const double alpha = ldg_cg(p.scal + 0);
+    Refl h{0.0, alpha, 0.0, alpha};
+    if (sumsq > 0.0) {
+      const double nrm = sqrt(alpha * alpha + sumsq);
+      h.beta = (alpha >= 0.0) ? -nrm : nrm;
+      h.tau = (h.beta - alpha) / h.beta;
+      h.scale = 1.0 / (alpha - h.beta);
+    }
+    sh[34] = h.tau;
+    sh[35] = h.beta;
+    sh[36] = h.scale;
+    sh[37] = h.alpha;
   }
-  return h;
+  __syncthreads();
+  return Refl{sh[34], sh[35], sh[36], sh[37]};
 }
 
 // v_i[r] for r >= i+1 during P2/P3 (column i still holds the unscaled x).
 __device__ __forceinline__ double vval(const PanelParams& p, int i, int r, double scale) {
   if (r == i + 1) return 1.0;
   return ldg_cg(p.A + r + (long long)i * p.n) * scale;
+}
+
+// ---------------------------------------------------------------------------
+// Integer symmetric mat-vec (k_panel<kPanelInt>, MOLGW_FLAG_EIG_TC).  Before a panel,
+// every stored 64 x 64 tile T of the trailing matrix is written as 53-bit fixed point on
+// its own grid: a = m 2^(e_T - 53), m = rint(a 2^(53 - e_T)) with max |a| over the tile
+// below 2^(e_T), so |m| <= 2^53, stored as m = h 2^27 + l (|h| <= 2^26,
+// -2^26 <= l < 2^26) in one 64-bit word (l low, h high), tile-local column-major
+// (element (r, c) at c * 64 + r).  In P2 x is put on one grid too, x = m_x 2^(e_x - 53)
+// (|x| < 2^(e_x)), split the same way, and every product is
+//   a x = [h h_x 2^54 + (h l_x + l h_x) 2^27 + l l_x] 2^(e_T + e_x - 106),
+// formed with 32 x 32 -> 64-bit integer multiply-adds, exact; the last term (below
+// 2^-54 of the grid's unit) is left out and the middle sum's 27 low bits are dropped
+// once per tile and row, giving 64-bit tile sums in units of 2^(e_T + e_x - 52).  Those
+// are moved to the common grid 2^(e_g - 56 + e_x - 52) (e_g: the largest tile exponent)
+// by left shifts of at most 56 places, exact, and added in 128 bits (below 2^125 for
+// up to 1024 tiles per row), then rounded to float64 once per row; tiles more than
+// 2^56 below the largest are shifted right instead.  Accuracy: every value is
+// represented to 2^-54 of its tile's largest and x to 2^-54 of its largest, i.e.
+// float64 accuracy in the normwise sense, not float64 arithmetic.  Throughput: a GB300 SM issues ~62 such multiply-adds per clock against
+// 1.7 float64 FMAs, so the mat-vec is bound by reading the image (8 bytes per element,
+// as float64) instead of the float64 pipe.
+constexpr int kPanelF64 = 0, kPanelTc = 1, kPanelInt = 2;
+constexpr long long kIxTileBytes = 64LL * 64 * 8;
+static_assert(kIxTileBytes <= kSvTileBytes, "the integer image fits where the tensor-core image goes");
+
+// rint(x 2^p) from the bit pattern (integer instructions only; the scaling by a power
+// of two is exact, the rounding to nearest with ties to even); |x| 2^p must stay below
+// 2^62.  Zero and subnormal x give 0.
+__device__ __forceinline__ long long fixed_round(double x, int p) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  if (ex == 0) return 0;
+  const unsigned long long m = (bits & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+  const int sh = ex - 1075 + p;                          // x = m 2^(ex - 1075)
+  unsigned long long t;
+  if (sh >= 0) {
+    t = m << sh;
+  } else if (sh > -64) {
+    const int r = -sh;
+    t = (r < 64) ? (m >> r) : 0ULL;
+    const unsigned long long rem = m & ((1ULL << r) - 1), half = 1ULL << (r - 1);
+    if (rem > half || (rem == half && (t & 1ULL))) ++t;
+  } else {
+    t = 0;
+  }
+  return (bits >> 63) ? -(long long)t : (long long)t;
+}
+// c + a b with a 32 x 32 -> 64-bit product (one widening integer multiply-add)
+__device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
+  long long d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+// m = h 2^27 + l with l in [-2^26, 2^26)
+__device__ __forceinline__ void split27(long long m, int& h, int& l) {
+  h = (int)((m + (1LL << 26)) >> 27);
+  l = (int)(m - ((long long)h << 27));
+}
+// 2^e as a float64 (e within the normal range; others through ldexp)
+__device__ __forceinline__ double pow2i(int e) {
+  return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
+}
+// the exponent e with |v| < 2^e for the largest |v| of a group (0 for an all-zero group)
+__device__ __forceinline__ int grid_exp(double vmax) {
+  int e = 0;
+  if (vmax > 0.0) frexp(vmax, &e);
+  return e;
+}
+
+// The integer image of every stored tile (R, J), rbp <= J <= R, one CTA per tile: the
+// tile's largest |a| (a maximum of bit patterns, ordered like the values: integer
+// instructions), its exponent texp[f] = e_T, the elements on that grid, and an atomic
+// maximum of the bit patterns into *gmax (zero before the launch).
+__global__ void __launch_bounds__(256) k_ix_image(const double* __restrict__ A, int n, int rbp, long long* img,
+                                                  int* texp, unsigned long long* gmax) {
+  __shared__ unsigned long long red[8];
+  int R, J;
+  tile_of(blockIdx.x, rbp, R, J);
+  const int t = threadIdx.x, r = t & 63, c0 = t >> 6;
+  const int gr = R * TB + r;
+  double v[16];
+  unsigned long long mx = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int gc = J * TB + c0 + 4 * k;
+    v[k] = (gr < n && gc < n) ? A[gr + (long long)gc * n] : 0.0;
+    mx = max(mx, (unsigned long long)__double_as_longlong(v[k]) & 0x7FFFFFFFFFFFFFFFULL);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((t & 31) == 0) red[t >> 5] = mx;
+  __syncthreads();
+  unsigned long long m = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) m = max(m, red[w]);
+  const int e = grid_exp(__longlong_as_double((long long)m));
+  long long* base = img + (long long)blockIdx.x * (TB * TB);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    int h, l;
+    split27(fixed_round(v[k], 53 - e), h, l);
+    base[(c0 + 4 * k) * TB + r] = (long long)(((unsigned long long)(unsigned int)h << 32) | (unsigned int)l);
+  }
+  if (t == 0) {
+    texp[blockIdx.x] = e;
+    atomicMax(gmax, m);
+  }
+}
+
+// 128-bit integer to float64 (two roundings, relative error below 2^-52)
+__device__ __forceinline__ double i128_to_f64(__int128 v) {
+  const long long hi = (long long)(v >> 64);
+  const unsigned long long lo = (unsigned long long)v;
+  return fma((double)hi, 0x1p64, (double)lo);
 }
 
 // ---------------------------------------------------------------------------
@@ -317,10 +468,8 @@ __global__ void __launch_bounds__(256) k_sv_digits(const double* __restrict__ A,
                                                    double* scl) {
   __shared__ double red[8];
   const long long f = blockIdx.x;
-  long long a = (long long)((sqrt(8.0 * (double)f + 1.0) - 1.0) * 0.5);
-  while (a * (a + 1) / 2 > f) --a;
-  while ((a + 1) * (a + 2) / 2 <= f) ++a;
-  const int R = rbp + (int)a, J = rbp + (int)(f - a * (a + 1) / 2);
+  int R, J;
+  tile_of(f, rbp, R, J);
   const int t = threadIdx.x, r = t & 63, c0 = t >> 6;
   const int gr = R * TB + r;
   double v[16];
@@ -354,15 +503,19 @@ __global__ void __launch_bounds__(256) k_sv_digits(const double* __restrict__ A,
   if (t == 0) scl[f] = u;
 }
 
-template <bool TC>
-__global__ void __launch_bounds__(RT, TC ? 1 : 2) k_panel(PanelParams p) {
+template <int MODE>
+__global__ void __launch_bounds__(RT, MODE == kPanelTc ? 1 : 2) k_panel(PanelParams p) {
+  // mat-vec of P2: float64 register tiles, tensor cores from 7-digit images, or integer
+  // multiply-adds from 53-bit images
+  constexpr bool TC = MODE == kPanelTc;
+  constexpr bool IX = MODE == kPanelInt;
   // the thread that arrives at the grid barriers: with the tensor-core mat-vec one of an
   // idle warp (warp 3), not the bulk-copy producer, whose fences would also wait for its
   // copies' bookkeeping
   constexpr int kLeader = TC ? 96 : 0;
-  __shared__ double sh[40];
+  __shared__ double sh[kShBuf + RT];
   __shared__ double Wi[NBP], Vi[NBP], vtv[NBP], wtv[NBP];
-  __shared__ double tile_s[TC ? 1 : TB * (TB + 1)];   // P1 scratch; P2 row-block sums [8][64]
+  __shared__ __align__(16) double tile_s[TC ? 1 : TB * (TB + 1)];   // P1 scratch; P2 row-block sums [8][64]
   // tensor-core mat-vec: a ring of stages (tile image, x_J and x_R digits) in dynamic
   // shared memory, whose first stage doubles as P1's scratch (the phases never overlap)
   extern __shared__ uint8_t sv_raw[];
@@ -417,6 +570,13 @@ __global__ void __launch_bounds__(RT, TC ? 1 : 2) k_panel(PanelParams p) {
   }
   long long sv_it = 0;       // tiles this CTA has taken through the tensor-core mat-vec
   bool aborted = false;
+  // integer mat-vec: the common grid of the row sums, 2^(ix_ref - 52) (times 2^(e_x))
+  int ix_ref = 0;
+  double ix_unit = 0.0;
+  if constexpr (IX) {
+    ix_ref = grid_exp(__longlong_as_double((long long)*p.ix_gmax)) - 56;
+    ix_unit = pow2i(ix_ref - 52);
+  }
 
   for (int j = 0; j < p.nbp; ++j) {
     const int i = k0 + j;
@@ -442,9 +602,10 @@ __global__ void __launch_bounds__(RT, TC ? 1 : 2) k_panel(PanelParams p) {
     __syncthreads();
     for (int ch = L; ch < n1; ch += gridDim.x) {
       const int r = i + ch * RC + rl;
+      const bool act = r < n;
       double upd = 0.0, wcorr = 0.0;
       double vs[NBP / 8], ws[NBP / 8];
-      if (r < n && j > 0)
+      if (act && j > 0)
         wcorr = ldg_cg(p.Wp + r + (long long)(j - 1) * ld) + alpha_w * ldg_cg(A + r + (long long)(i - 1) * ld);
       // k < ceil(j / 8) (the same in every lane): groups with no column below j cost
       // no float64 instructions (the pipe spends one issue per warp instruction, however
@@ -459,7 +620,7 @@ __global__ void __launch_bounds__(RT, TC ? 1 : 2) k_panel(PanelParams p) {
       for (int k = 0; k < NBP / 8; ++k) {
         if (k >= kj) break;
         const int c = q8 + 8 * k;
-        if (r < n && c < j) {
+        if (act && c < j) {
           vs[k] = ldg_cg(A + r + (long long)(k0 + c) * ld);
           ws[k] = (c == j - 1) ? wcorr : ldg_cg(p.Wp + r + (long long)c * ld);
           upd += vs[k] * Wi[c] + ws[k] * Vi[c];
@@ -469,9 +630,9 @@ __global__ void __launch_bounds__(RT, TC ? 1 : 2) k_panel(PanelParams p) {
       upd += __shfl_xor_sync(0xffffffffu, upd, 2);
       upd += __shfl_xor_sync(0xffffffffu, upd, 4);
       double a = 0.0;
-      if (r < n) a = ldg_cg(A + r + (long long)i * ld) - upd;
+      if (act) a = ldg_cg(A + r + (long long)i * ld) - upd;
       double sq = 0.0;
-      if (r < n && q8 == 0) {
+      if (act && q8 == 0) {
         if (j > 0) p.Wp[r + (long long)(j - 1) * ld] = wcorr;
         A[r + (long long)i * ld] = a;
         if (r == i) p.d[i] = a;
@@ -482,7 +643,7 @@ __global__ void __launch_bounds__(RT, TC ? 1 : 2) k_panel(PanelParams p) {
       // memory (row stride 2 NBP + 1) with a(r) beside them, and two threads per column
       // sum sixteen rows each with fused multiply-adds (a third of the float64
       // instructions of a shuffle reduction, on a pipe that P1 otherwise saturates)
-      const double aa = (r < n && r >= i + 2) ? a : 0.0;
+      const double aa = (act && r >= i + 2) ? a : 0.0;
       double* vw = tile;                         // [RC][2 NBP + 1]
       double* av = tile + RC * (2 * NBP + 1);    // [RC]
 #pragma unroll
@@ -508,9 +669,9 @@ __global__ void __launch_bounds__(RT, TC ? 1 : 2) k_panel(PanelParams p) {
         if (c < 2 * j && hf == 0) p.p_vw[(long long)ch * (2 * NBP) + c] = d2;
       }
       __syncthreads();
-      if constexpr (TC) {
+      if constexpr (TC || IX) {
         // largest |x_r| over the chunk's rows r >= i+1 (the scale of x's digits in P2)
-        double mx = (r < n && r >= i + 1 && q8 == 0) ? fabs(a) : 0.0;
+        double mx = (act && r >= i + 1 && q8 == 0) ? fabs(a) : 0.0;
         mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
         mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
         if ((t & 31) == 0) sh[t >> 5] = mx;
@@ -556,33 +717,52 @@ __global__ void __launch_bounds__(RT, TC ? 1 : 2) k_panel(PanelParams p) {
     // the reflector's norm is summed.
     int R0 = rb0, J0 = rb0;
     auto load_tile = [&](int R, int J) {
+      if constexpr (IX) {
+        // the same elements from the integer image (bit patterns held in float64 registers)
+        const int rbi = k0 / TB;
+        const long long fp = (long long)(R - rbi) * (R - rbi + 1) / 2 + (J - rbi);
+        const double* tb = reinterpret_cast<const double*>(p.ix_img + fp * (TB * TB));
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int gc = J * TB + cq0 + c;
+        for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int gr = R * TB + rq + 16 * k;
-          nxt[4 * c + k] = (gr < n && gc < n) ? __ldca(A + gr + (long long)gc * ld) : 0.0;
+          for (int k = 0; k < 4; ++k) nxt[4 * c + k] = __ldca(tb + (cq0 + c) * TB + rq + 16 * k);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int gc = J * TB + cq0 + c;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int gr = R * TB + rq + 16 * k;
+            nxt[4 * c + k] = (gr < n && gc < n) ? __ldca(A + gr + (long long)gc * ld) : 0.0;
+          }
         }
       }
     };
     if (f0 < f1) {
-      long long a = 0;
-      while ((a + 1) * (a + 2) / 2 <= f0) ++a;
-      R0 = rb0 + (int)a;
-      J0 = rb0 + (int)(f0 - a * (a + 1) / 2);
+      tile_of(f0, rb0, R0, J0);
       if constexpr (!TC) load_tile(R0, J0);
     }
-    const Refl h = householder(p, i, sh);
     double xmax = 0.0;
-    if constexpr (TC) xmax = max_partials(p.sv_mx, ceil_div_d(n - i, RC), sh);
+    const Refl h = householder(p, n1, sh, (TC || IX) ? &xmax : nullptr);
+    const int ixe = IX ? grid_exp(xmax) : 0;   // integer mat-vec: |x| < 2^ixe
     {
       // V^T v = V(i+1,:) + scale * (sum over the P1 chunks), the same for W^T v:
-      // the first CTAs finish these 2j sums (one warp per value) for P3
-      const int c = blockIdx.x * (RT / 32) + wq;
+      // these 2j sums are finished for P3 by one warp each, spread over the CTAs (warp 0
+      // of CTA c first) so that no SM's float64 pipe takes more than one or two of them
+      const int c = blockIdx.x + gridDim.x * wq;
       if (c < 2 * j) {
+        // eight loads in flight per lane, added in ascending chunk order
         double s2 = 0.0;
-        for (int ch = lane; ch < n1; ch += 32) s2 += ldg_cg(p.p_vw + (long long)ch * (2 * NBP) + c);
+        for (int ch0 = lane; ch0 < n1; ch0 += 32 * 8) {
+          double v8[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int ch = ch0 + 32 * u;
+            v8[u] = (ch < n1) ? ldg_cg(p.p_vw + (long long)ch * (2 * NBP) + c) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) s2 += v8[u];
+        }
         for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
         if (lane == 0) {
           const double row1 = (c < j) ? ldg_cg(A + lo + (long long)(k0 + c) * ld) : ldg_cg(p.Wp + lo + (long long)(c - j) * ld);
@@ -845,6 +1025,136 @@ __global__ void __launch_bounds__(RT, TC ? 1 : 2) k_panel(PanelParams p) {
         }
       }
       sv_it += nt;
+    } else if constexpr (IX) {
+      if (f0 < f1) {
+        const int rbi = k0 / TB;
+        // x on its grid, m_x = rint(x 2^(53 - e_x)) = h 2^27 + l, each value converted by
+        // one lane and handed to the lanes that use it by shuffles (x written by P1: read
+        // through L2; the next tile's values are loaded with the tile)
+        auto xv = [&](int r) { return (r >= lo && r < n) ? ldg_cg(A + r + (long long)i * ld) : 0.0; };
+        auto xdig = [&](double v, int& h, int& l) { split27(fixed_round(v, 53 - ixe), h, l); };
+        // y_R partials of the thread's rows on the common grid, 128-bit
+        __int128 acc[4] = {0, 0, 0, 0};
+        // x_R: lane converts rows lane and lane + 32 of the block, thread row rq + 16 k
+        // comes from lane (rq + 16 k) mod 32
+        int xrh[4], xrl[4];
+        auto load_xr = [&](int R) {
+          int h0, l0, h1, l1;
+          xdig(xv(R * TB + lane), h0, l0);
+          xdig(xv(R * TB + lane + 32), h1, l1);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int src = (rq + 16 * k) & 31;
+            xrh[k] = __shfl_sync(0xffffffffu, k < 2 ? h0 : h1, src);
+            xrl[k] = __shfl_sync(0xffffffffu, k < 2 ? l0 : l1, src);
+          }
+        };
+        int R = R0, J = J0;
+        load_xr(R);
+        // x_J: lane converts column 8 wq + (lane & 7); thread column cq0 + c comes from
+        // lane 4 (lane >> 4) + c
+        double xj_next = xv(J * TB + 8 * wq + (lane & 7));
+        for (long long f = f0; f < f1; ++f) {
+          int Rn = R, Jn = J + 1;             // next tile
+          if (Jn > Rn) { ++Rn; Jn = rb0; }
+          int ah[16], al[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const long long w = __double_as_longlong(nxt[e]);
+            al[e] = (int)(unsigned int)(unsigned long long)w;
+            ah[e] = (int)(w >> 32);
+          }
+          int xch[4], xcl[4];
+          {
+            int h, l;
+            xdig(xj_next, h, l);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              xch[c] = __shfl_sync(0xffffffffu, h, 4 * (lane >> 4) + c);
+              xcl[c] = __shfl_sync(0xffffffffu, l, 4 * (lane >> 4) + c);
+            }
+          }
+          if (f + 1 < f1) {
+            load_tile(Rn, Jn);                // in flight while this tile is used
+            xj_next = xv(Jn * TB + 8 * wq + (lane & 7));
+          }
+          const int sft = __ldg(p.ix_texp + ((long long)(R - rbi) * (R - rbi + 1) / 2 + (J - rbi))) - ix_ref;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            long long H = 0, M = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              H = mad_wide(ah[4 * c + k], xch[c], H);
+              M = mad_wide(ah[4 * c + k], xcl[c], M);
+              M = mad_wide(al[4 * c + k], xch[c], M);
+            }
+            const long long T = H + (M >> 27);
+            acc[k] += (sft >= 0) ? ((__int128)T << sft) : (__int128)(T >> min(-sft, 63));
+          }
+          if (J < R) {
+            long long q[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              long long H = 0, M = 0;
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                H = mad_wide(ah[4 * c + k], xrh[k], H);
+                M = mad_wide(ah[4 * c + k], xrl[k], M);
+                M = mad_wide(al[4 * c + k], xrh[k], M);
+              }
+              q[c] = H + (M >> 27);
+            }
+            // sums over the half-warp (the tile's 64 rows) scattering the four columns as
+            // in the float64 path, in 64-bit integers (at most 2^59 in magnitude)
+            const bool b3 = (rq & 8) != 0, b2 = (rq & 4) != 0;
+            const long long k0v = b3 ? q[2] : q[0], k1v = b3 ? q[3] : q[1];
+            const long long s0v = b3 ? q[0] : q[2], s1v = b3 ? q[1] : q[3];
+            const long long h0 = k0v + __shfl_xor_sync(0xffffffffu, s0v, 8);
+            const long long h1 = k1v + __shfl_xor_sync(0xffffffffu, s1v, 8);
+            long long v = (b2 ? h1 : h0) + __shfl_xor_sync(0xffffffffu, b2 ? h0 : h1, 4);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            if ((rq & 3) == 0) {
+              const long long ft = (long long)(R - rb0) * (R - rb0 + 1) / 2 + (J - rb0);
+              reinterpret_cast<long long*>(p.p_t)[ft * TB + cq0 + 2 * (b3 ? 1 : 0) + (b2 ? 1 : 0)] = v;
+            }
+          }
+          if (f + 1 == f1 || J == R) {
+            // end of this CTA's part of row block R: 128-bit sums over the 16 threads that
+            // hold each row (the two half-warps, then the eight warps through shared memory),
+            // rounded once to float64 on the row block's grid
+            __int128* red = reinterpret_cast<__int128*>(tile);   // [8][64]
+            __int128 a2[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              a2[k] = acc[k];
+              const long long lo64 = (long long)(unsigned long long)a2[k];
+              const long long hi64 = (long long)(a2[k] >> 64);
+              const unsigned long long olo = (unsigned long long)__shfl_xor_sync(0xffffffffu, lo64, 16);
+              const long long ohi = __shfl_xor_sync(0xffffffffu, hi64, 16);
+              a2[k] += ((__int128)ohi << 64) | (__int128)olo;
+            }
+            __syncthreads();
+            if (lane < 16) {
+#pragma unroll
+              for (int k = 0; k < 4; ++k) red[wq * TB + rq + 16 * k] = a2[k];
+            }
+            __syncthreads();
+            if (t < TB) {
+              __int128 y = red[t];
+#pragma unroll
+              for (int w2 = 1; w2 < RT / 32; ++w2) y += red[w2 * TB + t];
+              const int r = R * TB + t;
+              if (r < n) p.p_y[(long long)blockIdx.x * n + r] = i128_to_f64(y) * ix_unit * pow2i(ixe);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[k] = 0;
+            if (f + 1 < f1 && Rn != R) load_xr(Rn);
+          }
+          R = Rn;
+          J = Jn;
+        }
+      }
     } else {
       if (f0 < f1) {
         // x entries of rows >= lo (written by P1 of this column: read through L2)
@@ -933,8 +1243,9 @@ __global__ void __launch_bounds__(RT, TC ? 1 : 2) k_panel(PanelParams p) {
     __syncthreads();
     for (int ch = L; ch < n3; ch += gridDim.x) {
       const int r = lo + ch * RC + rl;
+      const bool act = r < n;
       double y = 0.0;
-      if (r < n) {
+      if (act) {
         // (A22 x)_r = (direct partials of the CTAs whose ranges cover row block R)
         //           + (transposed partials of the tiles (R', R) below it);
         // y_r = scale (A22 x)_r + (1 - scale alpha) A(r, i+1) - W(r,:) V^T v - V(r,:) W^T v
@@ -943,6 +1254,9 @@ __global__ void __launch_bounds__(RT, TC ? 1 : 2) k_panel(PanelParams p) {
         const long long fa = (long long)a * (a + 1) / 2, fb = fa + a;
         const int ca = (int)(((fa + 1) * gridDim.x - 1) / T), cb = (int)(((fb + 1) * gridDim.x - 1) / T);
         double yx = 0.0;
+        // integer mat-vec: the transposed partials (units 2^(e_T - 52 + e_x), below 2^59)
+        // moved to the common grid by left shifts (exact) and added in 128 bits
+        __int128 yxi = 0;
         for (int c = ca + q8; c <= cb; c += 8) {
           // CTAs with an empty tile range wrote nothing
           if ((long long)c * T / gridDim.x == (long long)(c + 1) * T / gridDim.x) continue;
@@ -951,8 +1265,17 @@ __global__ void __launch_bounds__(RT, TC ? 1 : 2) k_panel(PanelParams p) {
 #pragma unroll 8
         for (int R2 = Rr + 1 + q8; R2 < nrbt; R2 += 8) {
           const long long ft = (long long)(R2 - rb0) * (R2 - rb0 + 1) / 2 + a;
-          yx += ldg_cg(p.p_t + ft * TB + (r - Rr * TB));
+          if constexpr (IX) {
+            const long long v = __ldcg(reinterpret_cast<const long long*>(p.p_t) + ft * TB + (r - Rr * TB));
+            const int rbi = k0 / TB;
+            const int sft = __ldg(p.ix_texp + ((long long)(R2 - rbi) * (R2 - rbi + 1) / 2 + (Rr - rbi))) - ix_ref;
+            if (sft >= 0) yxi += (__int128)v << sft;
+            else yxi += (__int128)(v >> min(-sft, 63));
+          } else {
+            yx += ldg_cg(p.p_t + ft * TB + (r - Rr * TB));
+          }
         }
+        if constexpr (IX) yx = fma(i128_to_f64(yxi) * ix_unit, pow2i(ixe), yx);   // powers of two: exact scalings
         if (q8 == 0) y = (1.0 - h.scale * h.alpha) * ldg_cg(A + r + (long long)(i + 1) * ld);
 #pragma unroll 4
         for (int c = q8; c < j; c += 8) {
@@ -965,7 +1288,7 @@ __global__ void __launch_bounds__(RT, TC ? 1 : 2) k_panel(PanelParams p) {
       y += __shfl_xor_sync(0xffffffffu, y, 2);
       y += __shfl_xor_sync(0xffffffffu, y, 4);
       double part = 0.0;
-      if (r < n && q8 == 0) {
+      if (act && q8 == 0) {
         const double w = h.tau * y;
         p.Wp[r + (long long)j * ld] = w;
         if (r == lo) p.scal[3] = w;
@@ -1038,8 +1361,10 @@ __global__ void k_clean(double* A, int n) {
 
 int g_coop_blocks_per_sm = -1;   // the panel grid never exceeds kMaxPanelGrid (p_y has that many rows)
 int g_num_sms = 0;
-int g_sv_blocks_per_sm = -1;     // k_panel<true>: co-resident CTAs per SM with its stage ring (0: unusable)
+int g_sv_blocks_per_sm = -1;     // k_panel<kPanelTc>: co-resident CTAs per SM with its stage ring (0: unusable)
+int g_ix_blocks_per_sm = -1;     // k_panel<kPanelInt>: co-resident CTAs per SM
 constexpr int kSvMinRows = 1024; // trailing matrices from this size use the tensor-core mat-vec
+constexpr int kIxMinRows = 256;  // and the integer one
 
 }  // namespace
 
@@ -1049,15 +1374,20 @@ int tridiag_coop_capacity() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_panel<false>, RT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_panel<kPanelF64>, RT, 0);
     g_coop_blocks_per_sm = std::max(1, std::min(occ, 2));
     g_coop_blocks_per_sm = std::min(g_coop_blocks_per_sm, kMaxPanelGrid / std::max(g_num_sms, 1));
     int occ_sv = 0;
-    if (cudaFuncSetAttribute(k_panel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SV_SMEM) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_sv, k_panel<true>, RT, SV_SMEM) == cudaSuccess)
+    if (cudaFuncSetAttribute(k_panel<kPanelTc>, cudaFuncAttributeMaxDynamicSharedMemorySize, SV_SMEM) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_sv, k_panel<kPanelTc>, RT, SV_SMEM) == cudaSuccess)
       g_sv_blocks_per_sm = std::min(occ_sv, 1);
     else
       g_sv_blocks_per_sm = 0;
+    int occ_ix = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ix, k_panel<kPanelInt>, RT, 0) == cudaSuccess)
+      g_ix_blocks_per_sm = std::min(std::min(occ_ix, 2), kMaxPanelGrid / std::max(g_num_sms, 1));
+    else
+      g_ix_blocks_per_sm = 0;
     cudaGetLastError();
   }
   return g_num_sms * g_coop_blocks_per_sm;
@@ -1087,12 +1417,22 @@ void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
   if (ex.coop_cap > 0) cap = std::max(2 * NBP / (RT / 32), std::min(cap, ex.coop_cap));
   // Tensor-core mat-vec (MOLGW_FLAG_EIG_TC, the context's own stream): tile images and
   // scales in w.sv, then the column-maximum partials.
-  const bool sv_ok = w.sv && ex.coop_cap == 0 && n <= w.sv_n && g_sv_blocks_per_sm > 0;
-  if (sv_ok) {
+  // Integer mat-vec (the same arena: 32 KB images, the tiles' exponents where the tile
+  // scales are, the largest |a| after the column-maximum partials).  Which one
+  // runs: ex.panel_matvec (MOLGW_MATVEC_*), automatic = the integer one.
+  const bool arena = w.sv && ex.coop_cap == 0 && n <= w.sv_n;
+  const int want = ex.panel_matvec;
+  const bool sv_ok = arena && g_sv_blocks_per_sm > 0 && want == MOLGW_MATVEC_TC;
+  const bool ix_ok = arena && g_ix_blocks_per_sm > 0 && (want == MOLGW_MATVEC_AUTO || want == MOLGW_MATVEC_INT);
+
+  if (arena) {
     const long long cap_tiles = eig_sv_tiles(w.sv_n);
     p.sv_img = (const uint8_t*)w.sv;
     p.sv_scl = (const double*)((uint8_t*)w.sv + cap_tiles * kSvTileBytes);
     p.sv_mx = (double*)p.sv_scl + cap_tiles;
+    p.ix_img = (const long long*)w.sv;
+    p.ix_texp = (const int*)p.sv_scl;
+    p.ix_gmax = (const unsigned long long*)(p.sv_mx + (w.sv_n + 31) / 32 + 2);
   }
   const int ncols = n - 1;
   for (int k0 = 0; k0 < ncols; k0 += NBP) {
@@ -1101,7 +1441,20 @@ void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
     p.k0 = k0; p.nbp = nbp; p.k1 = k1;
     const int nrb = nrbt - (k0 + 1) / TB;
     const long long tiles = (long long)nrb * (nrb + 1) / 2;
-    if (sv_ok && n - k0 >= kSvMinRows) {
+    if (ix_ok && n - k0 >= kIxMinRows) {
+      KScope ks(ex, MOLGW_K_TRIDIAG_PANEL, 2);
+      const int rbp = k0 / TB;
+      const long long tiles_p = (long long)(nrbt - rbp) * (nrbt - rbp + 1) / 2;
+      cudaMemsetAsync((void*)p.ix_gmax, 0, sizeof(unsigned long long), ex.st);
+      k_ix_image<<<(unsigned)tiles_p, 256, 0, ex.st>>>(A, n, rbp, (long long*)p.ix_img, (int*)p.ix_texp,
+                                                       (unsigned long long*)p.ix_gmax);
+      const int cap_ix = g_num_sms * g_ix_blocks_per_sm;
+      const int grid = (int)std::max<long long>(2 * NBP / (RT / 32),
+                                                 std::min<long long>(cap_ix, std::max<long long>(tiles, ceil_div(n - k0, RC))));
+      cudaMemsetAsync(p.bar, 0, sizeof(GridBar), ex.st);
+      void* args[] = {&p};
+      cudaLaunchCooperativeKernel((const void*)k_panel<kPanelInt>, dim3(grid), dim3(RT), args, 0, ex.st);
+    } else if (sv_ok && n - k0 >= kSvMinRows) {
       KScope ks(ex, MOLGW_K_TRIDIAG_PANEL, 2);
       const int rbp = k0 / TB;
       const long long tiles_p = (long long)(nrbt - rbp) * (nrbt - rbp + 1) / 2;
@@ -1111,14 +1464,14 @@ void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
                                                  std::min<long long>(cap_sv, std::max<long long>(tiles, ceil_div(n - k0, RC))));
       cudaMemsetAsync(p.bar, 0, sizeof(GridBar), ex.st);
       void* args[] = {&p};
-      cudaLaunchCooperativeKernel((const void*)k_panel<true>, dim3(grid), dim3(RT), args, SV_SMEM, ex.st);
+      cudaLaunchCooperativeKernel((const void*)k_panel<kPanelTc>, dim3(grid), dim3(RT), args, SV_SMEM, ex.st);
     } else {
       const int grid = (int)std::max<long long>(2 * NBP / (RT / 32),
                                                  std::min<long long>(cap, std::max<long long>(tiles, ceil_div(n - k0, RC))));
       KScope ks(ex, MOLGW_K_TRIDIAG_PANEL, 1);
       cudaMemsetAsync(p.bar, 0, sizeof(GridBar), ex.st);
       void* args[] = {&p};
-      cudaLaunchCooperativeKernel((const void*)k_panel<false>, dim3(grid), dim3(RT), args, 0, ex.st);
+      cudaLaunchCooperativeKernel((const void*)k_panel<kPanelF64>, dim3(grid), dim3(RT), args, 0, ex.st);
     }
     const int m = n - k1;
     if (m > 0 && w.fx && m <= w.fx_rows && m >= 128) {

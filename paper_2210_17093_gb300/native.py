@@ -40,7 +40,9 @@ EXPORTS = ["molgw_b200_create", "molgw_b200_set_ri", "molgw_b200_set_orbitals", 
            "molgw_b200_status_string", "molgw_b200_eigh_noalloc", "molgw_b200_graph_replays",
            "molgw_b200_tc_gemm", "molgw_b200_autotune", "molgw_b200_lanes", "molgw_b200_g0w0",
            "molgw_b200_g0w0_window", "molgw_b200_inject_fault", "molgw_b200_set_orbitals_open",
-           "molgw_b200_plan_batch", "molgw_b200_set_wait_limits"]
+           "molgw_b200_plan_batch", "molgw_b200_set_wait_limits", "molgw_b200_set_panel_matvec"]
+# mat-vec of the tridiagonalisation's panel kernel with FLAG_EIG_TC (molgw_matvec)
+MATVEC = {"auto": 0, "fp64": 1, "tc": 2, "int": 3}
 NOALLOC_NMAX = 256
 
 
@@ -83,6 +85,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "molgw_b200_sync": ([vp], ip),
         "molgw_b200_inject_fault": ([vp, ip], ip),
         "molgw_b200_set_wait_limits": ([vp, ctypes.c_longlong, ip], ip),
+        "molgw_b200_set_panel_matvec": ([vp, ip], ip),
         "molgw_b200_fetch": ([vp, ip, ip, dp, sz], ip),
         "molgw_b200_rpa_matrix": ([vp, ip, dp], ip),
         "molgw_b200_eigh": ([vp, ip, dp, dp, dp], ip),
@@ -260,6 +263,11 @@ class Context:
         """Lower the bounds of the device waits (test hook; see molgw_b200_set_wait_limits);
         negative values restore the defaults."""
         _check(self._lib.molgw_b200_set_wait_limits(self._hh(), grid_spins, bisect_rounds), "set_wait_limits")
+
+    def set_panel_matvec(self, kind: str = "auto"):
+        """Choose the panel kernel's mat-vec under FLAG_EIG_TC: "auto", "fp64", "tc" or "int"
+        (see molgw_b200_set_panel_matvec)."""
+        _check(self._lib.molgw_b200_set_panel_matvec(self._hh(), MATVEC[kind]), "set_panel_matvec")
 
     def fetch(self, mol: int, item: str, out):
         n = out.size if isinstance(out, np.ndarray) else out.numel()

@@ -1,10 +1,11 @@
 """Small drivers to profile the library's kernels (e.g. under ncu).
 
-    python -m paper_2210_17093_gb300.prof eigh N [REPS [FLAGS]]
+    python -m paper_2210_17093_gb300.prof eigh N [REPS [FLAGS [MATVEC]]]
         float64 symmetric eigensolve of a random N x N matrix (tridiagonalisation,
         bisection, twisted vectors, full back-transformation) through molgw_b200_eigh
-        (FLAGS: e.g. 32 for MOLGW_FLAG_EIG_TC);
-    python -m paper_2210_17093_gb300.prof qsgw NB NO NA PRECISION [REPS [FLAGS]]
+        (FLAGS: e.g. 32 for MOLGW_FLAG_EIG_TC; MATVEC: the panel kernel's mat-vec
+        under it, auto, fp64, tc or int);
+    python -m paper_2210_17093_gb300.prof qsgw NB NO NA PRECISION [REPS [FLAGS [MATVEC]]]
         qsGW iterations of one synthetic molecule (seed 1) at the given precision
         (FLAGS: extra MOLGW_FLAG_* bits, e.g. 32 for MOLGW_FLAG_EIG_TC);
     python -m paper_2210_17093_gb300.prof batch PRECISION LANES [REPS]
@@ -29,7 +30,7 @@ def _stats(ctx):
     return {k: round(v[1], 2) for k, v in ctx.kernel_stats(reset=True).items() if v[0]}
 
 
-def eigh(n: int, reps: int = 1, flags: int = 0) -> None:
+def eigh(n: int, reps: int = 1, flags: int = 0, matvec: str = "auto") -> None:
     import torch
 
     from . import Context, FLAG_KTIMING
@@ -39,6 +40,7 @@ def eigh(n: int, reps: int = 1, flags: int = 0) -> None:
     w = torch.empty(n, dtype=torch.float64, device="cuda")
     Z = torch.empty(n * n, dtype=torch.float64, device="cuda")
     with Context(stream=torch.cuda.current_stream(), flags=FLAG_KTIMING | flags) as ctx:
+        ctx.set_panel_matvec(matvec)
         for r in range(reps):
             ctx.kernel_stats(reset=True)
             torch.cuda.synchronize()
@@ -145,7 +147,7 @@ def trace(nb: int, no: int, na: int, precision: str, flags: int, seed: int) -> N
 if __name__ == "__main__":
     a = sys.argv[1:]
     if a and a[0] == "eigh":
-        eigh(int(a[1]), int(a[2]) if len(a) > 2 else 1, int(a[3]) if len(a) > 3 else 0)
+        eigh(int(a[1]), int(a[2]) if len(a) > 2 else 1, int(a[3]) if len(a) > 3 else 0, a[4] if len(a) > 4 else "auto")
     elif a and a[0] == "batch":
         batch(a[1], int(a[2]), int(a[3]) if len(a) > 3 else 2)
     elif a and a[0] == "trace":

@@ -192,8 +192,11 @@ def test_bf16x10_tc_ab_within_1meV(nb, no, na, seed):
 
 
 def test_eig_tc_eigh_matches_float64():
-    """MOLGW_FLAG_EIG_TC: the trailing updates on 7 digits; eigenvalues to float64
-    accuracy and orthonormal residual-small eigenvectors."""
+    """MOLGW_FLAG_EIG_TC: the trailing updates on 7 digits and each mat-vec of the panel
+    kernel (float64, tensor cores from 7-digit tile images, integer multiply-adds from
+    53-bit images); eigenvalues to float64 accuracy and orthonormal residual-small
+    eigenvectors.  n = 1100 runs the first panel's mat-vec on the tensor cores (trailing
+    order >= 1024) and the integer one down to trailing order 256."""
     from paper_2210_17093_gb300 import FLAG_EIG_TC
     n = 1100
     rng = np.random.default_rng(11)
@@ -201,12 +204,14 @@ def test_eig_tc_eigh_matches_float64():
     A = (X + X.T) / 2 + np.diag(np.linspace(-5, 5, n))
     ref = np.linalg.eigvalsh(A)
     out = {}
-    for flags in (0, FLAG_EIG_TC):
+    for flags, kind in ((0, None), (FLAG_EIG_TC, "fp64"), (FLAG_EIG_TC, "tc"), (FLAG_EIG_TC, "int")):
         w = np.empty(n)
         Z = np.empty((n, n))
         with lib_context(flags=flags) as ctx:
+            if kind is not None:
+                ctx.set_panel_matvec(kind)
             ctx.eigh(np.ascontiguousarray(A), w, Z)
-        out[flags] = (w, Z)
+        out[(flags, kind)] = (w, Z)
     nrm = np.abs(ref).max()
     for flags, (w, Z) in out.items():
         assert np.max(np.abs(w - ref)) < 1e-12 * nrm, flags
@@ -219,14 +224,16 @@ def test_eig_tc_eigh_matches_float64():
         assert np.all(Zc[big, np.arange(n)] > 0), flags
 
 
+@pytest.mark.parametrize("matvec", ["tc", "int"])
 @pytest.mark.parametrize("prec,tol_ha", [("fp64", 1e-8), ("bf16x10", 1.0 * MEV)])
-def test_eig_tc_pass(prec, tol_ha):
+def test_eig_tc_pass(prec, tol_ha, matvec):
     from paper_2210_17093_gb300 import FLAG_EIG_TC
     nb, no, na = 100, 20, 300
     m = sy.molecule(nb, no, na, 1)
     r = qsgw.qsgw_pass(m["L"], m["eps"], m["C"], no, ETA)
     nov = no * (nb - no)
     with lib_context(precision=prec, eta=ETA, flags=FLAG_EIG_TC) as ctx:
+        ctx.set_panel_matvec(matvec)
         load_mol(ctx, 0, m)
         om = np.empty(nov)
         ctx.rpa(0, om)
