@@ -62,8 +62,8 @@ def measured_peaks() -> dict:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "kind": "fallback"}
 # DRAM bytes the tridiagonalisation panel kernel moves per algorithmic byte (the lower
 # triangle of the trailing matrix once per column), from one ncu capture of the panel of
-# columns 1280..1343 at n = 6400: 4.569 GB measured for 6.629 GB algorithmic.
-PANEL_TRAFFIC_RATIO = 4.569 / 6.629
+# columns 1280..1343 at n = 6400: 4.536 GB measured for 6.629 GB algorithmic.
+PANEL_TRAFFIC_RATIO = 4.536 / 6.629
 
 
 def panel_bytes(n):
@@ -134,8 +134,17 @@ def stage_rooflines(nb, no, na, stages_ms, precision="fp64", flags=0):
 
     bf16 = peaks["bf16_tflops"]
     panel = f["tridiag_panel"] + 2.0 / 3.0 * nb ** 3
-    put("tridiag_panel", panel, "TFLOP/s", FP64_PEAK_TFLOPS, "alu",
-        "2n^3/3 + 128n^2 (symmetric mat-vecs, column updates) for M and H")
+    if eig_tc:
+        # the integer mat-vec reads the 8-byte image of the lower triangle of A22 once per
+        # column (n^3/6 elements) and builds it once per 64-column panel (read float64,
+        # write the image: 16 B per element of the lower triangle, n^3/384 elements)
+        ms = stages_ms.get("tridiag_panel")
+        put("tridiag_panel", 8.0 * n ** 3 / 6.0 + 16.0 * n ** 3 / 384.0, "GB/s", peaks["hbm_gbs"], "hbm",
+            "integer mat-vec: 8-byte tile images of A22's lower triangle read once per column, built once per panel",
+            {"fp64_equivalent_tflops": round(panel / (ms / 1e3) / 1e12, 3) if ms else None})
+    else:
+        put("tridiag_panel", panel, "TFLOP/s", FP64_PEAK_TFLOPS, "alu",
+            "2n^3/3 + 128n^2 (symmetric mat-vecs, column updates) for M and H")
     syr2k = f["tridiag_syr2k"] + 2.0 / 3.0 * nb ** 3
     bt = f["backtransform"] + 2.0 * nb ** 3
     if eig_tc:
@@ -793,11 +802,12 @@ def run_ours(args, wl):
                                         "eigensolvers (c), (f) and the denominators float64")
         mixed_eig = variant(args.mixed, ab | FLAG_EIG_TC,
                             "as 'mixed', and the eigensolvers' SYR2K and back-transformation GEMMs on 7-digit "
-                            "fixed point (float64 accuracy, tensor cores); the panel mat-vecs, bisection and "
-                            "twisted vectors float64")
+                            "fixed point (tensor cores) and the panel mat-vecs on 53-bit integer images (integer "
+                            "multiply-adds), both float64-accurate normwise; bisection and twisted vectors float64")
         fp64_eig = variant("fp64", FLAG_EIG_TC,
                            "float64, with the eigensolvers' SYR2K and back-transformation GEMMs on 7-digit "
-                           "fixed point (float64 accuracy, tensor cores)")
+                           "fixed point (tensor cores) and the panel mat-vecs on 53-bit integer images "
+                           "(float64 accuracy normwise)")
 
     if rank != 0:
         return 0
@@ -822,7 +832,7 @@ def run_ours(args, wl):
             "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
             "traffic": traffic, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
             "traffic_source": "ncu dram__bytes_read+write of one panel launch (n=6400, columns 1280-1343: "
-                              "4.57 GB for 6.63 GB algorithmic, part of the trailing matrix served by L2), "
+                              "4.54 GB for 6.63 GB algorithmic, part of the trailing matrix served by L2), "
                               "that ratio times the algorithmic bytes per launch",
             "launches": nl, "event_ms": kms,
         },
