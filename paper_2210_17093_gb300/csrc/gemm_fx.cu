@@ -1,6 +1,7 @@
 // Fixed-point split GEMM (fx.cuh) on tcgen05 for sm_103a.
 //
-// One 128 x BN output tile and one K group (<= 1024 elements) per CTA; 12 warps:
+// Persistent CTAs (one per SM), each taking 128 x BN output tiles of one K group (<= 1024
+// elements) in turn; 12 warps:
 //   warp 0   TMA producer: the NS BF16 digit planes of a 128-row A box and a
 //            BN-row B box per K block into a shared-memory ring;
 //   warp 1   one thread issues tcgen05.mma (kind::f16, M=128, N=BN, K=16): per K
@@ -125,6 +126,7 @@ struct FxMaps {
 
 struct FxParams {
   int M, N, nkb, kb0;                 // K blocks (of the configuration's KE) in the range, first one
+  int nz;                             // K groups (split-K partials)
   const double* ua;
   int a_ngroups;
   const double* ub;
@@ -141,12 +143,20 @@ template <int NS>
 __global__ void __launch_bounds__(NT, 1) fx_gemm_kernel(const __grid_constant__ FxMaps maps, FxParams p) {
   using C = FxK<NS>;
   constexpr int BN = C::BN, STAGES = C::STAGES;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, gz = blockIdx.z;
-  if (p.lower_only && n0 / 64 > (m0 + BM - 1) / 64) return;   // only strictly-upper 64-blocks
-  const int kbl0 = gz * C::KB_GROUP;                        // first K block of this CTA (range-relative)
-  const int nk = min(p.nkb - kbl0, C::KB_GROUP);
-  const int nchunk = (nk + C::KB_CHUNK - 1) / C::KB_CHUNK;
-  const int group = (p.kb0 + kbl0) / C::KB_GROUP;           // scale group index of the operands
+  // Persistent: CTA b takes tiles b, b + gridDim.x, ... of the (N/BN) x (M/BM) x (K groups)
+  // grid, N fastest (neighbouring CTAs share A's rows).  Every role walks the same tile
+  // sequence; the stage ring and the two TMEM buffers run on counters kept across tiles, so
+  // the epilogue of one tile overlaps the next tile's copies and MMAs.
+  const int ntx = (p.N + BN - 1) / BN, nty = (p.M + BM - 1) / BM;
+  const long long ntiles = (long long)ntx * nty * p.nz;
+  auto tile_at = [&](long long t, int& n0, int& m0, int& gz) {
+    n0 = (int)(t % ntx) * BN;
+    m0 = (int)((t / ntx) % nty) * BM;
+    gz = (int)(t / ((long long)ntx * nty));
+  };
+  // only strictly-upper 64-blocks are skipped
+  auto skip = [&](int n0, int m0) { return p.lower_only && n0 / 64 > (m0 + BM - 1) / 64; };
+  auto k_blocks = [&](int gz) { return min(p.nkb - gz * C::KB_GROUP, C::KB_GROUP); };
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -180,22 +190,30 @@ __global__ void __launch_bounds__(NT, 1) fx_gemm_kernel(const __grid_constant__ 
   volatile int* abort = &abort_flag;
 
   if (warp == 0 && lane == 0) {
-    int issued = 0;
-    for (int i = 0; i < nk; ++i) {
-      const int s = i % STAGES;
-      if (i >= STAGES && !mbar_wait(&empty[s], ((i / STAGES) + 1) & 1, abort)) {
-        fail(p.status, abort);
-        break;
-      }
-      uint8_t* st = smem + s * C::STAGE;
-      mbar_expect_tx(&full[s], C::STAGE);
-      const int x = (p.kb0 + kbl0 + i) * C::KE;
+    int issued = 0;                               // K blocks copied, over all tiles
+    bool ok = true;
+    for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int n0, m0, gz;
+      tile_at(t, n0, m0, gz);
+      if (skip(n0, m0)) continue;
+      const int kbl0 = gz * C::KB_GROUP, nk = k_blocks(gz);
+      for (int i = 0; i < nk; ++i) {
+        const int gi = issued, s = gi % STAGES;
+        if (gi >= STAGES && !mbar_wait(&empty[s], ((gi / STAGES) + 1) & 1, abort)) {
+          fail(p.status, abort);
+          ok = false;
+          break;
+        }
+        uint8_t* st = smem + s * C::STAGE;
+        mbar_expect_tx(&full[s], C::STAGE);
+        const int x = (p.kb0 + kbl0 + i) * C::KE;
 #pragma unroll
-      for (int sl = 0; sl < NS; ++sl) {
-        tma_load_2d(st + sl * C::TA, &maps.a[sl], &full[s], x, m0);
-        tma_load_2d(st + NS * C::TA + sl * C::TB, &maps.b[sl], &full[s], x, n0);
+        for (int sl = 0; sl < NS; ++sl) {
+          tma_load_2d(st + sl * C::TA, &maps.a[sl], &full[s], x, m0);
+          tma_load_2d(st + NS * C::TA + sl * C::TB, &maps.b[sl], &full[s], x, n0);
+        }
+        issued = gi + 1;
       }
-      issued = i + 1;
     }
     // copies in flight (on an error path) land before the CTA leaves
     for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; ++i) {
@@ -213,43 +231,51 @@ __global__ void __launch_bounds__(NT, 1) fx_gemm_kernel(const __grid_constant__ 
   } else if (warp == 1 && lane == 0) {
     // D F32 (bit 4); A, B BF16 (1 at bits 7 and 10); K-major; N>>3 at bit 17; M>>4 at bit 24
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-    int i = 0;
+    int i = 0;                                    // K blocks consumed, over all tiles
+    int c = 0;                                    // chunks, over all tiles (TMEM buffer c & 1)
     bool ok = true;
-    for (int c = 0; c < nchunk && ok; ++c) {
-      const int buf = c & 1;
-      if (c >= 2 && !mbar_wait(&acce[buf], ((c >> 1) + 1) & 1, abort)) {
-        fail(p.status, abort);
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int kbn = min(C::KB_CHUNK, nk - c * C::KB_CHUNK);
-      for (int kb = 0; kb < kbn; ++kb, ++i) {
-        const int s = i % STAGES;
-        if (!mbar_wait(&full[s], (i / STAGES) & 1, abort)) {
+    for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int n0, m0, gz;
+      tile_at(t, n0, m0, gz);
+      if (skip(n0, m0)) continue;
+      const int nk = k_blocks(gz);
+      const int nchunk = (nk + C::KB_CHUNK - 1) / C::KB_CHUNK;
+      for (int cc = 0; cc < nchunk && ok; ++cc, ++c) {
+        const int buf = c & 1;
+        if (c >= 2 && !mbar_wait(&acce[buf], ((c >> 1) + 1) & 1, abort)) {
           fail(p.status, abort);
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        uint8_t* st = smem + s * C::STAGE;
+        const int kbn = min(C::KB_CHUNK, nk - cc * C::KB_CHUNK);
+        for (int kb = 0; kb < kbn; ++kb, ++i) {
+          const int s = i % STAGES;
+          if (!mbar_wait(&full[s], (i / STAGES) & 1, abort)) {
+            fail(p.status, abort);
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          uint8_t* st = smem + s * C::STAGE;
 #pragma unroll
-        for (int kk = 0; kk < C::KSTEPS; ++kk) {   // 32 bytes of K per step
-          const uint64_t o = 2 * kk;                // +32 B in the 16-byte-encoded address field
+          for (int kk = 0; kk < C::KSTEPS; ++kk) {   // 32 bytes of K per step
+            const uint64_t o = 2 * kk;                // +32 B in the 16-byte-encoded address field
 #pragma unroll
-          for (int l = 0; l < NS; ++l)
+            for (int l = 0; l < NS; ++l)
 #pragma unroll
-            for (int a = 0; a <= l; ++a) {
-              const int b = l - a;
-              const uint64_t ad = sdesc<C::LAYOUT, C::SBO>(st + a * C::TA) + o;
-              const uint64_t bd = sdesc<C::LAYOUT, C::SBO>(st + NS * C::TA + b * C::TB) + o;
-              const uint32_t dt = tbase + (uint32_t)(buf * C::LEVEL_COLS + l * BN);
-              mma_bf16(dt, ad, bd, idesc, (kb > 0 || kk > 0 || a > 0) ? 1u : 0u);
-            }
+              for (int a = 0; a <= l; ++a) {
+                const int b = l - a;
+                const uint64_t ad = sdesc<C::LAYOUT, C::SBO>(st + a * C::TA) + o;
+                const uint64_t bd = sdesc<C::LAYOUT, C::SBO>(st + NS * C::TA + b * C::TB) + o;
+                const uint32_t dt = tbase + (uint32_t)(buf * C::LEVEL_COLS + l * BN);
+                mma_bf16(dt, ad, bd, idesc, (kb > 0 || kk > 0 || a > 0) ? 1u : 0u);
+              }
+          }
+          mma_commit(&empty[s]);
         }
-        mma_commit(&empty[s]);
+        if (ok) mma_commit(&accf[buf]);
       }
-      if (ok) mma_commit(&accf[buf]);
     }
     if (!ok && i > 0) {
       // error path: the MMAs already issued finish before TMEM is released (bounded
@@ -268,60 +294,70 @@ __global__ void __launch_bounds__(NT, 1) fx_gemm_kernel(const __grid_constant__ 
     }
   } else if (warp >= 4) {
     const int q = warp & 3, h = (warp - 4) >> 2;            // TMEM lane quarter, column half
-    const int lrow = 32 * q + lane, row = m0 + lrow;
+    const int lrow = 32 * q + lane;
     constexpr int CPT = C::CPT;
     constexpr int NL = (NS == 7) ? CPT : 1;
-    long long Vh[CPT], Vl[NL];                              // Vl: levels 4.. (NS = 7 only)
-#pragma unroll
-    for (int j = 0; j < CPT; ++j) Vh[j] = 0;
-#pragma unroll
-    for (int j = 0; j < NL; ++j) Vl[j] = 0;
+    int c = 0;                                              // chunks, over all tiles
     bool ok = true;
-    for (int c = 0; c < nchunk; ++c) {
-      const int buf = c & 1;
-      const bool got = mbar_wait(&accf[buf], (c >> 1) & 1, abort);
-      if (!got) fail(p.status, abort);
-      ok = __all_sync(0xffffffffu, got);       // the TMEM loads below are warp-collective
-      if (!ok) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int n0, m0, gz;
+      tile_at(t, n0, m0, gz);
+      if (skip(n0, m0)) continue;
+      const int row = m0 + lrow;
+      const int nk = k_blocks(gz);
+      const int nchunk = (nk + C::KB_CHUNK - 1) / C::KB_CHUNK;
+      const int group = (p.kb0 + gz * C::KB_GROUP) / C::KB_GROUP;   // scale group index of the operands
+      long long Vh[CPT], Vl[NL];                            // Vl: levels 4.. (NS = 7 only)
 #pragma unroll
-      for (int cb = 0; cb < CPT / 8; ++cb) {
-        uint32_t r[NS][8];
+      for (int j = 0; j < CPT; ++j) Vh[j] = 0;
 #pragma unroll
-        for (int l = 0; l < NS; ++l)
-          tmem_ld8(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * C::LEVEL_COLS + l * BN + h * CPT + cb * 8),
-                   r[l]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      for (int j = 0; j < NL; ++j) Vl[j] = 0;
+      for (int cc = 0; cc < nchunk; ++cc, ++c) {
+        const int buf = c & 1;
+        const bool got = mbar_wait(&accf[buf], (c >> 1) & 1, abort);
+        if (!got) fail(p.status, abort);
+        ok = __all_sync(0xffffffffu, got);       // the TMEM loads below are warp-collective
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          // every level sum is an integer below 2^24: the conversions are exact
-          long long L[NS];
+        for (int cb = 0; cb < CPT / 8; ++cb) {
+          uint32_t r[NS][8];
 #pragma unroll
-          for (int l = 0; l < NS; ++l) L[l] = __float2int_rn(__uint_as_float(r[l][jj]));
-          Vh[cb * 8 + jj] += (L[0] << 24) + (L[1] << 16) + (L[2] << 8) + L[3];
-          if constexpr (NS == 7) Vl[cb * 8 + jj] += (L[4] << 16) + (L[5] << 8) + L[6];
+          for (int l = 0; l < NS; ++l)
+            tmem_ld8(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * C::LEVEL_COLS + l * BN + h * CPT + cb * 8),
+                     r[l]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            // every level sum is an integer below 2^24: the conversions are exact
+            long long L[NS];
+#pragma unroll
+            for (int l = 0; l < NS; ++l) L[l] = __float2int_rn(__uint_as_float(r[l][jj]));
+            Vh[cb * 8 + jj] += (L[0] << 24) + (L[1] << 16) + (L[2] << 8) + L[3];
+            if constexpr (NS == 7) Vl[cb * 8 + jj] += (L[4] << 16) + (L[5] << 8) + L[6];
+          }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&acce[buf]);
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(&acce[buf]);
-    }
-    if (ok && row < p.M) {
-      // value = (2^-24 Vh + 2^-48 Vl) u_a u_b = 2^-24 (Vh + 2^-24 Vl) u_a u_b; Vh, Vl exact in float64
-      const double ua = p.ua[(long long)row * p.a_ngroups + group] * 0x1p-24;
-      double* out = p.out + (long long)gz * p.split_stride;
+      if (ok && row < p.M) {
+        // value = (2^-24 Vh + 2^-48 Vl) u_a u_b = 2^-24 (Vh + 2^-24 Vl) u_a u_b; Vh, Vl exact in float64
+        const double ua = p.ua[(long long)row * p.a_ngroups + group] * 0x1p-24;
+        double* out = p.out + (long long)gz * p.split_stride;
 #pragma unroll
-      for (int j = 0; j < CPT; ++j) {
-        const int col = n0 + h * CPT + j;
-        if (col < p.N && !(p.lower_only && row / 64 < col / 64)) {
-          double v = (double)Vh[j];
-          if constexpr (NS == 7) v += (double)Vl[j] * 0x1p-24;
-          v *= ua * p.ub[(long long)col * p.b_ngroups + group];
-          if (p.diag && row == col) v += p.diag[row] * p.diag[row];
-          double* o = p.col_major ? out + (long long)col * p.out_ld + row : out + (long long)row * p.out_ld + col;
-          if (p.accumulate)
-            *o += p.alpha * v;
-          else
-            *o = v;
+        for (int j = 0; j < CPT; ++j) {
+          const int col = n0 + h * CPT + j;
+          if (col < p.N && !(p.lower_only && row / 64 < col / 64)) {
+            double v = (double)Vh[j];
+            if constexpr (NS == 7) v += (double)Vl[j] * 0x1p-24;
+            v *= ua * p.ub[(long long)col * p.b_ngroups + group];
+            if (p.diag && row == col) v += p.diag[row] * p.diag[row];
+            double* o = p.col_major ? out + (long long)col * p.out_ld + row : out + (long long)row * p.out_ld + col;
+            if (p.accumulate)
+              *o += p.alpha * v;
+            else
+              *o = v;
+          }
         }
       }
     }
@@ -410,7 +446,13 @@ int fx_launch(Exec& ex, const FxGemm& g) {
   p.alpha = g.alpha;
   p.diag = g.accumulate ? nullptr : g.diag;
   p.status = ex.status;
-  dim3 grid(ceil_div(g.N, C::BN), ceil_div(g.M, BM), fx_nsplit(g.K));
+  p.nz = fx_nsplit(g.K);
+  // persistent CTAs, one per SM (the stage ring and TMEM hold one per SM), at most one per tile
+  const long long tiles = (long long)ceil_div(g.N, C::BN) * ceil_div(g.M, BM) * p.nz;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, std::max(sms, 1)));
   KScope ks(ex, g.kclass, 1);
   cudaFuncSetAttribute(fx_gemm_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   fx_gemm_kernel<NS><<<grid, NT, C::SMEM, ex.st>>>(maps, p);
