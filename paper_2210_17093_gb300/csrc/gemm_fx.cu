@@ -12,7 +12,8 @@
 //   warps 4-11 the epilogue: for each chunk, tcgen05.ld of the levels of its 32
 //            lanes x BN/2 columns, conversion to integers (exact) and accumulation
 //            of sum_l 2^(-8l) L_l in 64-bit integers (two words for NS = 7); after
-//            the last chunk one rounding to float64 and the scales u_a u_b.
+//            the last chunk the words are joined in one 64-bit integer, rounded once
+//            to float64 and scaled by u_a u_b (powers of two).
 // Configurations:
 //   NS = 4: K block 64 elements (128-byte swizzle), BN = 64, 256-element chunks,
 //           2 stages of 96 KB;
@@ -341,22 +342,30 @@ __global__ void __launch_bounds__(NT, 1) fx_gemm_kernel(const __grid_constant__ 
         mbar_arrive(&acce[buf]);
       }
       if (ok && row < p.M) {
-        // value = (2^-24 Vh + 2^-48 Vl) u_a u_b = 2^-24 (Vh + 2^-24 Vl) u_a u_b; Vh, Vl exact in float64
-        const double ua = p.ua[(long long)row * p.a_ngroups + group] * 0x1p-24;
+        // value = 2^-24 Vh u_a u_b (4 digits) or 2^-48 (2^24 Vh + Vl) u_a u_b (7 digits), formed
+        // in integers as T = 2^14 Vh + floor(Vl / 2^10) = floor((2^24 Vh + Vl) / 2^10) (below
+        // 2^63: |Vh| < 2^49 for a 1024-element group) and rounded once to float64; the scales
+        // are powers of two (and alpha folded into u_a), so the float64 work per element is
+        // a conversion, a multiply and the fused multiply-add into the output
+        const double ua = p.ua[(long long)row * p.a_ngroups + group] * (NS == 7 ? 0x1p-38 : 0x1p-24);
+        const double uaa = p.accumulate ? ua * p.alpha : ua;
         double* out = p.out + (long long)gz * p.split_stride;
 #pragma unroll
         for (int j = 0; j < CPT; ++j) {
           const int col = n0 + h * CPT + j;
           if (col < p.N && !(p.lower_only && row / 64 < col / 64)) {
-            double v = (double)Vh[j];
-            if constexpr (NS == 7) v += (double)Vl[j] * 0x1p-24;
-            v *= ua * p.ub[(long long)col * p.b_ngroups + group];
-            if (p.diag && row == col) v += p.diag[row] * p.diag[row];
+            long long T = Vh[j];
+            if constexpr (NS == 7) T = (Vh[j] << 14) + (Vl[j] >> 10);
+            const double v = (double)T;
+            const double sc = uaa * p.ub[(long long)col * p.b_ngroups + group];
             double* o = p.col_major ? out + (long long)col * p.out_ld + row : out + (long long)row * p.out_ld + col;
-            if (p.accumulate)
-              *o += p.alpha * v;
-            else
-              *o = v;
+            if (p.accumulate) {
+              *o = fma(v, sc, *o);
+            } else {
+              double w = v * sc;
+              if (p.diag && row == col) w += p.diag[row] * p.diag[row];
+              *o = w;
+            }
           }
         }
       }

@@ -49,8 +49,9 @@ def fx_split_model(X, ns=4, group=1024, kblock=64):
 
 def fx_model(A, B, ns=4, group=1024):
     """The engine's arithmetic: exact level sums per chunk (256 elements with 4
-    digits, 128 with 7), levels combined in integers (two words with 7 digits),
-    one rounding per group, groups summed in order."""
+    digits, 128 with 7), levels combined in integers (two words with 7 digits, joined
+    into one 64-bit integer at the end of the group), one rounding per group, groups
+    summed in order."""
     chunk = 256 if ns == 4 else 128
     sa, ua, kp = fx_split_model(A, ns)
     sb, ub, _ = fx_split_model(B, ns)
@@ -68,10 +69,13 @@ def fx_model(A, B, ns=4, group=1024):
             Vh += (L[0] << 24) + (L[1] << 16) + (L[2] << 8) + L[3]
             if ns == 7:
                 Vl += (L[4] << 16) + (L[5] << 8) + L[6]
-        v = Vh.astype(np.float64)
         if ns == 7:
-            v = v + Vl.astype(np.float64) * 2.0 ** -24
-        C = C + v * (2.0 ** -24 * ua[:, g][:, None] * ub[:, g][None, :])
+            # floor((2^24 Vh + Vl) / 2^10), one rounding to float64, scale 2^-38 u_a u_b
+            v = ((Vh << 14) + (Vl >> 10)).astype(np.float64)
+            C = C + v * (2.0 ** -38 * ua[:, g][:, None] * ub[:, g][None, :])
+        else:
+            v = Vh.astype(np.float64)
+            C = C + v * (2.0 ** -24 * ua[:, g][:, None] * ub[:, g][None, :])
     return C
 
 
