@@ -173,11 +173,14 @@ __device__ __forceinline__ double chunk_rows_sum(double v, double* sh) {
 }
 
 // Sum of `cnt` partials, the same value and order in every thread of every CTA.
-__device__ double sum_partials(const double* p, int cnt, double* sh) {
+__device__ double sum_partials(const double* p, int cnt, double* sh, double v0) {
   const int t = threadIdx.x;
-  double v = (t < cnt) ? ldg_cg(p + t) : 0.0;
+  double v = v0;
   for (int k = t + RT; k < cnt; k += RT) v += ldg_cg(p + k);
   return cta_sum(v, sh);
+}
+__device__ double sum_partials(const double* p, int cnt, double* sh) {
+  return sum_partials(p, cnt, sh, (threadIdx.x < cnt) ? ldg_cg(p + threadIdx.x) : 0.0);
 }
 
 struct Refl { double tau, beta, scale, alpha; };
@@ -185,10 +188,11 @@ struct Refl { double tau, beta, scale, alpha; };
 // Sum of `cnt` partials ps[] and the largest of the non-negative pm[] (compared as
 // 64-bit integers: the bit patterns of non-negative doubles are ordered like their
 // values), both the same in every thread of every CTA.
-__device__ double sum_max_partials(const double* ps, const double* pm, int cnt, double* sh, double& mx) {
+__device__ double sum_max_partials(const double* ps, const double* pm, int cnt, double* sh, double& mx, double v0,
+                                  long long m0) {
   const int t = threadIdx.x;
-  double v = (t < cnt) ? ldg_cg(ps + t) : 0.0;
-  long long m = (t < cnt) ? __double_as_longlong(ldg_cg(pm + t)) : 0;
+  double v = v0;
+  long long m = m0;
   for (int k = t + RT; k < cnt; k += RT) {
     v += ldg_cg(ps + k);
     m = max(m, __double_as_longlong(ldg_cg(pm + k)));
@@ -206,9 +210,12 @@ __device__ double sum_max_partials(const double* ps, const double* pm, int cnt, 
 
 // The reflector of column i from P1's partial sums of squares (LAPACK dlarfg
 // convention), computed by thread 0 and shared; with xmax, also the largest |x_r| from
-// P1's chunk maxima (the fixed-point mat-vecs' scale of x).
-__device__ Refl householder(const PanelParams& p, int n_ss, double* sh, double* xmax = nullptr) {
-  const double sumsq = xmax ? sum_max_partials(p.p_ss, p.sv_mx, n_ss, sh, *xmax) : sum_partials(p.p_ss, n_ss, sh);
+// P1's chunk maxima (the fixed-point mat-vecs' scale of x).  v0 and m0 are this thread's
+// first partials (entry threadIdx.x, or 0), loaded by the caller ahead of other traffic.
+__device__ Refl householder(const PanelParams& p, int n_ss, double* sh, double v0, long long m0,
+                            double* xmax = nullptr) {
+  const double sumsq = xmax ? sum_max_partials(p.p_ss, p.sv_mx, n_ss, sh, *xmax, v0, m0)
+                            : sum_partials(p.p_ss, n_ss, sh, v0);
   if (threadIdx.x == 0) {
     const double alpha = ldg_cg(p.scal + 0);
     Refl h{0.0, alpha, 0.0, alpha};
@@ -337,6 +344,18 @@ __global__ void __launch_bounds__(256) k_ix_image(const double* __restrict__ A, 
   if (t == 0) {
     texp[blockIdx.x] = e;
     atomicMax(gmax, m);
+  }
+}
+
+// acc += v 2^s for s in [-63, 63] (a right shift, floor, for s < 0): the 128-bit shifted
+// value from two 64-bit shifts, no branch on the shift count
+__device__ __forceinline__ void add_shifted(__int128& acc, long long v, int s) {
+  if (s >= 0) {
+    const unsigned long long lo = (unsigned long long)v << s;
+    const long long hi = (v >> 1) >> (63 - s);
+    acc += ((__int128)hi << 64) | (__int128)lo;
+  } else {
+    acc += (__int128)(v >> min(-s, 63));
   }
 }
 
@@ -738,12 +757,16 @@ __global__ void __launch_bounds__(RT, MODE == kPanelTc ? 1 : 2) k_panel(PanelPar
         }
       }
     };
+    // the reflector's partials are loaded before the first tile, which would queue ahead of them
+    const double ss0 = (t < n1) ? ldg_cg(p.p_ss + t) : 0.0;
+    const long long mx0 = ((TC || IX) && t < n1) ? __double_as_longlong(ldg_cg(p.sv_mx + t)) : 0;
+    asm volatile("" ::: "memory");
     if (f0 < f1) {
       tile_of(f0, rb0, R0, J0);
       if constexpr (!TC) load_tile(R0, J0);
     }
     double xmax = 0.0;
-    const Refl h = householder(p, n1, sh, (TC || IX) ? &xmax : nullptr);
+    const Refl h = householder(p, n1, sh, ss0, mx0, (TC || IX) ? &xmax : nullptr);
     const int ixe = IX ? grid_exp(xmax) : 0;   // integer mat-vec: |x| < 2^ixe
     {
       // V^T v = V(i+1,:) + scale * (sum over the P1 chunks), the same for W^T v:
@@ -1089,7 +1112,7 @@ __global__ void __launch_bounds__(RT, MODE == kPanelTc ? 1 : 2) k_panel(PanelPar
               M = mad_wide(al[4 * c + k], xch[c], M);
             }
             const long long T = H + (M >> 27);
-            acc[k] += (sft >= 0) ? ((__int128)T << sft) : (__int128)(T >> min(-sft, 63));
+            add_shifted(acc[k], T, sft);
           }
           if (J < R) {
             long long q[4];
@@ -1269,8 +1292,7 @@ __global__ void __launch_bounds__(RT, MODE == kPanelTc ? 1 : 2) k_panel(PanelPar
             const long long v = __ldcg(reinterpret_cast<const long long*>(p.p_t) + ft * TB + (r - Rr * TB));
             const int rbi = k0 / TB;
             const int sft = __ldg(p.ix_texp + ((long long)(R2 - rbi) * (R2 - rbi + 1) / 2 + (Rr - rbi))) - ix_ref;
-            if (sft >= 0) yxi += (__int128)v << sft;
-            else yxi += (__int128)(v >> min(-sft, 63));
+            add_shifted(yxi, v, sft);
           } else {
             yx += ldg_cg(p.p_t + ft * TB + (r - Rr * TB));
           }
