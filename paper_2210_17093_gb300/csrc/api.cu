@@ -246,8 +246,10 @@ int ensure_eigfx(molgw_ctx c, Lane& l) {
   l.eig.fx_rows = l.eigfx_rows;
   l.eig.fx_cols = l.eigfx_cols;
   // the tensor-core mat-vec of the panel kernel runs on the context stream only (lane 0):
-  // its persistent launch holds one CTA per SM and TMEM, which concurrent lanes would share
-  if (&l == &c->lanes[0]) {
+  // its persistent launch holds one CTA per SM and TMEM, which concurrent lanes would share;
+  // the integer mat-vec runs on every lane (with the lane's share of the SMs)
+  const bool int_matvec = c->panel_matvec == MOLGW_MATVEC_AUTO || c->panel_matvec == MOLGW_MATVEC_INT;
+  if (&l == &c->lanes[0] || int_matvec) {
     if (rows > l.eigsv_n) {
       if (l.ex.capturing) return MOLGW_E_STATE;
       cudaStreamSynchronize(l.st);

@@ -1442,9 +1442,11 @@ void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
   // Integer mat-vec (the same arena: 32 KB images, the tiles' exponents where the tile
   // scales are, the largest |a| after the column-maximum partials).  Which one
   // runs: ex.panel_matvec (MOLGW_MATVEC_*), automatic = the integer one.
-  const bool arena = w.sv && ex.coop_cap == 0 && n <= w.sv_n;
+  // The tensor-core one only on the context's own stream (one CTA per SM and TMEM); the
+  // integer one on concurrent lanes too, with the lane's share of the co-resident CTAs.
+  const bool arena = w.sv && n <= w.sv_n;
   const int want = ex.panel_matvec;
-  const bool sv_ok = arena && g_sv_blocks_per_sm > 0 && want == MOLGW_MATVEC_TC;
+  const bool sv_ok = arena && ex.coop_cap == 0 && g_sv_blocks_per_sm > 0 && want == MOLGW_MATVEC_TC;
   const bool ix_ok = arena && g_ix_blocks_per_sm > 0 && (want == MOLGW_MATVEC_AUTO || want == MOLGW_MATVEC_INT);
 
   if (arena) {
@@ -1470,7 +1472,8 @@ void tridiagonalize(Exec& ex, EigWork& w, int n, double* A) {
       cudaMemsetAsync((void*)p.ix_gmax, 0, sizeof(unsigned long long), ex.st);
       k_ix_image<<<(unsigned)tiles_p, 256, 0, ex.st>>>(A, n, rbp, (long long*)p.ix_img, (int*)p.ix_texp,
                                                        (unsigned long long*)p.ix_gmax);
-      const int cap_ix = g_num_sms * g_ix_blocks_per_sm;
+      int cap_ix = g_num_sms * g_ix_blocks_per_sm;
+      if (ex.coop_cap > 0) cap_ix = std::max(2 * NBP / (RT / 32), std::min(cap_ix, ex.coop_cap));
       const int grid = (int)std::max<long long>(2 * NBP / (RT / 32),
                                                  std::min<long long>(cap_ix, std::max<long long>(tiles, ceil_div(n - k0, RC))));
       cudaMemsetAsync(p.bar, 0, sizeof(GridBar), ex.st);
