@@ -1145,7 +1145,7 @@ __global__ void __launch_bounds__(RT, MODE == kPanelTc ? 1 : 2) k_panel(PanelPar
           if (f + 1 == f1 || J == R) {
             // end of this CTA's part of row block R: 128-bit sums over the 16 threads that
             // hold each row (the two half-warps, then the eight warps through shared memory),
-            // rounded once to float64 on the row block's grid
+            // rounded once to float64 from the common grid
             __int128* red = reinterpret_cast<__int128*>(tile);   // [8][64]
             __int128 a2[4];
 #pragma unroll
