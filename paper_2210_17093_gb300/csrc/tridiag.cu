@@ -250,8 +250,10 @@ __device__ __forceinline__ double vval(const PanelParams& p, int i, int r, doubl
 // (|x| < 2^(e_x)), split the same way, and every product is
 //   a x = [h h_x 2^54 + (h l_x + l h_x) 2^27 + l l_x] 2^(e_T + e_x - 106),
 // formed with 32 x 32 -> 64-bit integer multiply-adds, exact; the last term (below
-// 2^-54 of the grid's unit) is left out and the middle sum's 27 low bits are dropped
-// once per tile and row, giving 64-bit tile sums in units of 2^(e_T + e_x - 52).  Those
+// 2^-54 of the grid's unit, of either sign) is left out and the middle sum is rounded to
+// a multiple of 2^27 once per thread's four elements of a row (rounded, not floored: a
+// floor would bias every row sum by n/8 units), giving 64-bit sums in units of
+// 2^(e_T + e_x - 52).  Those
 // are moved to the common grid 2^(e_g - 56 + e_x - 52) (e_g: the largest tile exponent)
 // by left shifts of at most 56 places, exact, and added in 128 bits (below 2^125 for
 // up to 1024 tiles per row), then rounded to float64 once per row; tiles more than
@@ -1111,7 +1113,7 @@ __global__ void __launch_bounds__(RT, MODE == kPanelTc ? 1 : 2) k_panel(PanelPar
               M = mad_wide(ah[4 * c + k], xcl[c], M);
               M = mad_wide(al[4 * c + k], xch[c], M);
             }
-            const long long T = H + (M >> 27);
+            const long long T = H + ((M + (1LL << 26)) >> 27);   // middle term rounded, not floored
             add_shifted(acc[k], T, sft);
           }
           if (J < R) {
@@ -1125,7 +1127,7 @@ __global__ void __launch_bounds__(RT, MODE == kPanelTc ? 1 : 2) k_panel(PanelPar
                 M = mad_wide(ah[4 * c + k], xrl[k], M);
                 M = mad_wide(al[4 * c + k], xrh[k], M);
               }
-              q[c] = H + (M >> 27);
+              q[c] = H + ((M + (1LL << 26)) >> 27);
             }
             // sums over the half-warp (the tile's 64 rows) scattering the four columns as
             // in the float64 path, in 64-bit integers (at most 2^59 in magnitude)
