@@ -66,6 +66,14 @@ def test_stage_rooflines_fractions():
     assert r7["tridiag_syr2k"]["fp64_equivalent_tflops"] == pytest.approx(useful / 0.031 / 1e12, rel=1e-3)
     rf = bench.stage_rooflines(200, 40, 600, {"sigma": 8.1, "gemm_tc": 9.4}, "bf16x10", bench.FLAG_TC_AB_BIT)
     assert rf["sigma"]["bound"] == "hbm" and rf["gemm_tc"]["bound"] == "tensor"
+    # with EIG_TC the panel's integer mat-vec reads 8-byte tile images: HBM-bound, bytes
+    # n^3/6 elements x 8 per column sweep + the image built once per 64-column panel
+    ri = bench.stage_rooflines(200, 40, 600, {"tridiag_panel": 252.6}, "bf16x10", bench.FLAG_EIG_TC_BIT)
+    p = ri["tridiag_panel"]
+    assert p["bound"] == "hbm" and p["unit"] == "GB/s"
+    assert p["achieved"] == pytest.approx((8.0 * n ** 3 / 6.0 + 16.0 * n ** 3 / 384.0) / 0.2526 / 1e9, rel=1e-3)
+    assert p["frac"] == pytest.approx(p["achieved"] / bench.measured_peaks()["hbm_gbs"], rel=1e-3)
+    assert p["fp64_equivalent_tflops"] == pytest.approx(panel / 0.2526 / 1e12, rel=1e-2)
 
 
 def test_headline_is_short_and_complete():
