@@ -52,6 +52,13 @@ def test_create_rejects_bad_opts_without_touching_the_device(lib):
     assert lib.molgw_b200_destroy(None) == 0
 
 
+def test_context_setters_reject_a_null_context_without_touching_the_device(lib):
+    assert lib.molgw_b200_set_panel_matvec(None, 0) == -1
+    assert lib.molgw_b200_set_panel_matvec(None, 3) == -1
+    assert lib.molgw_b200_set_wait_limits(None, -1, -1) == -1
+    assert lib.molgw_b200_inject_fault(None, -6) == -1
+
+
 def test_no_cpu_fallback(lib):
     """Without a usable CUDA device the product path raises; a missing library raises on load."""
     import torch
