@@ -62,8 +62,8 @@ def measured_peaks() -> dict:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "kind": "fallback"}
 # DRAM bytes the tridiagonalisation panel kernel moves per algorithmic byte (the lower
 # triangle of the trailing matrix once per column), from one ncu capture of the panel of
-# columns 1280..1343 at n = 6400: 4.536 GB measured for 6.629 GB algorithmic.
-PANEL_TRAFFIC_RATIO = 4.536 / 6.629
+# columns 1280..1343 at n = 6400: 4.564 GB measured for 6.629 GB algorithmic.
+PANEL_TRAFFIC_RATIO = 4.564 / 6.629
 
 
 def panel_bytes(n):
@@ -832,7 +832,7 @@ def run_ours(args, wl):
             "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
             "traffic": traffic, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
             "traffic_source": "ncu dram__bytes_read+write of one panel launch (n=6400, columns 1280-1343: "
-                              "4.54 GB for 6.63 GB algorithmic, part of the trailing matrix served by L2), "
+                              "4.56 GB for 6.63 GB algorithmic, part of the trailing matrix served by L2), "
                               "that ratio times the algorithmic bytes per launch",
             "launches": nl, "event_ms": kms,
         },

@@ -101,4 +101,4 @@ def test_peaks():
     assert bench.FP64_PEAK_TFLOPS == pytest.approx(1.25856, rel=1e-6)
     p = bench.measured_peaks()
     assert p["kind"] in ("measured", "fallback") and p["hbm_gbs"] > 1000 and p["bf16_tflops"] > 500
-    assert math.isclose(bench.PANEL_TRAFFIC_RATIO, 4.536 / 6.629)   # profiles/k_panel_n6400.md
+    assert math.isclose(bench.PANEL_TRAFFIC_RATIO, 4.564 / 6.629)   # profiles/k_panel_n6400.md
